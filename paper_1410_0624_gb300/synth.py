@@ -1,0 +1,111 @@
+"""Seeded synthetic density fields: the inputs both the CUDA path and the oracle read.
+
+This module holds no arithmetic of the column-density method.  It only draws
+densities with the statistics of the paper's workloads (log-normal,
+multi-decade, turbulent-like, refined by density thresholds as an AMR code
+would, §4.2 and §5) so that the library and the tests can be fed without the
+paper's simulation outputs, which are not available.
+
+Recipes (numpy PCG64, seed s):
+  * ``lognormal_iid``: z ~ N(0,1) i.i.d. per cell, n = exp(mu + sigma z) with
+    mu = ln(mean) - sigma^2/2, rescaled so that the sample mean is exactly
+    ``mean``.
+  * ``lognormal_grf``: g = irfft(FFT(white noise) x k^(-11/6)) with the k = 0
+    mode removed, so that P(k) ~ k^(-11/3); g is normalised to zero mean and
+    unit variance and exponentiated as above.
+  * ``amr_leaves``: refine a uniform base grid by thresholds on the block mean
+    of a finer field (level base+l cells whose mean exceeds thr[l] are split),
+    the way the paper's runs refine on density.
+  * ``sphere``: the uniform spherical cloud of §4.1 (n_in inside radius R,
+    n_out elsewhere) sampled at cell centres.
+Arrays are float32 and indexed [z, y, x] (x fastest).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+PC_CM = 3.0857e18
+
+
+def _rescale_lognormal(g: np.ndarray, mean: float, sigma_ln: float) -> np.ndarray:
+    mu = np.log(mean) - 0.5 * sigma_ln * sigma_ln
+    n = np.exp(mu + sigma_ln * g)
+    n *= mean / n.mean(dtype=np.float64)
+    return n.astype(np.float32)
+
+
+def lognormal_iid(n: int, mean: float, sigma_ln: float, seed: int) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    z = rng.standard_normal((n, n, n))
+    return _rescale_lognormal(z, mean, sigma_ln)
+
+
+def gaussian_random_field(n: int, seed: int, slope: float = -11.0 / 3.0) -> np.ndarray:
+    """Zero-mean, unit-variance field with power spectrum P(k) ~ k^slope."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    w = rng.standard_normal((n, n, n)).astype(np.float32)
+    wk = np.fft.rfftn(w)
+    kz = np.fft.fftfreq(n) * n
+    ky = np.fft.fftfreq(n) * n
+    kx = np.fft.rfftfreq(n) * n
+    k2 = (kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2)
+    k2[0, 0, 0] = 1.0
+    amp = k2 ** (slope / 4.0)          # |k|^(slope/2)
+    amp[0, 0, 0] = 0.0
+    g = np.fft.irfftn(wk * amp, s=(n, n, n), axes=(0, 1, 2))
+    g -= g.mean()
+    g /= g.std()
+    return g
+
+
+def lognormal_grf(n: int, mean: float, sigma_ln: float, seed: int) -> np.ndarray:
+    return _rescale_lognormal(gaussian_random_field(n, seed), mean, sigma_ln)
+
+
+def sphere(n: int, box_cm: float, radius_cm: float, n_in: float = 1000.0,
+           n_out: float = 10.0, centre_cm=None) -> np.ndarray:
+    c = np.full(3, 0.5 * box_cm) if centre_cm is None else np.asarray(centre_cm, float)
+    h = box_cm / n
+    x = (np.arange(n) + 0.5) * h
+    r2 = ((x[None, None, :] - c[0]) ** 2 + (x[None, :, None] - c[1]) ** 2
+          + (x[:, None, None] - c[2]) ** 2)
+    return np.where(r2 <= radius_cm * radius_cm, n_in, n_out).astype(np.float32)
+
+
+def _block_mean(f: np.ndarray, b: int) -> np.ndarray:
+    n = f.shape[0] // b
+    return f.reshape(n, b, n, b, n, b).mean(axis=(1, 3, 5), dtype=np.float64)
+
+
+def amr_leaves(fine: np.ndarray, base_level: int, thresholds) -> dict:
+    """Leaves of an octree refined on density.
+
+    ``fine`` is the field at the finest level lmax = base_level + len(thresholds).
+    A cell at level base_level + l (l = 0, 1, ...) is split when the mean of
+    ``fine`` over it exceeds thresholds[l]; a leaf carries that mean.
+    Returns dict(level int8 [n], ijk int32 [n,3] (x, y, z), rho float32 [n],
+    base, lmax)."""
+    nf = fine.shape[0]
+    lmax = int(round(np.log2(nf)))
+    assert (1 << lmax) == nf and lmax == base_level + len(thresholds)
+    levels, ijks, rhos = [], [], []
+    refined = None  # boolean mask of refined cells at the current level
+    for l in range(base_level, lmax + 1):
+        m = _block_mean(fine, 1 << (lmax - l))
+        n = 1 << l
+        if refined is None:
+            exists = np.ones((n, n, n), dtype=bool)
+        else:
+            exists = np.repeat(np.repeat(np.repeat(refined, 2, 0), 2, 1), 2, 2)
+        if l < lmax:
+            split = exists & (m > thresholds[l - base_level])
+        else:
+            split = np.zeros_like(exists)
+        leaf = exists & ~split
+        z, y, x = np.nonzero(leaf)
+        levels.append(np.full(z.shape[0], l, dtype=np.int8))
+        ijks.append(np.stack([x, y, z], axis=1).astype(np.int32))
+        rhos.append(m[leaf].astype(np.float32))
+        refined = split
+    return dict(level=np.concatenate(levels), ijk=np.concatenate(ijks),
+                rho=np.concatenate(rhos), base=base_level, lmax=lmax)
