@@ -1,0 +1,366 @@
+"""Throughput of the tree-based column-density hot path on one GB300.
+
+Workload (default): 256^3 uniform leaves (levels 0..8) in a 10 pc box, a
+log-normal density n = exp(g) with g a seeded Gaussian random field of power
+spectrum P(k) ~ k^-11/3 (mean 30 cm^-3, sigma_ln 2, seed 2), 48 HEALPix
+directions.  One step = the per-simulation-step hot path: restriction of the
+new leaf densities to every level (cd_tree_update) and the column densities
+of every leaf and direction with the screening factor (cd_column_density,
+N_H and shield written).  Geometry tables are built once beforehand, as the
+precalculation module does (§3.3).
+
+Metric: cell-directions/s = n_leaf * n_dir / step time (CUDA events on the
+launching stream, L2 flushed between steps, max over ranks).  With --gpus N
+every rank runs an independent replica of the workload (replicas only; the
+value is the sum over ranks).
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores (the only other place this file runs the oracle).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-directions/s for N_H"
+UNIT = "cell-dirs/s"
+# algorithmic HBM bytes per cell-direction: the N_H store (4 B) plus, per leaf,
+# the density read (4 B), the shield store (4 B) and the coarse-level reads
+# (4/7 B: levels 0..L-1 hold 1/7 of the leaf count)
+def algo_bytes_per_cell_dir(nd: int) -> float:
+    return 4.0 + (4.0 + 4.0 + 4.0 / 7.0) / nd
+
+
+def _rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def make_workload(args):
+    from paper_1410_0624_gb300 import synth
+    n = 1 << args.level
+    t0 = time.time()
+    rho = synth.lognormal_grf(n, 30.0, 2.0, seed=2)
+    return rho, 10.0 * synth.PC_CM, time.time() - t0
+
+
+def _sample_ijk(L, n, seed=11):
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 1 << L, size=(n, 3)).astype(np.int64)
+
+
+def _morton(ijk):
+    m = np.zeros(len(ijk), dtype=np.int64)
+    for b in range(21):
+        for a in range(3):
+            m |= ((ijk[:, a] >> b) & 1) << (3 * b + a)
+    return m
+
+
+def oracle_sample(rho, box, L, nside, target_s, min_leaves=16, max_leaves=20000):
+    """Times the FP64 oracle on a seeded leaf sample sized for ~target_s seconds.
+    Returns (cell-dirs/s, n_leaves, seconds, ijk, N_ref)."""
+    import oracle
+    T = oracle.Tree.uniform(rho, box)
+    dirs = oracle.dirs_healpix(nside)
+    n = min_leaves
+    while True:
+        ijk = _sample_ijk(L, n)
+        t0 = time.perf_counter()
+        ref = T.column_density(dirs, np.full(n, L), ijk)
+        dt = time.perf_counter() - t0
+        if dt >= target_s or n >= max_leaves:
+            return n * len(dirs) / dt, n, dt, ijk, ref
+        n = int(min(max_leaves, max(2 * n, n * target_s / max(dt, 1e-3) * 1.1)))
+
+
+def run_reference(args):
+    rank, world, _ = _rank()
+    if rank != 0:
+        return 0
+    rho, box, _ = make_workload(args)
+    L, nd = args.level, 12 * args.nside ** 2
+    # calibrate one step to ~2 s of CPU work, then time W + K such steps
+    rate, n, dt, _, _ = oracle_sample(rho, box, L, args.nside, 2.0)
+    import oracle
+    T = oracle.Tree.uniform(rho, box)
+    dirs = oracle.dirs_healpix(args.nside)
+    times = []
+    for s in range(args.warmup + args.steps):
+        ijk = _sample_ijk(L, n, seed=100 + s)
+        t0 = time.perf_counter()
+        T.column_density(dirs, np.full(n, L), ijk)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(times))
+    value = n * nd / (ms / 1e3)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "uniform %d^3 leaves, 10 pc, k^-11/3 log-normal (mean 30, sigma_ln 2, seed 2), "
+                                   "%d HEALPix dirs" % (1 << L, nd), "sample_leaves_per_step": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d seeded random leaves x %d dirs per step" % (n, nd)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_1410_0624_gb300 import colden
+
+    rank, world, local = _rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    colden.load()
+    precision = {"fp32": colden.FP32, "bf16": colden.BF16}[args.precision]
+
+    rho_np, box, gen_s = make_workload(args)
+    L = args.level
+    dev = torch.device("cuda", local)
+    rho = torch.from_numpy(rho_np).to(dev).reshape(-1).contiguous()
+    tree = colden.build_tree_uniform(rho.reshape(1 << L, 1 << L, 1 << L), box)
+    geom = colden.precompute_geometry("healpix", args.nside)
+    nd = geom.n_dir
+    n_leaf = tree.n_leaf
+    n_h = torch.empty(n_leaf * nd, device=dev)
+    sh = torch.empty(n_leaf, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        colden.tree_update(tree, rho, stream=stream)
+        colden.column_density(tree, geom, n_h=n_h, shield=sh, precision=precision, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    colden.stats_reset(timing=False)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    launches = sum(colden.stats_get(k)[0] for k in range(4))
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = n_leaf * nd * world / (ms / 1e3)
+
+    # per-kernel device times (separate pass, events on the launching stream)
+    colden.stats_reset(timing=True)
+    for _ in range(args.steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    kern = {}
+    for k, name in enumerate(["restrict", "shell", "leaf", "other"]):
+        n, kms = colden.stats_get(k)
+        kern[name] = {"launches_per_step": n / args.steps, "ms_per_step": kms / args.steps}
+    colden.stats_reset(timing=False)
+    dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
+    dom_ms = kern[dom]["ms_per_step"] / max(kern[dom]["launches_per_step"], 1)
+    peak, peak_kind = _peaks()
+    bpu = algo_bytes_per_cell_dir(nd)
+    achieved = bpu * n_leaf * nd / (dom_ms / 1e3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+        key = "%s/%s/L%d/nd%d" % (args.precision, dom, L, nd)
+        traffic = tr.get(key)
+    except Exception:
+        pass
+
+    # e2e: host density in, host N_H + shield out, through the public API
+    e2e = None
+    if args.e2e_steps > 0:
+        h_rho = torch.from_numpy(rho_np.reshape(-1)).pin_memory()
+        h_nh = torch.empty(n_leaf * nd, dtype=torch.float32).pin_memory()
+        h_sh = torch.empty(n_leaf, dtype=torch.float32).pin_memory()
+        d_rho = torch.empty_like(rho)
+        times = []
+        for s in range(args.e2e_steps + 1):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            d_rho.copy_(h_rho, non_blocking=True)
+            colden.tree_update(tree, d_rho, stream=stream)
+            colden.column_density(tree, geom, n_h=n_h, shield=sh, precision=precision, stream=stream)
+            h_nh.copy_(n_h, non_blocking=True)
+            h_sh.copy_(sh, non_blocking=True)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if s > 0:
+                times.append(a.elapsed_time(b))
+        e_ms = float(np.mean(times))
+        if dist:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": n_leaf * nd * world / (e_ms / 1e3), "unit": UNIT, "ms_per_step": e_ms,
+               "h2d_bytes_per_step": 4 * n_leaf, "d2h_bytes_per_step": 4 * n_leaf * nd + 4 * n_leaf}
+
+    # accuracy at a seeded leaf sample and the CPU oracle baseline (rank 0, N = 1)
+    cpu = None
+    err = None
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        rate, n, dt, ijk, ref = oracle_sample(rho_np, box, L, args.nside, args.cpu_seconds)
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d seeded random leaves x %d dirs (%.1f s)" % (n, nd, dt)}
+        rows = _morton(ijk)
+        got = n_h.reshape(-1, nd)[torch.from_numpy(rows).to(dev)].double().cpu().numpy()
+        rel = np.abs(got - ref) / ref
+        av_abs = np.abs(got - ref) / 1.87e21
+        import oracle
+        err = {"n_h_rel_max": float(rel.max()), "n_h_rel_p99": float(np.percentile(rel, 99)),
+               "a_v_abs_max": float(av_abs.max()),
+               "shield_abs_max": float(np.max(np.abs(sh[torch.from_numpy(rows).to(dev)].double().cpu().numpy()
+                                                      - oracle.shield(ref)))),
+               "leaves_checked": int(n)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16",
+                "data": "synthetic",
+                "config": {"workload": "uniform %d^3 leaves (levels 0..%d), 10 pc box, k^-11/3 log-normal "
+                                       "(mean 30, sigma_ln 2, seed 2), %d HEALPix dirs, N_H + shield out"
+                                       % (1 << L, L, nd), "precision": args.precision,
+                           "l2": "512 MB buffer written between timed steps; N_H output (%.2f GB) > L2"
+                                 % (4 * n_leaf * nd / 1e9),
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "gpu_launches": int(launches),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic, "kernel": dom,
+                             "kernel_ms": dom_ms, "peak_kind": peak_kind,
+                             "algo_bytes_per_cell_dir": bpu},
+                "step_roofline_frac": bpu * n_leaf * nd / (ms / 1e3) / 1e9 / peak,
+                "kernels": kern,
+                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "error_vs_oracle": err}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--level", type=int, default=8)
+    ap.add_argument("--nside", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

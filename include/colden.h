@@ -1,0 +1,174 @@
+/*
+ * colden.h -- C ABI of libcolden.so, a GB300 (sm_103a) implementation of the
+ * tree-based column-density method of Valdivia & Hennebelle, "A fast
+ * tree-based method for estimating column densities in Adaptive Mesh
+ * Refinement codes" (A&A, arXiv:1410.0624).
+ *
+ * For every leaf cell t of a fully threaded octree and every direction d of a
+ * sphere partition the library computes
+ *
+ *   N_H[t,d] = sum_i n_i dx_i(d)                               (Eq. N_discret1)
+ *            = internal + local (the target and its oct, §3.2)
+ *            + sum_l dx_l sum_{i in C_l} n_i K(r_i - r_t, d, dl)   (Eq. N_discret)
+ *
+ * where C_l is the cubic shell of level l, K the precomputed geometric factor
+ * of the precalculation module (§3.3), then A_V = N_H * av_per_nh and the
+ * direction-averaged screening factor shield[t] = (1/N_dir) sum_d exp(-k A_V)
+ * (Eqs. eq_chi and chi_discret with equal solid angles).
+ *
+ * Conventions shared by every entry point
+ *   - Status codes, never aborts.  cd_last_error() returns a thread-local
+ *     message describing the last failure of the calling thread.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and is asynchronous unless stated otherwise.  Device errors of
+ *     kernels surface as CD_ECUDA from a later call on the same device.
+ *   - The box is [0, box_cm]^3, non-periodic; density outside it is zero.
+ *     Level l has cells of size dx_l = box_cm / 2^l (§3.2, "dx_l = 0.5^l L").
+ *   - Octant code of a cell with integer index (i, j, k) at its level:
+ *     (i & 1) + 2 (j & 1) + 4 (k & 1).  Leaves are numbered in Morton
+ *     depth-first order (children visited in octant order); cd_tree_leaves()
+ *     returns each leaf's level and index in that order.
+ *   - Units: n in cm^-3, lengths in cm, N_H in cm^-2.
+ *   - Handles (cd_tree, cd_geom) are owned by the library and freed with the
+ *     matching *_free call, which synchronises the device first.
+ *   - All entry points are callable from several host threads on different
+ *     handles; one handle must not be used by two threads at once.
+ */
+#ifndef COLDEN_H
+#define COLDEN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cd_tree_s *cd_tree;
+typedef struct cd_geom_s *cd_geom;
+
+typedef enum {
+    CD_OK = 0,
+    CD_EINVAL = -1,        /* bad argument: message in cd_last_error() */
+    CD_ENOMEM = -2,        /* device allocation failed */
+    CD_ECUDA = -3,         /* a CUDA runtime call failed */
+    CD_ETIMEOUT = -4,      /* a bounded device-side wait gave up */
+    CD_EUNSUPPORTED = -5   /* valid request this build does not provide */
+} cd_status;
+
+/* Direction sets (§3.2). */
+enum {
+    CD_DIRS_HEALPIX = 0,   /* HEALPix ring-scheme pixel centres (Gorski et al. 2005): p0 = Nside, 12 Nside^2 dirs */
+    CD_DIRS_MXN = 1,       /* the paper's equal-area set: p0 = M, p1 = N; theta_m = arccos(1 + (1-2m)/M),
+                              phi_n = 2 pi (n-1)/N, direction index (m-1) N + (n-1) */
+    CD_DIRS_AXES = 2,      /* the six-ray set of §4.4: +x, -x, +y, -y, +z, -z */
+    CD_DIRS_CUSTOM = 3     /* caller's list of n_custom vectors (normalised by the library) */
+};
+
+/* Reference point of the external rays (§3.3 vs §4.4). */
+enum {
+    CD_MODE_PREC = 0,      /* precalculation module, two-level approximation: the shell at level l is seen from
+                              the centre of the target's ancestor at level min(l+2, l0-1) */
+    CD_MODE_INSITU = 1     /* every shell seen from the oct centre (not provided by this build) */
+};
+
+/* Arithmetic of the shell contraction. */
+enum {
+    CD_FP32 = 0,           /* FP32 CUDA-core contraction against FP32 sparse weights (<= 1e-5 rel. vs FP64) */
+    CD_BF16 = 1            /* BF16 densities x BF16 weights on the tcgen05 tensor cores, FP32 accumulate */
+};
+
+typedef struct {
+    int precision;         /* CD_FP32 or CD_BF16 */
+    int reserved0;
+    double av_per_nh;      /* A_V = N_H * av_per_nh; default 1 / 1.87e21 cm^2 */
+    double shield_k;       /* shield = <exp(-shield_k A_V)>; default 2.5 */
+    const void *net;       /* reserved for the learned correction; NULL */
+} cd_opts;
+
+/* Fills *o with the defaults above. */
+void cd_opts_default(cd_opts *o);
+
+/* Builds the octree of a uniform grid of 2^leaf_level leaves per axis
+ * (§3 intro: octs of 2^3 cells, levels 0..leaf_level) and every coarse level
+ * by the volume mean of its eight children (the coarse density "corresponds
+ * to a mean", §3.2).
+ *   leaf_level     1 .. 10
+ *   box_cm         box edge in cm, > 0
+ *   rho            (2^L)^3 floats, index (k * 2^L + j) * 2^L + i (x fastest),
+ *                  finite and >= 0; a device pointer if rho_on_device != 0,
+ *                  else host memory (copied before return)
+ *   *out           receives the new tree
+ * Errors: CD_EINVAL for bad sizes or a NULL pointer; CD_ENOMEM; CD_ECUDA.
+ * A negative or non-finite density is not detected on the device path. */
+cd_status cd_build_tree_uniform(int leaf_level, double box_cm, const float *rho, int rho_on_device,
+                                void *stream, cd_tree *out);
+
+/* Replaces the leaf densities of an existing tree built by
+ * cd_build_tree_uniform (same layout and rules as there) and recomputes every
+ * coarse level.  This is the per-step call of a simulation whose density
+ * changes but whose mesh does not; it allocates nothing.  Asynchronous for a
+ * device pointer; for host memory the data are copied before return. */
+cd_status cd_tree_update(cd_tree tree, const float *rho, int rho_on_device, void *stream);
+
+/* Precomputes the geometric factors of the precalculation module (§3.3) in
+ * FP64 on the device and stores them in FP32 (sparse lists) and BF16 (dense
+ * GEMM operands):
+ *   K1[o][d][s]       shell of level l0-1, seen from the oct centre (8 configs)
+ *   K2[o1 o2][d][s]   shell of level l0-2, seen from the oct centre (64)
+ *   K3[o1 o2 o3][d][s] shells of level l <= l0-3, seen from the centre of
+ *                      the ancestor at level l+2 (512)
+ *   Kloc[t][s][d]     rays from the centre of oct child t through child s
+ * s runs over the 6x6x6 level-l cells covering the 3x3x3 neighbourhood of the
+ * level-(l-1) ancestor; cells of the inner region get 0.
+ *   scheme         CD_DIRS_*; p0, p1 as documented there
+ *   dirs           CD_DIRS_CUSTOM only: n_custom x 3 doubles (host)
+ *   mode           CD_MODE_PREC (CD_MODE_INSITU returns CD_EUNSUPPORTED)
+ * 1 <= number of directions <= 768.  Components below 1e-14 in magnitude are
+ * set to zero and each vector renormalised. */
+cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs, int n_custom, int mode,
+                                 void *stream, cd_geom *out);
+
+/* The hot path.  For every leaf t (Morton order) and direction d:
+ *   n_h[t * n_dir + d]   N_H in cm^-2 (or NULL)
+ *   a_v[t * n_dir + d]   N_H * av_per_nh (or NULL)
+ *   shield[t]            (1/n_dir) sum_d exp(-shield_k * A_V) (or NULL)
+ * All three are caller-owned DEVICE buffers.  opts may be NULL (defaults).
+ * Scratch (per-level partial sums) is owned by the tree and reused. */
+cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts, float *n_h, float *a_v,
+                            float *shield, void *stream);
+
+/* Sizes of a tree: number of leaves, finest level, base level, number of
+ * leaf-bearing octs.  Any pointer may be NULL. */
+cd_status cd_tree_info(cd_tree tree, int64_t *n_leaf, int *max_level, int *base_level, int64_t *n_oct);
+
+/* Level and (i, j, k) index of every leaf in output order, written to host
+ * arrays of n_leaf and 3 n_leaf elements.  Synchronous. */
+cd_status cd_tree_leaves(cd_tree tree, int8_t *level, int32_t *ijk);
+
+/* Number of directions and, if dirs != NULL, the n_dir x 3 unit vectors (host). */
+cd_status cd_geom_info(cd_geom geom, int *n_dir, double *dirs);
+
+/* Launch statistics of this process, for benchmarks.  Kernel kinds: */
+enum {
+    CD_K_RESTRICT = 0,     /* level restriction and leaf reordering */
+    CD_K_SHELL = 1,        /* shell contraction of one level (FP32 or tensor core) */
+    CD_K_LEAF = 2,         /* per-leaf combine + epilogue */
+    CD_K_OTHER = 3,        /* geometry precompute and the rest */
+    CD_K_COUNT = 4
+};
+/* Resets the counters; with timing != 0 later launches also record CUDA
+ * events on their stream (a synchronisation happens in cd_stats_get). */
+void cd_stats_reset(int timing);
+/* Number of kernel launches of one kind since the reset and, if timing was
+ * on, their summed device time in milliseconds (synchronises the device). */
+cd_status cd_stats_get(int kind, int64_t *launches, double *ms);
+
+void cd_tree_free(cd_tree tree);
+void cd_geom_free(cd_geom geom);
+const char *cd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COLDEN_H */

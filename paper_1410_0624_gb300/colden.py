@@ -1,0 +1,252 @@
+"""Thin ctypes binding of libcolden.so (include/colden.h).
+
+Argument marshalling only: every step of the column-density path runs in the
+library's CUDA kernels.  PyTorch provides device memory and streams.  There is
+no CPU fallback: if the library is missing or was not built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+CD_OK, CD_EINVAL, CD_ENOMEM, CD_ECUDA, CD_ETIMEOUT, CD_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+DIRS_HEALPIX, DIRS_MXN, DIRS_AXES, DIRS_CUSTOM = 0, 1, 2, 3
+MODE_PREC, MODE_INSITU = 0, 1
+FP32, BF16 = 0, 1
+
+_STATUS = {CD_EINVAL: "EINVAL", CD_ENOMEM: "ENOMEM", CD_ECUDA: "ECUDA", CD_ETIMEOUT: "ETIMEOUT",
+           CD_EUNSUPPORTED: "EUNSUPPORTED"}
+
+# every symbol include/colden.h declares (checked by the ABI test)
+EXPORTS = (
+    "cd_opts_default", "cd_build_tree_uniform", "cd_tree_update", "cd_precompute_geometry",
+    "cd_column_density", "cd_tree_info", "cd_tree_leaves", "cd_geom_info", "cd_stats_reset", "cd_stats_get",
+    "cd_tree_free", "cd_geom_free", "cd_last_error",
+)
+K_RESTRICT, K_SHELL, K_LEAF, K_OTHER = 0, 1, 2, 3
+
+
+class ColdenError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_STATUS.get(code, code), msg))
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("reserved0", ctypes.c_int), ("av_per_nh", ctypes.c_double),
+                ("shield_k", ctypes.c_double), ("net", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Loads libcolden.so; raises if it is absent (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise RuntimeError("libcolden.so is not built (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    L.cd_opts_default.argtypes = [ctypes.POINTER(Opts)]
+    L.cd_opts_default.restype = None
+    L.cd_build_tree_uniform.argtypes = [I, D, P, I, P, ctypes.POINTER(P)]
+    L.cd_tree_update.argtypes = [P, P, I, P]
+    L.cd_stats_reset.argtypes = [I]
+    L.cd_stats_reset.restype = None
+    L.cd_stats_get.argtypes = [I, ctypes.POINTER(I64), ctypes.POINTER(D)]
+    L.cd_precompute_geometry.argtypes = [I, I, I, P, I, I, P, ctypes.POINTER(P)]
+    L.cd_column_density.argtypes = [P, P, ctypes.POINTER(Opts), P, P, P, P]
+    L.cd_tree_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I64)]
+    L.cd_tree_leaves.argtypes = [P, P, P]
+    L.cd_geom_info.argtypes = [P, ctypes.POINTER(I), P]
+    L.cd_tree_free.argtypes = [P]
+    L.cd_tree_free.restype = None
+    L.cd_geom_free.argtypes = [P]
+    L.cd_geom_free.restype = None
+    L.cd_last_error.argtypes = []
+    L.cd_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("cd_opts_default", "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_stats_reset"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(code):
+    if code != CD_OK:
+        raise ColdenError(code, load().cd_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(t):
+    if t is None:
+        return None
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and t.dtype == torch.float32
+    return t.data_ptr()
+
+
+def opts_default() -> Opts:
+    o = Opts()
+    load().cd_opts_default(ctypes.byref(o))
+    return o
+
+
+class Tree:
+    """Library-owned octree (cd_tree)."""
+
+    def __init__(self, handle):
+        self._h = ctypes.c_void_p(handle)
+        n_leaf, n_oct = ctypes.c_int64(), ctypes.c_int64()
+        lmax, base = ctypes.c_int(), ctypes.c_int()
+        _check(load().cd_tree_info(self._h, ctypes.byref(n_leaf), ctypes.byref(lmax), ctypes.byref(base),
+                                   ctypes.byref(n_oct)))
+        self.n_leaf, self.max_level, self.base_level, self.n_oct = n_leaf.value, lmax.value, base.value, n_oct.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def leaves(self):
+        """(level int8 [n], ijk int32 [n, 3]) of every leaf in output order."""
+        lv = np.zeros(self.n_leaf, dtype=np.int8)
+        ijk = np.zeros((self.n_leaf, 3), dtype=np.int32)
+        _check(load().cd_tree_leaves(self._h, lv.ctypes.data_as(ctypes.c_void_p),
+                                     ijk.ctypes.data_as(ctypes.c_void_p)))
+        return lv, ijk
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            load().cd_tree_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Geometry:
+    """Library-owned geometry tables (cd_geom)."""
+
+    def __init__(self, handle):
+        self._h = ctypes.c_void_p(handle)
+        nd = ctypes.c_int()
+        _check(load().cd_geom_info(self._h, ctypes.byref(nd), None))
+        self.n_dir = nd.value
+        d = np.zeros((self.n_dir, 3))
+        _check(load().cd_geom_info(self._h, ctypes.byref(nd), d.ctypes.data_as(ctypes.c_void_p)))
+        self.dirs = d
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            load().cd_geom_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_tree_uniform(rho, box_cm: float, stream=None) -> Tree:
+    """cd_build_tree_uniform.  rho: [n, n, n] float32 indexed [z, y, x]; a CUDA
+    tensor (device path) or a numpy array / CPU tensor (host path)."""
+    import torch
+    if isinstance(rho, torch.Tensor) and rho.is_cuda:
+        assert rho.dtype == torch.float32 and rho.is_contiguous()
+        ptr, on_dev, keep = rho.data_ptr(), 1, rho
+    else:
+        keep = np.ascontiguousarray(rho.cpu().numpy() if isinstance(rho, torch.Tensor) else rho, dtype=np.float32)
+        ptr, on_dev = keep.ctypes.data, 0
+    n = keep.shape[0]
+    L = int(n).bit_length() - 1
+    if keep.shape != (n, n, n) or (1 << L) != n:
+        raise ValueError("rho must be a cube of side 2^L")
+    h = ctypes.c_void_p()
+    _check(load().cd_build_tree_uniform(L, float(box_cm), ctypes.c_void_p(ptr), on_dev,
+                                        ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
+    return Tree(h.value)
+
+
+def tree_update(tree: Tree, rho, stream=None) -> Tree:
+    """cd_tree_update: new leaf densities for an existing uniform tree."""
+    import torch
+    if isinstance(rho, torch.Tensor) and rho.is_cuda:
+        assert rho.dtype == torch.float32 and rho.is_contiguous() and rho.numel() == tree.n_leaf
+        ptr, on_dev = rho.data_ptr(), 1
+    else:
+        keep = np.ascontiguousarray(rho.cpu().numpy() if isinstance(rho, torch.Tensor) else rho, dtype=np.float32)
+        assert keep.size == tree.n_leaf
+        ptr, on_dev = keep.ctypes.data, 0
+    _check(load().cd_tree_update(tree.handle, ctypes.c_void_p(ptr), on_dev, ctypes.c_void_p(_stream_ptr(stream))))
+    return tree
+
+
+def stats_reset(timing: bool = False):
+    load().cd_stats_reset(1 if timing else 0)
+
+
+def stats_get(kind: int):
+    """(launches, milliseconds) of one kernel kind since the last reset."""
+    n, ms = ctypes.c_int64(), ctypes.c_double()
+    _check(load().cd_stats_get(int(kind), ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
+
+
+def precompute_geometry(scheme="healpix", p0: int = 1, p1: int = 0, dirs=None, mode: int = MODE_PREC,
+                        stream=None) -> Geometry:
+    """cd_precompute_geometry.  scheme: 'healpix' (p0 = Nside), 'mxn' (p0 = M,
+    p1 = N), 'axes', 'custom' (dirs: [n, 3])."""
+    code = {"healpix": DIRS_HEALPIX, "mxn": DIRS_MXN, "axes": DIRS_AXES, "custom": DIRS_CUSTOM}[scheme] \
+        if isinstance(scheme, str) else int(scheme)
+    arr, n = None, 0
+    if code == DIRS_CUSTOM:
+        arr = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+        n = arr.shape[0]
+    h = ctypes.c_void_p()
+    _check(load().cd_precompute_geometry(code, int(p0), int(p1),
+                                         arr.ctypes.data_as(ctypes.c_void_p) if arr is not None else None, n,
+                                         int(mode), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
+    return Geometry(h.value)
+
+
+def column_density(tree: Tree, geom: Geometry, n_h=None, a_v=None, shield=None, precision: int = FP32,
+                   av_per_nh: float = 1.0 / 1.87e21, shield_k: float = 2.5, stream=None):
+    """cd_column_density into caller-owned CUDA float32 tensors (any may be None)."""
+    o = opts_default()
+    o.precision = int(precision)
+    o.av_per_nh = float(av_per_nh)
+    o.shield_k = float(shield_k)
+    _check(load().cd_column_density(tree.handle, geom.handle, ctypes.byref(o), _dptr(n_h), _dptr(a_v),
+                                    _dptr(shield), ctypes.c_void_p(_stream_ptr(stream))))
+    return n_h, a_v, shield

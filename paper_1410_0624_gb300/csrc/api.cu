@@ -1,0 +1,410 @@
+// C ABI of libcolden: argument checking, handle lifetime, workspace and the
+// order in which the kernels of one column-density evaluation run.
+//
+// Evaluation order for a tree whose leaves sit at level L (prec mode, §3.3):
+//   1. k = 3 .. L-2: S_k[c] = S_{k-1}[parent c] + far shell of level k-2 seen
+//      from the centre of c (table 3).  S_k holds, for every level-k cell, the
+//      summed shells l <= k-2 it shares with all its descendants' octs.
+//   2. k = L-1 (the octs): E[c] = S_{L-2}[parent c] + shells L-3 (table 3),
+//      L-2 (table 2) and L-1 (table 1), all seen from the oct centre.
+//   3. leaves: N_H = E[oct] + internal + local, then A_V and the shield.
+// Every shell l = 1 .. L-1 enters exactly once (Eq. N_discret).
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+#include <math.h>
+
+#include "common.cuh"
+
+namespace cd {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+static void free_workspace(cd_tree t)
+{
+    for (int l = 0; l <= CD_MAXL; ++l) {
+        if (t->ws.S[l]) cudaFree(t->ws.S[l]);
+        t->ws.S[l] = nullptr;
+    }
+    if (t->ws.E) cudaFree(t->ws.E);
+    t->ws.E = nullptr;
+    t->ws.ndir = 0;
+}
+
+static cd_status ensure_workspace(cd_tree t, int nd)
+{
+    if (t->ws.ndir == nd) return CD_OK;
+    free_workspace(t);
+    for (int k = 3; k <= t->L - 2; ++k) {
+        const size_t bytes = sizeof(float) * ((size_t)1 << (3 * k)) * nd;
+        if (cudaMalloc(&t->ws.S[k], bytes) != cudaSuccess) {
+            cudaGetLastError();
+            free_workspace(t);
+            set_error("workspace allocation failed (%zu bytes)", bytes);
+            return CD_ENOMEM;
+        }
+    }
+    if (t->L >= 2) {
+        const size_t bytes = sizeof(float) * (size_t)t->n_oct * nd;
+        if (cudaMalloc(&t->ws.E, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            free_workspace(t);
+            set_error("workspace allocation failed (%zu bytes)", bytes);
+            return CD_ENOMEM;
+        }
+    }
+    t->ws.ndir = nd;
+    return CD_OK;
+}
+
+static float dx_of(const cd_tree t, int l) { return (float)(t->box_cm / (double)((int64_t)1 << l)); }
+
+}  // namespace cd
+
+using namespace cd;
+
+extern "C" {
+
+void cd_opts_default(cd_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = CD_FP32;
+    o->av_per_nh = 1.0 / 1.87e21;
+    o->shield_k = 2.5;
+    o->net = nullptr;
+}
+
+const char *cd_last_error(void) { return g_err; }
+
+cd_status cd_build_tree_uniform(int leaf_level, double box_cm, const float *rho, int rho_on_device, void *stream,
+                                cd_tree *out)
+{
+    if (!out) {
+        set_error("out is NULL");
+        return CD_EINVAL;
+    }
+    *out = nullptr;
+    if (leaf_level < 1 || leaf_level > 10) {
+        set_error("leaf_level %d outside 1..10", leaf_level);
+        return CD_EINVAL;
+    }
+    if (!(box_cm > 0.0) || !isfinite(box_cm)) {
+        set_error("box_cm must be finite and > 0");
+        return CD_EINVAL;
+    }
+    if (!rho) {
+        set_error("rho is NULL");
+        return CD_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = leaf_level;
+    const int64_t n = (int64_t)1 << L, N = n * n * n;
+    if (!rho_on_device) {
+        for (int64_t i = 0; i < N; ++i)
+            if (!(rho[i] >= 0.f) || !isfinite(rho[i])) {
+                set_error("rho[%lld] = %g is negative or not finite", (long long)i, (double)rho[i]);
+                return CD_EINVAL;
+            }
+    }
+    cd_tree t = new cd_tree_s();
+    cudaGetDevice(&t->dev);
+    t->L = L;
+    t->base = L;
+    t->box_cm = box_cm;
+    t->n_leaf = N;
+    t->n_oct = N / 8;
+    cd_status st = CD_OK;
+    float *staging = nullptr;
+    auto fail = [&](cd_status code) {
+        if (staging) cudaFree(staging);
+        cd_tree_free(t);
+        return code;
+    };
+    if (cudaMalloc(&t->rho_leaf, sizeof(float) * N) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cannot allocate %lld leaves", (long long)N);
+        return fail(CD_ENOMEM);
+    }
+    for (int l = 0; l <= L - 1; ++l) {
+        const int64_t m = (int64_t)1 << l;
+        if (cudaMalloc(&t->rho_lvl[l], sizeof(float) * m * m * m) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cannot allocate level %d", l);
+            return fail(CD_ENOMEM);
+        }
+        if (l >= 1 && cudaMalloc(&t->rho_brick[l], sizeof(__nv_bfloat16) * m * m * m) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cannot allocate level %d bricks", l);
+            return fail(CD_ENOMEM);
+        }
+    }
+    const float *src = rho;
+    if (!rho_on_device) {
+        if (cudaMalloc(&staging, sizeof(float) * N) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cannot allocate the upload buffer");
+            return fail(CD_ENOMEM);
+        }
+        if (cudaMemcpyAsync(staging, rho, sizeof(float) * N, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            set_error("upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+            return fail(CD_ECUDA);
+        }
+        src = staging;
+    }
+    st = restrict_uniform(t, src, s);
+    if (st != CD_OK) return fail(st);
+    if (staging) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            set_error("tree build failed: %s", cudaGetErrorString(cudaGetLastError()));
+            return fail(CD_ECUDA);
+        }
+        cudaFree(staging);
+        staging = nullptr;
+    }
+    *out = t;
+    return CD_OK;
+}
+
+cd_status cd_tree_update(cd_tree t, const float *rho, int rho_on_device, void *stream)
+{
+    if (!t || !rho) {
+        set_error("tree or rho is NULL");
+        return CD_EINVAL;
+    }
+    if (t->amr) {
+        set_error("cd_tree_update serves uniform trees");
+        return CD_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = t->n_leaf;
+    if (rho_on_device) return restrict_uniform(t, rho, s);
+    for (int64_t i = 0; i < N; ++i)
+        if (!(rho[i] >= 0.f) || !isfinite(rho[i])) {
+            set_error("rho[%lld] = %g is negative or not finite", (long long)i, (double)rho[i]);
+            return CD_EINVAL;
+        }
+    // host data: stage through the workspace-independent leaf buffer is not
+    // possible (the restriction reads row-major input), so use a temporary
+    float *staging = nullptr;
+    if (cudaMallocAsync(&staging, sizeof(float) * N, s) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cannot allocate the upload buffer");
+        return CD_ENOMEM;
+    }
+    cd_status st = CD_OK;
+    if (cudaMemcpyAsync(staging, rho, sizeof(float) * N, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        set_error("upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+        st = CD_ECUDA;
+    }
+    if (st == CD_OK) st = restrict_uniform(t, staging, s);
+    cudaFreeAsync(staging, s);
+    if (st == CD_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("tree update failed: %s", cudaGetErrorString(cudaGetLastError()));
+        st = CD_ECUDA;
+    }
+    return st;
+}
+
+cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs, int n_custom, int mode,
+                                 void *stream, cd_geom *out)
+{
+    if (!out) {
+        set_error("out is NULL");
+        return CD_EINVAL;
+    }
+    *out = nullptr;
+    if (mode == CD_MODE_INSITU) {
+        set_error("the in-situ variant is not provided by this build");
+        return CD_EUNSUPPORTED;
+    }
+    if (mode != CD_MODE_PREC) {
+        set_error("unknown mode %d", mode);
+        return CD_EINVAL;
+    }
+    static thread_local double buf[3 * CD_MAXDIR];
+    const int nd = make_directions(scheme, p0, p1, dirs, n_custom, buf);
+    if (nd < 1) {
+        set_error("bad direction set (scheme %d, p0 %d, p1 %d, n_custom %d)", scheme, p0, p1, n_custom);
+        return CD_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cd_geom g = new cd_geom_s();
+    cudaGetDevice(&g->dev);
+    g->n_dir = nd;
+    g->mode = mode;
+    g->dirs_host = new double[3 * nd];
+    memcpy(g->dirs_host, buf, sizeof(double) * 3 * nd);
+    auto fail = [&](cd_status code) {
+        cd_geom_free(g);
+        return code;
+    };
+    bool ok = cudaMalloc(&g->dirs_dev, sizeof(double) * 3 * nd) == cudaSuccess;
+    for (int t = 1; t <= 3 && ok; ++t) {
+        const size_t rows = ((size_t)1 << (3 * t)) * nd;
+        ok = cudaMalloc(&g->cnt[t], rows) == cudaSuccess && cudaMalloc(&g->idx[t], rows * CD_MAXE) == cudaSuccess &&
+             cudaMalloc(&g->w[t], rows * CD_MAXE * sizeof(float)) == cudaSuccess;
+    }
+    ok = ok && cudaMalloc(&g->kloc, sizeof(float) * 64 * nd) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        set_error("geometry allocation failed");
+        return fail(CD_ENOMEM);
+    }
+    if (cudaMemcpyAsync(g->dirs_dev, g->dirs_host, sizeof(double) * 3 * nd, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess) {
+        set_error("direction upload failed");
+        return fail(CD_ECUDA);
+    }
+    cd_status st = build_geometry_tables(g, s);
+    if (st != CD_OK) return fail(st);
+    *out = g;
+    return CD_OK;
+}
+
+cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, float *n_h, float *a_v,
+                            float *shield, void *stream)
+{
+    if (!tree || !geom) {
+        set_error("tree or geometry is NULL");
+        return CD_EINVAL;
+    }
+    cd_opts opts;
+    if (opts_in) opts = *opts_in; else cd_opts_default(&opts);
+    if (opts.precision != CD_FP32 && opts.precision != CD_BF16) {
+        set_error("unknown precision %d", opts.precision);
+        return CD_EINVAL;
+    }
+    if (opts.precision == CD_BF16) {
+        set_error("BF16 path not built yet");
+        return CD_EUNSUPPORTED;
+    }
+    if (opts.net) {
+        set_error("learned correction not available");
+        return CD_EUNSUPPORTED;
+    }
+    if (!n_h && !a_v && !shield) return CD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nd = geom->n_dir, L = tree->L;
+    cd_status st = ensure_workspace(tree, nd);
+    if (st != CD_OK) return st;
+
+    for (int k = 3; k <= L - 2; ++k) {
+        ExtLaunch a = {};
+        a.k = k;
+        a.nd = nd;
+        a.tmask = 4;
+        a.rho[3] = tree->rho_lvl[k - 2];
+        a.dx[3] = dx_of(tree, k - 2);
+        a.prefix_in = (k > 3) ? tree->ws.S[k - 1] : nullptr;
+        a.out = tree->ws.S[k];
+        if ((st = launch_ext_fp32(a, geom, s)) != CD_OK) return st;
+    }
+    if (L >= 2) {
+        ExtLaunch a = {};
+        const int k = L - 1;
+        a.k = k;
+        a.nd = nd;
+        for (int t = 1; t <= 3 && t <= k; ++t) {
+            a.tmask |= 1 << (t - 1);
+            a.rho[t] = tree->rho_lvl[k - t + 1];
+            a.dx[t] = dx_of(tree, k - t + 1);
+        }
+        a.prefix_in = (L - 2 >= 3) ? tree->ws.S[L - 2] : nullptr;
+        a.out = tree->ws.E;
+        if ((st = launch_ext_fp32(a, geom, s)) != CD_OK) return st;
+    }
+    LeafLaunch b = {};
+    b.n_oct = tree->n_oct;
+    b.nd = nd;
+    b.dx_leaf = dx_of(tree, L);
+    b.av_per_nh = (float)opts.av_per_nh;
+    b.shield_k = (float)opts.shield_k;
+    b.rho_leaf = tree->rho_leaf;
+    b.E = tree->ws.E;
+    b.kloc = geom->kloc;
+    b.n_h = n_h;
+    b.a_v = a_v;
+    b.shield = shield;
+    return launch_leaf(b, s);
+}
+
+cd_status cd_tree_info(cd_tree t, int64_t *n_leaf, int *max_level, int *base_level, int64_t *n_oct)
+{
+    if (!t) {
+        set_error("tree is NULL");
+        return CD_EINVAL;
+    }
+    if (n_leaf) *n_leaf = t->n_leaf;
+    if (max_level) *max_level = t->L;
+    if (base_level) *base_level = t->base;
+    if (n_oct) *n_oct = t->n_oct;
+    return CD_OK;
+}
+
+cd_status cd_tree_leaves(cd_tree t, int8_t *level, int32_t *ijk)
+{
+    if (!t) {
+        set_error("tree is NULL");
+        return CD_EINVAL;
+    }
+    for (int64_t i = 0; i < t->n_leaf; ++i) {
+        if (level) level[i] = (int8_t)t->L;
+        if (ijk) {
+            ijk[3 * i] = (int32_t)compact3((uint64_t)i);
+            ijk[3 * i + 1] = (int32_t)compact3((uint64_t)i >> 1);
+            ijk[3 * i + 2] = (int32_t)compact3((uint64_t)i >> 2);
+        }
+    }
+    return CD_OK;
+}
+
+cd_status cd_geom_info(cd_geom g, int *n_dir, double *dirs)
+{
+    if (!g) {
+        set_error("geometry is NULL");
+        return CD_EINVAL;
+    }
+    if (n_dir) *n_dir = g->n_dir;
+    if (dirs) memcpy(dirs, g->dirs_host, sizeof(double) * 3 * g->n_dir);
+    return CD_OK;
+}
+
+void cd_tree_free(cd_tree t)
+{
+    if (!t) return;
+    cudaDeviceSynchronize();
+    free_workspace(t);
+    for (int l = 0; l <= CD_MAXL; ++l) {
+        if (t->rho_lvl[l]) cudaFree(t->rho_lvl[l]);
+        if (t->rho_brick[l]) cudaFree(t->rho_brick[l]);
+    }
+    if (t->rho_leaf) cudaFree(t->rho_leaf);
+    delete t;
+}
+
+void cd_geom_free(cd_geom g)
+{
+    if (!g) return;
+    cudaDeviceSynchronize();
+    if (g->dirs_dev) cudaFree(g->dirs_dev);
+    for (int t = 0; t < 4; ++t) {
+        if (g->cnt[t]) cudaFree(g->cnt[t]);
+        if (g->idx[t]) cudaFree(g->idx[t]);
+        if (g->w[t]) cudaFree(g->w[t]);
+    }
+    if (g->kloc) cudaFree(g->kloc);
+    if (g->wb) cudaFree(g->wb);
+    delete[] g->dirs_host;
+    delete g;
+}
+
+}  // extern "C"

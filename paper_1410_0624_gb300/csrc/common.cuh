@@ -1,0 +1,160 @@
+// Internal declarations of libcolden: handle layouts, error plumbing, Morton
+// helpers and the kernel launchers each translation unit provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/colden.h"
+
+#define CD_MAXL 16          // deepest level a tree may have
+#define CD_STENCIL 216      // 6 x 6 x 6 level-l cells around a level-(l-1) ancestor
+#define CD_MAXE 16          // most non-zero weights one ray can have in a 6^3 stencil
+#define CD_MAXDIR 768       // the leaf kernel stages 64 * n_dir floats in shared memory
+
+namespace cd {
+
+void set_error(const char *fmt, ...);
+
+#define CD_CUDA(call)                                                                  \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            ::cd::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call,                  \
+                            cudaGetErrorString(e_));                                   \
+            return CD_ECUDA;                                                           \
+        }                                                                              \
+    } while (0)
+
+#define CD_CHECK_LAUNCH()                                                              \
+    do {                                                                               \
+        cudaError_t e_ = cudaGetLastError();                                           \
+        if (e_ != cudaSuccess) {                                                       \
+            ::cd::set_error("%s:%d kernel launch: %s", __FILE__, __LINE__,             \
+                            cudaGetErrorString(e_));                                   \
+            return CD_ECUDA;                                                           \
+        }                                                                              \
+    } while (0)
+
+// ---- Morton (octant bits x = 1, y = 2, z = 4) --------------------------------
+
+__host__ __device__ inline uint64_t spread3(uint32_t v)
+{
+    uint64_t x = v & 0x1fffff;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+__host__ __device__ inline uint32_t compact3(uint64_t x)
+{
+    x &= 0x1249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+    x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+    x = (x ^ (x >> 32)) & 0x1fffff;
+    return (uint32_t)x;
+}
+
+__host__ __device__ inline uint64_t morton3(uint32_t x, uint32_t y, uint32_t z)
+{
+    return spread3(x) | (spread3(y) << 1) | (spread3(z) << 2);
+}
+
+// ---- handles -----------------------------------------------------------------
+
+struct Workspace {
+    int ndir = 0;
+    float *S[CD_MAXL + 1] = {};  // prefix sums of the far shells, Morton order, [8^k][ndir]
+    float *E = nullptr;          // external column of every oct, Morton order, [n_oct][ndir]
+};
+
+}  // namespace cd
+
+struct cd_tree_s {
+    int L = 0;                          // finest leaf level
+    int base = 0;                       // base (coarsest leaf) level
+    int amr = 0;
+    double box_cm = 0;
+    int64_t n_leaf = 0;
+    int64_t n_oct = 0;                  // leaf-bearing octs (uniform: 8^(L-1))
+    float *rho_lvl[CD_MAXL + 1] = {};   // dense row-major volume means, levels 0..L-1
+    __nv_bfloat16 *rho_brick[CD_MAXL + 1] = {};  // BF16 copies in brick order (tensor path)
+    float *rho_leaf = nullptr;          // leaf densities, Morton order
+    cd::Workspace ws;
+    int dev = 0;
+};
+
+struct cd_geom_s {
+    int n_dir = 0;
+    int mode = 0;
+    double *dirs_host = nullptr;        // n_dir x 3
+    double *dirs_dev = nullptr;
+    // sparse FP32 shell tables, t = 1..3 (index 0 unused): for entry (cfg, d)
+    // cnt[cfg*nd + d] non-zeros, idx/w[(cfg*nd + d)*CD_MAXE + e]
+    uint8_t *cnt[4] = {};
+    uint8_t *idx[4] = {};
+    float *w[4] = {};
+    float *kloc = nullptr;              // [8 t][8 s][nd], units of dx
+    // BF16 B operands for the tensor-core contraction (see colden_tc.cu)
+    __nv_bfloat16 *wb = nullptr;
+    size_t wb_bytes = 0;
+    int max_entries = 0;
+    int dev = 0;
+};
+
+namespace cd {
+
+// stats.cu: counts (and optionally times) one kernel launch on stream s for
+// the lifetime of the scope; construct it right before the launch.
+class LaunchScope {
+  public:
+    LaunchScope(int kind, cudaStream_t s);
+    ~LaunchScope();
+    LaunchScope(const LaunchScope &) = delete;
+    LaunchScope &operator=(const LaunchScope &) = delete;
+
+  private:
+    int kind_;
+    cudaStream_t s_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
+// tree.cu
+cd_status restrict_uniform(cd_tree t, const float *rho_dev, cudaStream_t s);
+
+// geometry.cu
+int make_directions(int scheme, int p0, int p1, const double *custom, int n_custom, double *out);
+cd_status build_geometry_tables(cd_geom g, cudaStream_t s);
+
+// colden_fp32.cu
+struct ExtLaunch {
+    int k;                    // level of the cells that receive the sum
+    int nd;
+    int tmask;                // bit (t-1): table t contributes (shell level k - t + 1)
+    const float *rho[4];      // dense level arrays of the shell level of each table
+    float dx[4];              // dx of that shell level, cm
+    const float *prefix_in;   // S_{k-1} (Morton) or NULL
+    float *out;               // Morton [8^k][nd]
+};
+cd_status launch_ext_fp32(const ExtLaunch &a, cd_geom g, cudaStream_t s);
+
+struct LeafLaunch {
+    int64_t n_oct;
+    int nd;
+    float dx_leaf;
+    float av_per_nh, shield_k;
+    const float *rho_leaf;    // Morton, 8 per oct
+    const float *E;           // [n_oct][nd] or NULL
+    const float *kloc;        // [8][8][nd]
+    float *n_h, *a_v, *shield;
+};
+cd_status launch_leaf(const LeafLaunch &a, cudaStream_t s);
+
+}  // namespace cd
