@@ -138,6 +138,29 @@ cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs,
 cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts, float *n_h, float *a_v,
                             float *shield, void *stream);
 
+/* Same evaluation as cd_column_density (FP32, uniform trees), but its scratch
+ * lives in a fixed 16 MiB device array compiled into the library, so the call
+ * allocates and frees nothing.  The paper has no counterpart: this serves
+ * simulation codes that reserve all device memory once at start-up and must
+ * not allocate inside their time-step loop (allocation calls may synchronise
+ * the device and stall an asynchronous step loop).  Build the tree and the
+ * geometry during set-up, then call this every step.
+ *   Limit: n_dir * (8^3 + ... + 8^(L-2) + 8^(L-1)) floats (plus 256-byte
+ *   rounding) must fit in 4 Mi floats, e.g. L <= 6 with 48 directions; larger
+ *   trees get CD_EINVAL with the required size in cd_last_error().
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Every call on a device shares the one array and leaves its contents
+ *   behind; nothing in it needs clearing (each element read is written
+ *   earlier in the same call).  Calls that overlap on the GPU (different
+ *   streams or host threads) race on the array: serialise them.
+ *   Every GPU that loads the library holds the 16 MiB until the process exits.
+ * Other arguments, outputs and errors as for cd_column_density;
+ * CD_EUNSUPPORTED for BF16, AMR trees or a learned correction. */
+cd_status cd_column_density_noalloc(cd_tree tree, cd_geom geom, const cd_opts *opts, float *n_h, float *a_v,
+                                    float *shield, void *stream);
+
 /* Sizes of a tree: number of leaves, finest level, base level, number of
  * leaf-bearing octs.  Any pointer may be NULL. */
 cd_status cd_tree_info(cd_tree tree, int64_t *n_leaf, int *max_level, int *base_level, int64_t *n_oct);

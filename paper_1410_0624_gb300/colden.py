@@ -26,7 +26,7 @@ _STATUS = {CD_EINVAL: "EINVAL", CD_ENOMEM: "ENOMEM", CD_ECUDA: "ECUDA", CD_ETIME
 EXPORTS = (
     "cd_opts_default", "cd_build_tree_uniform", "cd_tree_update", "cd_precompute_geometry",
     "cd_column_density", "cd_tree_info", "cd_tree_leaves", "cd_geom_info", "cd_stats_reset", "cd_stats_get",
-    "cd_tree_free", "cd_geom_free", "cd_last_error",
+    "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_column_density_noalloc",
 )
 K_RESTRICT, K_SHELL, K_LEAF, K_OTHER = 0, 1, 2, 3
 
@@ -71,6 +71,7 @@ def load(build_if_missing: bool = False):
     L.cd_stats_get.argtypes = [I, ctypes.POINTER(I64), ctypes.POINTER(D)]
     L.cd_precompute_geometry.argtypes = [I, I, I, P, I, I, P, ctypes.POINTER(P)]
     L.cd_column_density.argtypes = [P, P, ctypes.POINTER(Opts), P, P, P, P]
+    L.cd_column_density_noalloc.argtypes = [P, P, ctypes.POINTER(Opts), P, P, P, P]
     L.cd_tree_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I64)]
     L.cd_tree_leaves.argtypes = [P, P, P]
     L.cd_geom_info.argtypes = [P, ctypes.POINTER(I), P]
@@ -249,4 +250,19 @@ def column_density(tree: Tree, geom: Geometry, n_h=None, a_v=None, shield=None, 
     o.shield_k = float(shield_k)
     _check(load().cd_column_density(tree.handle, geom.handle, ctypes.byref(o), _dptr(n_h), _dptr(a_v),
                                     _dptr(shield), ctypes.c_void_p(_stream_ptr(stream))))
+    return n_h, a_v, shield
+
+
+def column_density_noalloc(tree: Tree, geom: Geometry, n_h=None, a_v=None, shield=None,
+                           av_per_nh: float = 1.0 / 1.87e21, shield_k: float = 2.5, stream=None):
+    """cd_column_density_noalloc: FP32 evaluation whose scratch is a fixed
+    16 MiB device array inside the library, for callers that must not
+    allocate device memory once their time-step loop runs (small trees only,
+    see include/colden.h)."""
+    o = opts_default()
+    o.precision = FP32
+    o.av_per_nh = float(av_per_nh)
+    o.shield_k = float(shield_k)
+    _check(load().cd_column_density_noalloc(tree.handle, geom.handle, ctypes.byref(o), _dptr(n_h), _dptr(a_v),
+                                            _dptr(shield), ctypes.c_void_p(_stream_ptr(stream))))
     return n_h, a_v, shield
