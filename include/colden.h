@@ -172,6 +172,13 @@ cd_status cd_tree_leaves(cd_tree tree, int8_t *level, int32_t *ijk);
 /* Number of directions and, if dirs != NULL, the n_dir x 3 unit vectors (host). */
 cd_status cd_geom_info(cd_geom geom, int *n_dir, double *dirs);
 
+/* Synchronises `stream` and reports whether any library kernel on the current
+ * device gave up a bounded wait since the last call: CD_ETIMEOUT (flag
+ * cleared, message in cd_last_error()) or CD_OK.  Kernels never trap; a wait
+ * that runs out of polls records this flag and the kernel returns early, so
+ * its outputs are then incomplete. */
+cd_status cd_device_status(void *stream);
+
 /* Launch statistics of this process, for benchmarks.  Kernel kinds: */
 enum {
     CD_K_RESTRICT = 0,     /* level restriction and leaf reordering */

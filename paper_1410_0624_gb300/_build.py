@@ -20,7 +20,10 @@ LIB = os.path.join(LIBDIR, "libcolden.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+# -ftz=true: FP32 denormals flush to zero.  The path's FP32 values (densities,
+# path lengths x cell sizes, columns) are normal numbers; only exp() of very
+# negative screening arguments underflows, to 0 instead of a denormal.
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-ftz=true",
          "-I", INCLUDE]
 
 

@@ -26,7 +26,7 @@ _STATUS = {CD_EINVAL: "EINVAL", CD_ENOMEM: "ENOMEM", CD_ECUDA: "ECUDA", CD_ETIME
 EXPORTS = (
     "cd_opts_default", "cd_build_tree_uniform", "cd_tree_update", "cd_precompute_geometry",
     "cd_column_density", "cd_tree_info", "cd_tree_leaves", "cd_geom_info", "cd_stats_reset", "cd_stats_get",
-    "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_column_density_noalloc",
+    "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_column_density_noalloc", "cd_device_status",
 )
 K_RESTRICT, K_SHELL, K_LEAF, K_OTHER = 0, 1, 2, 3
 
@@ -72,6 +72,7 @@ def load(build_if_missing: bool = False):
     L.cd_precompute_geometry.argtypes = [I, I, I, P, I, I, P, ctypes.POINTER(P)]
     L.cd_column_density.argtypes = [P, P, ctypes.POINTER(Opts), P, P, P, P]
     L.cd_column_density_noalloc.argtypes = [P, P, ctypes.POINTER(Opts), P, P, P, P]
+    L.cd_device_status.argtypes = [P]
     L.cd_tree_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I64)]
     L.cd_tree_leaves.argtypes = [P, P, P]
     L.cd_geom_info.argtypes = [P, ctypes.POINTER(I), P]
@@ -211,6 +212,11 @@ def tree_update(tree: Tree, rho, stream=None) -> Tree:
         ptr, on_dev = keep.ctypes.data, 0
     _check(load().cd_tree_update(tree.handle, ctypes.c_void_p(ptr), on_dev, ctypes.c_void_p(_stream_ptr(stream))))
     return tree
+
+
+def device_status(stream=None):
+    """cd_device_status: raises ColdenError(CD_ETIMEOUT) if a kernel gave up a bounded wait."""
+    _check(load().cd_device_status(ctypes.c_void_p(_stream_ptr(stream))))
 
 
 def stats_reset(timing: bool = False):

@@ -249,9 +249,9 @@ cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs,
     };
     bool ok = cudaMalloc(&g->dirs_dev, sizeof(double) * 3 * nd) == cudaSuccess;
     for (int t = 1; t <= 3 && ok; ++t) {
-        const size_t rows = ((size_t)1 << (3 * t)) * nd;
-        ok = cudaMalloc(&g->cnt[t], rows) == cudaSuccess && cudaMalloc(&g->idx[t], rows * CD_MAXE) == cudaSuccess &&
-             cudaMalloc(&g->w[t], rows * CD_MAXE * sizeof(float)) == cudaSuccess;
+        const size_t ncfg = (size_t)1 << (3 * t);
+        ok = cudaMalloc(&g->tab[t], ncfg * CD_MAXE * nd * sizeof(int2)) == cudaSuccess &&
+             cudaMalloc(&g->cmax[t], ncfg * sizeof(int)) == cudaSuccess;
     }
     ok = ok && cudaMalloc(&g->kloc, sizeof(float) * 64 * nd) == cudaSuccess;
     if (!ok) {
@@ -337,6 +337,12 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
     return launch_leaf(b, s);
 }
 
+cd_status cd_device_status(void *stream)
+{
+    CD_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return leaf_fault_check();
+}
+
 cd_status cd_tree_info(cd_tree t, int64_t *n_leaf, int *max_level, int *base_level, int64_t *n_oct)
 {
     if (!t) {
@@ -397,9 +403,8 @@ void cd_geom_free(cd_geom g)
     cudaDeviceSynchronize();
     if (g->dirs_dev) cudaFree(g->dirs_dev);
     for (int t = 0; t < 4; ++t) {
-        if (g->cnt[t]) cudaFree(g->cnt[t]);
-        if (g->idx[t]) cudaFree(g->idx[t]);
-        if (g->w[t]) cudaFree(g->w[t]);
+        if (g->tab[t]) cudaFree(g->tab[t]);
+        if (g->cmax[t]) cudaFree(g->cmax[t]);
     }
     if (g->kloc) cudaFree(g->kloc);
     if (g->wb) cudaFree(g->wb);

@@ -18,6 +18,13 @@ namespace cd {
 
 void set_error(const char *fmt, ...);
 
+// Shared-memory staging of the shell kernels: the density region read by
+// table t is a cube of side kRegionSide[t] level-(k-t+1) cells (6 + 2 x the
+// ancestors per axis of one CTA) starting at kRegionBase[t].
+__host__ __device__ constexpr int region_side(int t) { return t == 1 ? 12 : t == 2 ? 8 : t == 3 ? 6 : 0; }
+__host__ __device__ constexpr int region_base(int t) { return t == 2 ? 12 * 12 * 12 : t == 3 ? 12 * 12 * 12 + 8 * 8 * 8 : 0; }
+constexpr int kRegionTotal = 12 * 12 * 12 + 8 * 8 * 8 + 6 * 6 * 6;
+
 #define CD_CUDA(call)                                                                  \
     do {                                                                               \
         cudaError_t e_ = (call);                                                       \
@@ -96,11 +103,11 @@ struct cd_geom_s {
     int mode = 0;
     double *dirs_host = nullptr;        // n_dir x 3
     double *dirs_dev = nullptr;
-    // sparse FP32 shell tables, t = 1..3 (index 0 unused): for entry (cfg, d)
-    // cnt[cfg*nd + d] non-zeros, idx/w[(cfg*nd + d)*CD_MAXE + e]
-    uint8_t *cnt[4] = {};
-    uint8_t *idx[4] = {};
-    float *w[4] = {};
+    // sparse FP32 shell tables, t = 1..3 (index 0 unused): entry e of (cfg, d)
+    // at tab[t][(cfg * CD_MAXE + e) * nd + d] = {offset in the staged region of
+    // table t, weight bits}; cmax[t][cfg] = largest non-zero count over d
+    int2 *tab[4] = {};
+    int *cmax[4] = {};
     float *kloc = nullptr;              // [8 t][8 s][nd], units of dx
     // BF16 B operands for the tensor-core contraction (see colden_tc.cu)
     __nv_bfloat16 *wb = nullptr;
@@ -156,5 +163,8 @@ struct LeafLaunch {
     float *n_h, *a_v, *shield;
 };
 cd_status launch_leaf(const LeafLaunch &a, cudaStream_t s);
+
+// leaf.cu: CD_ETIMEOUT if a leaf kernel gave up a bounded wait (clears it)
+cd_status leaf_fault_check();
 
 }  // namespace cd

@@ -131,10 +131,11 @@ __device__ double path_in_cube(const double *p, const double *u, double lx, doub
     return leave > enter ? leave - enter : 0.0;
 }
 
-__global__ void shell_tables(int t, int nd, const double *__restrict__ dirs, uint8_t *__restrict__ cnt,
-                             uint8_t *__restrict__ idx, float *__restrict__ w, int *__restrict__ max_count)
+__global__ void shell_tables(int t, int nd, const double *__restrict__ dirs, int2 *__restrict__ tab,
+                             int *__restrict__ cmax, int *__restrict__ max_count)
 {
     const int ncfg = 1 << (3 * t);
+    const int R = region_side(t);
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncfg * nd; e += gridDim.x * blockDim.x) {
         const int cfg = e / nd, d = e - cfg * nd;
         const double u[3] = {dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2]};
@@ -149,6 +150,7 @@ __global__ void shell_tables(int t, int nd, const double *__restrict__ dirs, uin
             p[a] = x + ldexp(1.0, -t);
             top[a] = 2 + (((cfg >> (3 * (t - 1))) >> a) & 1);
         }
+        int2 *row = tab + (size_t)cfg * CD_MAXE * nd + d;
         int n = 0;
         for (int s = 0; s < CD_STENCIL; ++s) {
             const int a = s % 6, b = (s / 6) % 6, c = s / 36;
@@ -157,18 +159,12 @@ __global__ void shell_tables(int t, int nd, const double *__restrict__ dirs, uin
             if (inner) continue;
             const double len = path_in_cube(p, u, a, b, c);
             if (len > 0.0) {
-                if (n < CD_MAXE) {
-                    idx[(size_t)e * CD_MAXE + n] = (uint8_t)s;
-                    w[(size_t)e * CD_MAXE + n] = (float)len;
-                }
+                if (n < CD_MAXE) row[(size_t)n * nd] = make_int2(a + R * (b + R * c), __float_as_int((float)len));
                 ++n;
             }
         }
-        for (int m = n; m < CD_MAXE; ++m) {
-            idx[(size_t)e * CD_MAXE + m] = 0;
-            w[(size_t)e * CD_MAXE + m] = 0.f;
-        }
-        cnt[e] = (uint8_t)(n < CD_MAXE ? n : CD_MAXE);
+        for (int m = n; m < CD_MAXE; ++m) row[(size_t)m * nd] = make_int2(0, 0);
+        atomicMax(&cmax[cfg], n < CD_MAXE ? n : CD_MAXE);
         atomicMax(max_count, n);
     }
 }
@@ -196,8 +192,9 @@ cd_status build_geometry_tables(cd_geom g, cudaStream_t s)
     CD_CUDA(cudaMemsetAsync(d_max, 0, sizeof(int), s));
     for (int t = 1; t <= 3; ++t) {
         const int n = (1 << (3 * t)) * nd;
+        CD_CUDA(cudaMemsetAsync(g->cmax[t], 0, sizeof(int) << (3 * t), s));
         LaunchScope ls(CD_K_OTHER, s);
-        shell_tables<<<(n + 127) / 128, 128, 0, s>>>(t, nd, g->dirs_dev, g->cnt[t], g->idx[t], g->w[t], d_max);
+        shell_tables<<<(n + 127) / 128, 128, 0, s>>>(t, nd, g->dirs_dev, g->tab[t], g->cmax[t], d_max);
         CD_CHECK_LAUNCH();
     }
     {

@@ -174,6 +174,24 @@ def test_only_requested_outputs_written_and_launches_counted():
     colden.stats_reset(timing=False)
 
 
+@pytest.mark.parametrize("offset", [0, 1])
+def test_unaligned_outputs_take_the_generic_kernel(offset):
+    L, box = 4, 2 * PC
+    rho = synth.lognormal_grf(16, 30.0, 2.0, seed=12)
+    tree = colden.build_tree_uniform(torch.from_numpy(rho).cuda(), box)
+    geom, dirs = _geom("healpix1")
+    nd = geom.n_dir
+    buf = torch.full((tree.n_leaf * nd + 4,), -1.0, device="cuda")
+    sbuf = torch.full((tree.n_leaf + 4,), -1.0, device="cuda")
+    n_h, sh = buf[offset:offset + tree.n_leaf * nd], sbuf[offset:offset + tree.n_leaf]
+    colden.column_density(tree, geom, n_h=n_h, shield=sh)
+    colden.device_status()
+    lv, ijk = tree.leaves()
+    ref = oracle.Tree.uniform(rho, box).column_density(dirs, lv, ijk)
+    _compare(n_h.double().cpu().numpy(), None, sh.double().cpu().numpy(), ref, nd)
+    assert buf[:offset].eq(-1).all() and buf[offset + tree.n_leaf * nd:].eq(-1).all()
+
+
 def test_invalid_arguments_rejected():
     with pytest.raises(colden.ColdenError):
         colden.precompute_geometry("mxn", 0, 4)
