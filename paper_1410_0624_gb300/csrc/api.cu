@@ -266,6 +266,7 @@ cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs,
     }
     cd_status st = build_geometry_tables(g, s);
     if (st != CD_OK) return fail(st);
+    if ((st = build_tc_tables(g, s)) != CD_OK) return fail(st);
     *out = g;
     return CD_OK;
 }
@@ -283,10 +284,6 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
         set_error("unknown precision %d", opts.precision);
         return CD_EINVAL;
     }
-    if (opts.precision == CD_BF16) {
-        set_error("BF16 path not built yet");
-        return CD_EUNSUPPORTED;
-    }
     if (opts.net) {
         set_error("learned correction not available");
         return CD_EUNSUPPORTED;
@@ -296,6 +293,10 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
     const int nd = geom->n_dir, L = tree->L;
     cd_status st = ensure_workspace(tree, nd);
     if (st != CD_OK) return st;
+    // BF16 tensor cores for receiving levels >= 4 when the direction count
+    // fits the accumulator; the few cells of coarser levels stay FP32
+    const bool bf16 = opts.precision == CD_BF16 && tc_supported(nd) && geom->wb != nullptr;
+    const auto use_tc = [&](int k) { return bf16 && k >= 4; };
 
     for (int k = 3; k <= L - 2; ++k) {
         ExtLaunch a = {};
@@ -306,7 +307,8 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
         a.dx[3] = dx_of(tree, k - 2);
         a.prefix_in = (k > 3) ? tree->ws.S[k - 1] : nullptr;
         a.out = tree->ws.S[k];
-        if ((st = launch_ext_fp32(a, geom, s)) != CD_OK) return st;
+        st = use_tc(k) ? launch_ext_tc(a, tree->rho_brick, geom, s) : launch_ext_fp32(a, geom, s);
+        if (st != CD_OK) return st;
     }
     if (L >= 2) {
         ExtLaunch a = {};
@@ -320,7 +322,8 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
         }
         a.prefix_in = (L - 2 >= 3) ? tree->ws.S[L - 2] : nullptr;
         a.out = tree->ws.E;
-        if ((st = launch_ext_fp32(a, geom, s)) != CD_OK) return st;
+        st = use_tc(k) ? launch_ext_tc(a, tree->rho_brick, geom, s) : launch_ext_fp32(a, geom, s);
+        if (st != CD_OK) return st;
     }
     LeafLaunch b = {};
     b.n_oct = tree->n_oct;
@@ -340,7 +343,9 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
 cd_status cd_device_status(void *stream)
 {
     CD_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-    return leaf_fault_check();
+    cd_status a = leaf_fault_check();
+    cd_status b = tc_fault_check();
+    return a != CD_OK ? a : b;
 }
 
 cd_status cd_tree_info(cd_tree t, int64_t *n_leaf, int *max_level, int *base_level, int64_t *n_oct)

@@ -167,4 +167,10 @@ cd_status launch_leaf(const LeafLaunch &a, cudaStream_t s);
 // leaf.cu: CD_ETIMEOUT if a leaf kernel gave up a bounded wait (clears it)
 cd_status leaf_fault_check();
 
+// colden_tc.cu: BF16 tensor-core shell contraction for receiving levels >= 4
+bool tc_supported(int nd);
+cd_status build_tc_tables(cd_geom g, cudaStream_t s);
+cd_status launch_ext_tc(const ExtLaunch &a, const __nv_bfloat16 *const *brick, cd_geom g, cudaStream_t s);
+cd_status tc_fault_check();
+
 }  // namespace cd

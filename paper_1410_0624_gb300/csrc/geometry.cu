@@ -22,6 +22,7 @@
 #include <string.h>
 
 #include "common.cuh"
+#include "geom_device.cuh"
 
 namespace cd {
 
@@ -107,30 +108,6 @@ int make_directions(int scheme, int p0, int p1, const double *custom, int n_cust
 
 namespace {
 
-// Length of {p + s u : s >= 0} inside the cube [lo, lo + 1]^3 (slab method).
-__device__ double path_in_cube(const double *p, const double *u, double lx, double ly, double lz)
-{
-    const double lo[3] = {lx, ly, lz};
-    double enter = 0.0, leave = 1e300;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (u[a] == 0.0) {
-            if (p[a] < lo[a] || p[a] > lo[a] + 1.0) return 0.0;
-        } else {
-            double s0 = (lo[a] - p[a]) / u[a];
-            double s1 = (lo[a] + 1.0 - p[a]) / u[a];
-            if (s0 > s1) {
-                const double x = s0;
-                s0 = s1;
-                s1 = x;
-            }
-            enter = fmax(enter, s0);
-            leave = fmin(leave, s1);
-        }
-    }
-    return leave > enter ? leave - enter : 0.0;
-}
-
 __global__ void shell_tables(int t, int nd, const double *__restrict__ dirs, int2 *__restrict__ tab,
                              int *__restrict__ cmax, int *__restrict__ max_count)
 {
@@ -139,26 +116,12 @@ __global__ void shell_tables(int t, int nd, const double *__restrict__ dirs, int
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncfg * nd; e += gridDim.x * blockDim.x) {
         const int cfg = e / nd, d = e - cfg * nd;
         const double u[3] = {dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2]};
-        double p[3];
-        int top[3];
-        for (int a = 0; a < 3; ++a) {
-            double x = 2.0;
-            for (int j = 0; j < t; ++j) {
-                const int o = (cfg >> (3 * (t - 1 - j))) & 7;
-                x += (double)((o >> a) & 1) * ldexp(1.0, -j);
-            }
-            p[a] = x + ldexp(1.0, -t);
-            top[a] = 2 + (((cfg >> (3 * (t - 1))) >> a) & 1);
-        }
         int2 *row = tab + (size_t)cfg * CD_MAXE * nd + d;
         int n = 0;
         for (int s = 0; s < CD_STENCIL; ++s) {
-            const int a = s % 6, b = (s / 6) % 6, c = s / 36;
-            const bool inner = (t == 1) ? (a == top[0] && b == top[1] && c == top[2])
-                                        : (abs(a - top[0]) <= 1 && abs(b - top[1]) <= 1 && abs(c - top[2]) <= 1);
-            if (inner) continue;
-            const double len = path_in_cube(p, u, a, b, c);
+            const double len = shell_weight(t, cfg, s, u);
             if (len > 0.0) {
+                const int a = s % 6, b = (s / 6) % 6, c = s / 36;
                 if (n < CD_MAXE) row[(size_t)n * nd] = make_int2(a + R * (b + R * c), __float_as_int((float)len));
                 ++n;
             }
