@@ -5,9 +5,10 @@
 //   1. k = 3 .. L-2: S_k[c] = S_{k-1}[parent c] + far shell of level k-2 seen
 //      from the centre of c (table 3).  S_k holds, for every level-k cell, the
 //      summed shells l <= k-2 it shares with all its descendants' octs.
-//   2. k = L-1 (the octs): E[c] = S_{L-2}[parent c] + shells L-3 (table 3),
-//      L-2 (table 2) and L-1 (table 1), all seen from the oct centre.
-//   3. leaves: N_H = E[oct] + internal + local, then A_V and the shield.
+//   2. k = L-1 (the octs): E[c] = shells L-3 (table 3), L-2 (table 2) and
+//      L-1 (table 1), all seen from the oct centre.
+//   3. leaves: N_H = E[oct] + S_{L-2}[parent oct] + internal + local, then A_V
+//      and the shield.
 // Every shell l = 1 .. L-1 enters exactly once (Eq. N_discret).
 #include <stdarg.h>
 #include <stdio.h>
@@ -320,7 +321,7 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
             a.rho[t] = tree->rho_lvl[k - t + 1];
             a.dx[t] = dx_of(tree, k - t + 1);
         }
-        a.prefix_in = (L - 2 >= 3) ? tree->ws.S[L - 2] : nullptr;
+        a.prefix_in = nullptr;   // the leaf kernel adds S_{L-2}[parent]
         a.out = tree->ws.E;
         st = use_tc(k) ? launch_ext_tc(a, tree->rho_brick, geom, s) : launch_ext_fp32(a, geom, s);
         if (st != CD_OK) return st;
@@ -333,6 +334,7 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
     b.shield_k = (float)opts.shield_k;
     b.rho_leaf = tree->rho_leaf;
     b.E = tree->ws.E;
+    b.Sp = (L - 2 >= 3) ? tree->ws.S[L - 2] : nullptr;
     b.kloc = geom->kloc;
     b.n_h = n_h;
     b.a_v = a_v;

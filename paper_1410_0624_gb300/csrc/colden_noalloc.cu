@@ -121,7 +121,7 @@ extern "C" cd_status cd_column_density_noalloc(cd_tree tree, cd_geom geom, const
             a.rho[t] = tree->rho_lvl[k - t + 1];
             a.dx[t] = dx(k - t + 1);
         }
-        a.prefix_in = (L - 2 >= 3) ? base + off[L - 2] : nullptr;
+        a.prefix_in = nullptr;   // the leaf kernel adds S_{L-2}[parent]
         a.out = base + offE;
         if ((st = launch_ext_fp32(a, geom, s)) != CD_OK) return st;
     }
@@ -133,6 +133,7 @@ extern "C" cd_status cd_column_density_noalloc(cd_tree tree, cd_geom geom, const
     b.shield_k = (float)opts.shield_k;
     b.rho_leaf = tree->rho_leaf;
     b.E = (L >= 2) ? base + offE : nullptr;
+    b.Sp = (L - 2 >= 3) ? base + off[L - 2] : nullptr;
     b.kloc = geom->kloc;
     b.n_h = n_h;
     b.a_v = a_v;

@@ -7,21 +7,25 @@
 //   A[P, (t, q, ch)] = rho_{k-t+1}(child ch of neighbour q of A_{k-t}(P))
 //   B[(t, q, ch), (o, d)] = 2^(t-1) K_t[cfg_t(P, o)][s(q, ch)][d]
 //   E[8P + o][d] = dx_k D[P, (o, d)] + S_{k-1}[P][d]
-// with q over the 27 level-(k-t) neighbours (+1 zero brick: 28 per table),
+// with q over the 27 level-(k-t) neighbours (+3 zero bricks: 30 per table),
 // ch over their 8 children and o over the children of P.  cfg_t depends on
 // the octants of P and of its parent, so the 64 classes (oct(par P), oct(P))
 // each get their own B and a tile holds 128 parents of one class.  Powers
 // of two fold dx_{k-t+1} = 2^(t-1) dx_k into B exactly.
 //
 // Densities are stored per level as BF16 "bricks" (the 8 children of one
-// coarser cell, 16 bytes), so an A row is 84 bricks and one brick is exactly
+// coarser cell, 16 bytes), so an A row is 90 bricks and one brick is exactly
 // one row of an 8x16-byte core matrix: cp.async 16-byte copies place them
-// straight into the K-major no-swizzle operand layout.  B is precomputed in
-// global memory in that layout per K-chunk, so each chunk is one bulk copy.
+// straight into the K-major no-swizzle operand layout.  A K-chunk is 6 bricks,
+// i.e. two x-runs of 3 neighbours (48 contiguous bytes each), and consecutive
+// lanes copy consecutive bricks of a row, so one warp instruction touches few
+// lines.  B is precomputed in global memory in the operand layout per K-chunk,
+// so each chunk is one bulk copy.
 //
-// CTA (256 threads): warp 0 issues the MMAs (M = 128, N = 8 nd split in n_mma
+// CTA (384 threads): warp 0 issues the MMAs (M = 128, N = 8 nd split in n_mma
 // instructions, K = 16) and owns the TMEM accumulator; warp 1 bulk-copies B;
-// warps 2-3 gather A; warps 4-7 drain TMEM (lane quarter = warp % 4) into E.
+// warps 4-7 gather A (one row each); warps 8-11 drain TMEM (lane quarter =
+// warp % 4) into E; warps 2-3 only join the final barrier.
 // A 4-stage mbarrier pipeline couples them; every wait is bounded and a
 // timeout sets a device flag instead of trapping.
 #include <algorithm>
@@ -33,41 +37,55 @@
 namespace cd {
 namespace {
 
-constexpr int kStages = 4;
-constexpr int kChunkBricks = 4;                 // K = 32 per chunk (2 MMA K-steps)
-constexpr int kBricksPerTable = 28;             // 27 neighbours + 1 zero brick
-constexpr int kChunks = 3 * kBricksPerTable / kChunkBricks;  // 21
-constexpr int kThreads = 256;
+constexpr int kStages = 3;
+constexpr int kChunkBricks = 6;                 // K = 48 per chunk (3 MMA K-steps)
+constexpr int kBricksPerTable = 30;             // 27 neighbours + 3 zero bricks
+constexpr int kChunks = 3 * kBricksPerTable / kChunkBricks;  // 15
+constexpr int kThreads = 320;                   // 10 warps
 constexpr uint32_t kMaxPolls = 1u << 26;
-constexpr uint32_t kAStageBytes = 128 * kChunkBricks * 16;   // 8 KB
+// A stage: core matrix (row group mg, brick b) at mg * kASbo + b * kALbo; the
+// 144-byte K stride puts the bricks of one row in different bank quads
+constexpr uint32_t kALbo = 144, kASbo = kChunkBricks * kALbo;
+constexpr uint32_t kAStageBytes = 16 * kASbo;                // 13.5 KB
+constexpr int kTmemCols = 256;
 
 static __device__ int g_tc_fault;
 
 struct TcArgs {
     int k;                       // receiving level (>= 4)
-    int nd, N, n_mma, Nh;        // directions, N = 8 nd, MMAs per K-step, columns per MMA
-    int c0, c1;                  // chunk range (tables 1..3 -> 0..21, table 3 only -> 14..21)
+    int nd, N, Nt;               // directions, N = 8 nd, Nt = N / 2 columns per tile (children 4h .. 4h+3)
+    int c0, c1;                  // chunk range (tables 1..3 -> 0..15, table 3 only -> 10..15)
     const __nv_bfloat16 *brick[4];   // brick arrays of levels k, k-1, k-2 (tables 1, 2, 3)
-    const __nv_bfloat16 *B;      // [64 class][21 chunk][N/8][4][8][8]
-    const float *prefix_in;      // S_{k-1} [8^(k-1)][nd] or NULL
-    float *out;                  // [8^k][nd]
+    const __nv_bfloat16 *B;      // [64 class][15 chunk][N/8][6][8][8]
+    float *out;                  // [8^k][nd]: the shell sum of this launch (no far-field prefix)
     float dx_k;
     int64_t nG;                  // 8^(k-3)
-    int64_t ntiles;              // 64 * ceil(nG / 128)
+    int64_t ntiles;              // 2 * 64 * ceil(nG / 128)
 };
+
+// tile -> (row block gb, class cls, half h); the two halves of one row block
+// are consecutive tiles
+__device__ __forceinline__ void tile_coords(int64_t tile, int64_t &gb, int &cls, int &h)
+{
+    h = (int)(tile & 1);
+    cls = (int)((tile >> 1) & 63);
+    gb = tile >> 7;
+}
 
 __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity)
 {
     return mbar_wait_bounded(bar, parity, kMaxPolls);
 }
 
-__global__ void __launch_bounds__(kThreads, 1) shell_sum_tc(TcArgs P)
+__global__ void __launch_bounds__(kThreads, 2) shell_sum_tc(TcArgs P)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    const uint32_t bstage = (uint32_t)P.N * kChunkBricks * 16;       // N/8 groups x 4 bricks x 128 B
+    const uint32_t bstage = (uint32_t)P.Nt * kChunkBricks * 16;      // Nt/8 groups x 6 bricks x 128 B
+    const uint32_t bhalf = (uint32_t)P.N * kChunkBricks * 16;        // one chunk of the global B
     unsigned char *sA = smem;                                        // [kStages][8 KB]
     unsigned char *sB = smem + kStages * kAStageBytes;               // [kStages][bstage]
-    uint64_t *full = reinterpret_cast<uint64_t *>(sB + kStages * bstage);
+    float *sT = reinterpret_cast<float *>(sB + kStages * bstage);    // [4 warps][32][33] transpose
+    uint64_t *full = reinterpret_cast<uint64_t *>(sT + 4 * 32 * 33);
     uint64_t *empty = full + kStages;
     uint64_t *acc_full = empty + kStages;
     uint64_t *acc_empty = acc_full + 1;
@@ -79,7 +97,7 @@ __global__ void __launch_bounds__(kThreads, 1) shell_sum_tc(TcArgs P)
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], 64 + 1);       // 64 gather threads + the B producer
+            mbar_init(&full[s], 128 + 1);      // 128 gather threads + the B producer
             mbar_init(&empty[s], 1);
         }
         mbar_init(acc_full, 1);
@@ -87,7 +105,7 @@ __global__ void __launch_bounds__(kThreads, 1) shell_sum_tc(TcArgs P)
         fence_mbar_init();
         s_fault = 0;
     }
-    if (warp == 0) tmem_alloc(tslot, 512);
+    if (warp == 0) tmem_alloc(tslot, kTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -97,6 +115,7 @@ __global__ void __launch_bounds__(kThreads, 1) shell_sum_tc(TcArgs P)
     if (warp == 0) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
+            const uint32_t idesc = umma_idesc_bf16(128, P.Nt);
             uint32_t q = 0;
             int u = 0;
             for (int64_t tile = blockIdx.x; tile < P.ntiles && !fault; tile += gridDim.x, ++u) {
@@ -108,15 +127,10 @@ __global__ void __launch_bounds__(kThreads, 1) shell_sum_tc(TcArgs P)
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(sA + s * kAStageBytes), b0 = smem_u32(sB + s * bstage);
 #pragma unroll
-                    for (int ks = 0; ks < kChunkBricks / 2; ++ks) {
-                        const uint64_t ad = umma_smem_desc(a0 + ks * 256, 128, kChunkBricks * 128);
-                        for (int h = 0; h < P.n_mma; ++h) {
-                            const uint64_t bd =
-                                umma_smem_desc(b0 + h * (P.Nh / 8) * (kChunkBricks * 128) + ks * 256, 128,
-                                               kChunkBricks * 128);
-                            umma_bf16(tbase + h * P.Nh, ad, bd, umma_idesc_bf16(128, P.Nh), (j > 0 || ks > 0) ? 1u : 0u);
-                        }
-                    }
+                    for (int ks = 0; ks < kChunkBricks / 2; ++ks)
+                        umma_bf16(tbase, umma_smem_desc(a0 + ks * 2 * kALbo, kALbo, kASbo),
+                                  umma_smem_desc(b0 + ks * 256, 128, kChunkBricks * 128), idesc,
+                                  (j > 0 || ks > 0) ? 1u : 0u);
                     umma_commit(&empty[s]);
                 }
                 if (fault) break;
@@ -129,37 +143,56 @@ __global__ void __launch_bounds__(kThreads, 1) shell_sum_tc(TcArgs P)
         if (lane == 0) {
             uint32_t q = 0;
             for (int64_t tile = blockIdx.x; tile < P.ntiles && !fault; tile += gridDim.x) {
-                const int cls = (int)(tile % 64);
-                const unsigned char *Bc = reinterpret_cast<const unsigned char *>(P.B) + (size_t)cls * kChunks * bstage;
+                int64_t gb;
+                int cls, h;
+                tile_coords(tile, gb, cls, h);
+                const unsigned char *Bc = reinterpret_cast<const unsigned char *>(P.B) + (size_t)cls * kChunks * bhalf +
+                                          (size_t)h * bstage;
                 for (int j = 0; j < nchunk; ++j, ++q) {
                     const int s = q % kStages;
                     if (!wait_bar(&empty[s], ((q / kStages) & 1) ^ 1)) { fault = true; break; }
                     mbar_expect_tx(&full[s], bstage);
-                    bulk_g2s(sB + s * bstage, Bc + (size_t)(P.c0 + j) * bstage, bstage, &full[s]);
+                    bulk_g2s(sB + s * bstage, Bc + (size_t)(P.c0 + j) * bhalf, bstage, &full[s]);
                 }
             }
         }
         __syncwarp();
-    } else if (warp < 4) {
-        // ---------------- A gather (64 threads, 8 bricks each per chunk) ----------------
-        const int g = tid - 64;                  // 0..63
+    } else if (warp < 6) {
+        // ---------------- A gather (128 threads, one row each) ----------------
+        // Per tile a thread keeps, for each table, a pointer to the brick of its
+        // (-1,-1,-1) neighbour and a 27-bit in-box mask; per chunk the six
+        // neighbour offsets are uniform, so each brick is an add, a bit test and
+        // one 16-byte cp.async.
+        const int m = tid - 64;
+        unsigned char *dst_row = sA + (m >> 3) * kASbo + (m & 7) * 16;
         uint32_t q = 0;
         for (int64_t tile = blockIdx.x; tile < P.ntiles && !fault; tile += gridDim.x) {
-            const int cls = (int)(tile % 64);
-            const int64_t gb = tile / 64;
-            // this thread's two rows m = g, g + 64: parent P = (G << 6) | cls
-            int64_t acx[2][3], acy[2][3], acz[2][3];   // anchors A_{k-t}(P) for t = 1..3
-            bool valid[2];
-            for (int r = 0; r < 2; ++r) {
-                const int64_t G = gb * 128 + g + 64 * r;
-                valid[r] = G < P.nG;
-                const uint64_t Pm = ((uint64_t)(valid[r] ? G : 0) << 6) | (uint64_t)cls;
-                const int64_t px = compact3(Pm), py = compact3(Pm >> 1), pz = compact3(Pm >> 2);
-                for (int t = 0; t < 3; ++t) {
-                    acx[r][t] = px >> t;
-                    acy[r][t] = py >> t;
-                    acz[r][t] = pz >> t;
+            int64_t gb;
+            int cls, h;
+            tile_coords(tile, gb, cls, h);
+            const int64_t G = gb * 128 + m;
+            const bool valid = G < P.nG;
+            const uint64_t Pm = ((uint64_t)(valid ? G : 0) << 6) | (uint64_t)cls;
+            const int px = (int)compact3(Pm), py = (int)compact3(Pm >> 1), pz = (int)compact3(Pm >> 2);
+            const __nv_bfloat16 *corner[3];
+            uint32_t mask[3];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const int n = 1 << (P.k - 1 - t);
+                const int ax = (px >> t) - 1, ay = (py >> t) - 1, az = (pz >> t) - 1;
+                corner[t] = P.brick[t + 1] + ((int64_t)((int64_t)az * n + ay) * n + ax) * 8;
+                uint32_t mx = 0, my = 0, mz = 0;
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    mx |= (uint32_t)(ax + d >= 0 && ax + d < n) << d;
+                    my |= (uint32_t)(ay + d >= 0 && ay + d < n) << d;
+                    mz |= (uint32_t)(az + d >= 0 && az + d < n) << d;
                 }
+                uint32_t mm = 0;
+#pragma unroll
+                for (int nq = 0; nq < 27; ++nq)
+                    mm |= ((mx >> (nq % 3)) & (my >> ((nq / 3) % 3)) & (mz >> (nq / 9)) & 1u) << nq;
+                mask[t] = valid ? mm : 0u;
             }
             for (int j = 0; j < nchunk; ++j, ++q) {
                 const int s = q % kStages;
@@ -167,64 +200,58 @@ __global__ void __launch_bounds__(kThreads, 1) shell_sum_tc(TcArgs P)
                 if (lane == 0) ok = wait_bar(&empty[s], ((q / kStages) & 1) ^ 1);
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) { fault = true; break; }
-                unsigned char *dst = sA + s * kAStageBytes;
-                const int c = P.c0 + j;
+                const int kb0 = (P.c0 + j) * kChunkBricks;           // uniform
+                const int t = kb0 / kBricksPerTable, nq0 = kb0 - t * kBricksPerTable;
+                const int n = 1 << (P.k - 1 - t);
+                const __nv_bfloat16 *cor = t == 0 ? corner[0] : t == 1 ? corner[1] : corner[2];
+                const uint32_t mk = t == 0 ? mask[0] : t == 1 ? mask[1] : mask[2];
+                unsigned char *dst = dst_row + s * kAStageBytes;
 #pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const int m = g + 64 * r;
-#pragma unroll
-                    for (int b = 0; b < kChunkBricks; ++b) {
-                        const int kb = c * kChunkBricks + b;             // 0..83
-                        const int t = kb / kBricksPerTable, nq = kb % kBricksPerTable;
-                        const int lvl_side_log = P.k - t - 1;            // neighbours live at level k-t-1
-                        const int64_t n = (int64_t)1 << lvl_side_log;
-                        const int64_t x = acx[r][t] + (nq % 3) - 1, y = acy[r][t] + (nq / 3) % 3 - 1,
-                                      z = acz[r][t] + nq / 9 - 1;
-                        const bool in = valid[r] && nq < 27 && x >= 0 && y >= 0 && z >= 0 && x < n && y < n && z < n;
-                        const __nv_bfloat16 *src = P.brick[t + 1] + (in ? 8 * ((z * n + y) * n + x) : 0);
-                        // core matrix (m / 8, b) of the stage, row m % 8
-                        cp_async16(dst + ((m >> 3) * kChunkBricks + b) * 128 + (m & 7) * 16, src, in ? 16u : 0u);
-                    }
+                for (int b = 0; b < kChunkBricks; ++b) {
+                    const int nq = nq0 + b;                           // uniform
+                    const int64_t off = ((int64_t)((nq / 9) * n + (nq / 3) % 3) * n + nq % 3) * 8;
+                    const bool in = nq < 27 && ((mk >> nq) & 1u);
+                    cp_async16_ca(dst + b * kALbo, in ? cor + off : P.brick[1], in ? 16u : 0u);
                 }
                 cp_async_arrive(&full[s]);
             }
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else {
-        // ---------------- epilogue: TMEM -> E ----------------
-        const int quarter = warp & 3;             // TMEM lanes 32 quarter .. +31
-        const int m = quarter * 32 + lane;
+        // ---------------- epilogue: TMEM -> E (warps 6..9, TMEM lane quarter warp % 4) ----------------
+        const int ew = warp - 6;
+        const int quarter = warp & 3;
+        float *T = sT + ew * 32 * 33;
         int u = 0;
         for (int64_t tile = blockIdx.x; tile < P.ntiles && !fault; tile += gridDim.x, ++u) {
-            const int cls = (int)(tile % 64);
-            const int64_t G = (tile / 64) * 128 + m;
-            const bool valid = G < P.nG;
-            const int64_t Pm = ((valid ? G : 0) << 6) | cls;
+            int64_t gb;
+            int cls, h;
+            tile_coords(tile, gb, cls, h);
+            const int64_t G0 = gb * 128 + quarter * 32;               // the warp's first row
+            const int nrows = (int)(P.nG - G0 < 32 ? (P.nG - G0 > 0 ? P.nG - G0 : 0) : 32);
+            // row r of the warp is parent P = ((G0 + r) << 6) | cls; its columns of
+            // this tile are the contiguous run out[(8P + 4h) nd .. + Nt)
+            float *row0 = P.out + (size_t)((((G0 << 6) | cls) * 8) + 4 * h) * P.nd;
+            const size_t rstride = (size_t)64 * 8 * P.nd;
             bool ok = true;
             if (lane == 0) ok = wait_bar(acc_full, u & 1);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) { fault = true; break; }
             tc_fence_after();
-            float *orow = P.out + (size_t)Pm * 8 * P.nd;
-            const float *pre = P.prefix_in ? P.prefix_in + (size_t)Pm * P.nd : nullptr;
-            int o_d = 0;                          // running direction index of column c
-            for (int c = 0; c < P.N; c += 32) {
+            for (int c = 0; c < P.Nt; c += 32) {
                 uint32_t v[32];
                 tmem_ld32(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c, v);
                 tmem_ld_wait();
-                if (valid) {
-                    float o[32];
-                    int d = o_d;
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        o[i] = P.dx_k * __uint_as_float(v[i]) + (pre ? pre[d] : 0.f);
-                        d = (d + 1 == P.nd) ? 0 : d + 1;
-                    }
-#pragma unroll
-                    for (int i = 0; i < 32; i += 4)
-                        *reinterpret_cast<float4 *>(orow + c + i) = make_float4(o[i], o[i + 1], o[i + 2], o[i + 3]);
+                for (int i = 0; i < 32; ++i) T[lane * 33 + i] = __uint_as_float(v[i]);
+                __syncwarp();
+                const int col = c + lane;
+                if (col < P.Nt) {
+                    float *o = row0 + col;
+#pragma unroll 4
+                    for (int r = 0; r < nrows; ++r, o += rstride) *o = P.dx_k * T[r * 33 + lane];
                 }
-                o_d = (o_d + 32) % P.nd;
+                __syncwarp();
             }
             tc_fence_before();
             __syncwarp();
@@ -247,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 1) shell_sum_tc(TcArgs P)
         }
         __syncwarp();
         tc_fence_after();
-        tmem_dealloc(tbase, 512);
+        tmem_dealloc(tbase, kTmemCols);
     }
 }
 
@@ -284,6 +311,22 @@ __global__ void build_b(int nd, const double *__restrict__ dirs, __nv_bfloat16 *
     }
 }
 
+// out[c][d] += parent[c >> 3][d] over n = 8^k nd elements (nd % 4 == 0).
+__global__ void add_parent_rows(float *__restrict__ out, const float *__restrict__ parent, int nd, int64_t n)
+{
+    for (int64_t e = 4 * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); e < n; e += 4 * (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / nd;
+        const int d = (int)(e - c * nd);
+        float4 v = *reinterpret_cast<float4 *>(out + e);
+        const float4 p = *reinterpret_cast<const float4 *>(parent + (c >> 3) * nd + d);
+        v.x += p.x;
+        v.y += p.y;
+        v.z += p.z;
+        v.w += p.w;
+        *reinterpret_cast<float4 *>(out + e) = v;
+    }
+}
+
 int num_sms()
 {
     int dev = 0, n = 0;
@@ -294,12 +337,13 @@ int num_sms()
 
 }  // namespace
 
-// N = 8 nd accumulator columns: at most 512 (TMEM), a multiple of 32 (the
-// epilogue drains 32 columns per load) and at most two MMAs of N/2 <= 256.
+// A tile holds half the children of its parents: Nt = 4 nd accumulator
+// columns, one MMA of N = Nt (a multiple of 16, at most 256 = the TMEM
+// columns of one of the two CTAs an SM runs).
 bool tc_supported(int nd)
 {
-    const int N = 8 * nd;
-    return N <= 512 && N % 32 == 0;
+    const int Nt = 4 * nd;
+    return Nt <= 256 && Nt % 16 == 0;
 }
 
 cd_status build_tc_tables(cd_geom g, cudaStream_t s)
@@ -331,8 +375,7 @@ cd_status launch_ext_tc(const ExtLaunch &a, const __nv_bfloat16 *const *brick, c
     P.k = a.k;
     P.nd = a.nd;
     P.N = 8 * a.nd;
-    P.n_mma = P.N > 256 ? 2 : 1;
-    P.Nh = P.N / P.n_mma;
+    P.Nt = 4 * a.nd;
     const bool all3 = (a.tmask & 7) == 7;
     if (!all3 && a.tmask != 4) {
         set_error("tensor-core shell serves tables {1,2,3} or {3}");
@@ -345,18 +388,26 @@ cd_status launch_ext_tc(const ExtLaunch &a, const __nv_bfloat16 *const *brick, c
     P.brick[2] = brick[a.k - 1];
     P.brick[3] = brick[a.k - 2];
     P.B = g->wb;
-    P.prefix_in = a.prefix_in;
     P.out = a.out;
     P.dx_k = a.dx[1] > 0.f ? a.dx[1] : a.dx[3] * 0.25f;
     P.nG = (int64_t)1 << (3 * (a.k - 3));
-    P.ntiles = 64 * ((P.nG + 127) / 128);
-    const size_t bstage = (size_t)P.N * kChunkBricks * 16;
-    const size_t smem = kStages * (kAStageBytes + bstage) + (2 * kStages + 2) * 8 + 16;
+    P.ntiles = 2 * 64 * ((P.nG + 127) / 128);
+    const size_t bstage = (size_t)P.Nt * kChunkBricks * 16;
+    const size_t smem = kStages * (kAStageBytes + bstage) + sizeof(float) * 4 * 32 * 33 + (2 * kStages + 2) * 8 + 16;
     CD_CUDA(cudaFuncSetAttribute(shell_sum_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int64_t grid = std::min<int64_t>(P.ntiles, num_sms());
-    LaunchScope ls(CD_K_SHELL, s);
-    shell_sum_tc<<<(unsigned)grid, kThreads, smem, s>>>(P);
+    const int64_t grid = std::min<int64_t>(P.ntiles, 2 * (int64_t)num_sms());
+    {
+        LaunchScope ls(CD_K_SHELL, s);
+        shell_sum_tc<<<(unsigned)grid, kThreads, smem, s>>>(P);
+    }
     CD_CHECK_LAUNCH();
+    if (a.prefix_in) {
+        // S_k[c] += S_{k-1}[parent c]
+        const int64_t n = ((int64_t)1 << (3 * a.k)) * a.nd;
+        LaunchScope ls(CD_K_SHELL, s);
+        add_parent_rows<<<(unsigned)std::min<int64_t>((n / 4 + 255) / 256, 152 * 16), 256, 0, s>>>(a.out, a.prefix_in, a.nd, n);
+        CD_CHECK_LAUNCH();
+    }
     return CD_OK;
 }
 

@@ -158,7 +158,8 @@ struct LeafLaunch {
     float dx_leaf;
     float av_per_nh, shield_k;
     const float *rho_leaf;    // Morton, 8 per oct
-    const float *E;           // [n_oct][nd] or NULL
+    const float *E;           // [n_oct][nd] or NULL: shells l0-3 .. l0-1 of every oct
+    const float *Sp;          // [n_oct / 8][nd] or NULL: far shells shared by the 8 octs of a parent
     const float *kloc;        // [8][8][nd]
     float *n_h, *a_v, *shield;
 };

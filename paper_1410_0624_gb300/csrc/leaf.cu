@@ -1,13 +1,13 @@
 // Per-leaf combine and epilogue (§3.2 internal + local contributions; Eqs.
 // eq_chi / chi_discret for the direction average):
-//   N_H[t][d] = E[oct][d] + sum_s rho_leaf[oct][s] dx_L Kloc[t][s][d]
+//   N_H[t][d] = E[oct][d] + Sp[oct / 8][d] + sum_s rho_leaf[oct][s] dx_L Kloc[t][s][d]
 //   A_V = N_H av_per_nh,   shield[t] = (1/nd) sum_d exp(-k A_V)
 // This kernel writes the N_H array, the dominant HBM traffic of the path
 // (4 bytes per cell-direction), so it is built as a streaming pipeline:
 //
 //   - persistent CTAs, each walking batches of B consecutive octs (Morton
 //     order, so every batch is one contiguous span of E, rho and N_H);
-//   - E and rho of the next batch arrive by bulk asynchronous copies (TMA,
+//   - E, Sp and rho of the next batch arrive by bulk asynchronous copies (TMA,
 //     cp.async.bulk) into a double-buffered shared-memory stage, completed on
 //     an mbarrier, while the current batch is computed;
 //   - every thread owns one fixed (child t, four directions) slot of the oct,
@@ -37,8 +37,9 @@ struct LeafTmaArgs {
     LeafLaunch a;
     int G;           // thread groups; one group = 2 nd threads = one oct at a time
     int B;           // octs per batch
+    int prows;       // parent rows a batch can touch: B / 8 + 2
     int64_t nbatch;
-    float c_exp;     // exp argument per unit N_H: -shield_k * av_per_nh
+    float c_exp2;    // base-2 exponent per unit N_H: -shield_k * av_per_nh * log2(e)
     float inv_nd;
 };
 
@@ -49,34 +50,42 @@ struct LeafTmaArgs {
 // partials of batch i are summed in a fixed order while batch i+1 is computed
 // and their store trails the N_H store by one batch, so results are bitwise
 // reproducible with two barriers per batch.
-template <int W>
-__global__ void __launch_bounds__(384, 3) leaf_tma(LeafTmaArgs P)
+// ND > 0 fixes the direction count at compile time (every offset folds to an
+// immediate); ND = 0 reads it from the arguments.
+template <int ND, int W>
+__global__ void __launch_bounds__(384, 2) leaf_tma(LeafTmaArgs P)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int nd = P.a.nd, B = P.B, q4 = nd >> 2, slots = 2 * nd, pw = slots / W, lw = q4 / W;
+    constexpr int kG = ND ? (384 / (2 * ND) > 1 ? 384 / (2 * ND) : 1) : 0;
+    const int nd = ND ? ND : P.a.nd;
+    const int G = ND ? kG : P.G;
+    const int B = ND ? 4 * kG : P.B;
+    const int prows = ND ? (4 * kG) / 8 + 2 : P.prows;
+    const int q4 = nd >> 2, slots = 2 * nd, pw = slots / W, lw = q4 / W;
     const bool want_nh = P.a.n_h != nullptr, want_sh = P.a.shield != nullptr;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     float *Eb = reinterpret_cast<float *>(smem + 128);      // [kLoadStages][B nd]
     float *Rb = Eb + kLoadStages * B * nd;                  // [kLoadStages][B 8]
-    float *Sb = Rb + kLoadStages * B * 8;                   // [3][B 8]
+    float *Pb = Rb + kLoadStages * B * 8;                   // [kLoadStages][(B/8 + 2) nd] parent rows
+    float *Sb = Pb + kLoadStages * prows * nd;              // [3][B 8]
     float *part = Sb + 3 * B * 8;                           // [2][B][slots / W]
     float *Ob = part + 2 * B * pw;                          // [2][B 8 nd]
 
     const int tid = threadIdx.x;
     const int g = tid / slots, r = tid - g * slots;
     const int t = r / q4, d0 = 4 * (r - t * q4);
-    float2 K2[8][2];   // dx_L * Kloc[t][s][d0 .. d0+3] as two pairs
+    // dx_L * Kloc[t][s][d0 + i] for sibling pairs j = (2j, 2j+1) and directions i
+    float2 KP[4][4];
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        const float *k = P.a.kloc + (t * 8 + s) * nd + d0;
-        K2[s][0] = make_float2(P.a.dx_leaf * k[0], P.a.dx_leaf * k[1]);
-        K2[s][1] = make_float2(P.a.dx_leaf * k[2], P.a.dx_leaf * k[3]);
-    }
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            KP[j][i] = make_float2(P.a.dx_leaf * P.a.kloc[(t * 8 + 2 * j) * nd + d0 + i],
+                                   P.a.dx_leaf * P.a.kloc[(t * 8 + 2 * j + 1) * nd + d0 + i]);
 
     // this thread's offsets in the stages (oct g of the batch) and the strides
     // to its next octs g + G, g + 2G, g + 3G (B = 4G)
-    const int G = P.G;
-    const bool has_E = P.a.E != nullptr, lead = (r % W) == 0;
+    const bool has_E = P.a.E != nullptr, has_Sp = P.a.Sp != nullptr;
     const int eoff = g * nd + d0, roff = g * 8, ooff = (g * 8 + t) * nd + d0, poff = g * pw + r / W;
     const int sE = G * nd, sR = G * 8, sO = G * 8 * nd, sP = G * pw;
 
@@ -94,8 +103,11 @@ __global__ void __launch_bounds__(384, 3) leaf_tma(LeafTmaArgs P)
         const int64_t o0 = batch_o0(it);
         const int nb = batch_nb(it);
         const uint32_t eb = P.a.E ? (uint32_t)nb * nd * 4 : 0u;
-        mbar_expect_tx(&bar[st], eb + (uint32_t)nb * 32);
+        const int64_t p0 = o0 >> 3;
+        const uint32_t pb = P.a.Sp ? (uint32_t)(((o0 + nb - 1) >> 3) - p0 + 1) * nd * 4 : 0u;
+        mbar_expect_tx(&bar[st], eb + pb + (uint32_t)nb * 32);
         if (P.a.E) bulk_g2s(Eb + st * B * nd, P.a.E + o0 * nd, eb, &bar[st]);
+        if (P.a.Sp) bulk_g2s(Pb + st * prows * nd, P.a.Sp + p0 * nd, pb, &bar[st]);
         bulk_g2s(Rb + st * B * 8, P.a.rho_leaf + o0 * 8, (uint32_t)nb * 32, &bar[st]);
     };
     // screening factor of batch `it` from its partials, in a fixed order
@@ -136,51 +148,62 @@ __global__ void __launch_bounds__(384, 3) leaf_tma(LeafTmaArgs P)
 
         const int64_t o0 = batch_o0(it);
         const int nb = batch_nb(it);
+        // 32-bit shared-memory bases of this thread's slot in every stage
         const float *E = Eb + ls * B * nd + eoff;
+        const float *Spr = Pb + ls * prows * nd + d0;
         const float *R = Rb + ls * B * 8 + roff;
         float *O = Ob + os * B * 8 * nd + ooff;
         float *pp = part + (it & 1) * B * pw + poff;
+        const int par0 = (int)(o0 & 7);           // parent row of oct b: (par0 + b) >> 3
         float *AV = P.a.a_v ? P.a.a_v + o0 * 8 * nd + ooff : nullptr;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const int b = g + k * G;
-            const bool live = b < nb;
-            float n[4] = {0.f, 0.f, 0.f, 0.f};
+            const bool live = nb == B || b < nb;
+            float2 n01 = make_float2(0.f, 0.f), n23 = make_float2(0.f, 0.f);
             if (live) {
                 if (has_E) {
                     const float4 e4 = *reinterpret_cast<const float4 *>(E + k * sE);
-                    n[0] = e4.x;
-                    n[1] = e4.y;
-                    n[2] = e4.z;
-                    n[3] = e4.w;
+                    n01 = make_float2(e4.x, e4.y);
+                    n23 = make_float2(e4.z, e4.w);
+                }
+                if (has_Sp) {
+                    const float4 p4 = *reinterpret_cast<const float4 *>(Spr + ((par0 + b) >> 3) * nd);
+                    n01 = __fadd2_rn(n01, make_float2(p4.x, p4.y));
+                    n23 = __fadd2_rn(n23, make_float2(p4.z, p4.w));
                 }
                 const float4 r0 = *reinterpret_cast<const float4 *>(R + k * sR);
                 const float4 r1 = *reinterpret_cast<const float4 *>(R + k * sR + 4);
-                const float rs[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-                // packed FP32x2 FMAs: two directions per instruction, each rounded as fmaf
-                float2 n01 = make_float2(n[0], n[1]), n23 = make_float2(n[2], n[3]);
+                // packed FP32x2 FMAs over sibling pairs (s, s+1): acc[i] holds the
+                // even- and odd-sibling partial sums of direction d0 + i
+                const float2 rp[4] = {make_float2(r0.x, r0.y), make_float2(r0.z, r0.w), make_float2(r1.x, r1.y),
+                                      make_float2(r1.z, r1.w)};
+                float2 acc[4];
 #pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    const float2 rr = make_float2(rs[s], rs[s]);
-                    n01 = __ffma2_rn(rr, K2[s][0], n01);
-                    n23 = __ffma2_rn(rr, K2[s][1], n23);
+                for (int i = 0; i < 4; ++i) {
+                    acc[i] = __fmul2_rn(rp[0], KP[0][i]);
+#pragma unroll
+                    for (int j = 1; j < 4; ++j) acc[i] = __ffma2_rn(rp[j], KP[j][i], acc[i]);
                 }
-                n[0] = n01.x;
-                n[1] = n01.y;
-                n[2] = n23.x;
-                n[3] = n23.y;
-                if (want_nh) *reinterpret_cast<float4 *>(O + k * sO) = make_float4(n[0], n[1], n[2], n[3]);
+                n01.x += acc[0].x + acc[0].y;
+                n01.y += acc[1].x + acc[1].y;
+                n23.x += acc[2].x + acc[2].y;
+                n23.y += acc[3].x + acc[3].y;
+                if (want_nh) *reinterpret_cast<float4 *>(O + k * sO) = make_float4(n01.x, n01.y, n23.x, n23.y);
                 if (AV) {
-                    const float a = P.a.av_per_nh;
-                    *reinterpret_cast<float4 *>(AV + k * sO) = make_float4(n[0] * a, n[1] * a, n[2] * a, n[3] * a);
+                    const float2 a2 = make_float2(P.a.av_per_nh, P.a.av_per_nh);
+                    const float2 x = __fmul2_rn(n01, a2), y = __fmul2_rn(n23, a2);
+                    *reinterpret_cast<float4 *>(AV + k * sO) = make_float4(x.x, x.y, y.x, y.y);
                 }
             }
             if (want_sh) {
-                float e = (__expf(P.c_exp * n[0]) + __expf(P.c_exp * n[1])) +
-                          (__expf(P.c_exp * n[2]) + __expf(P.c_exp * n[3]));
+                // exp(-k A_V) = 2^(c2 N_H), c2 = -k av log2(e) precomputed on the host
+                const float2 c2 = make_float2(P.c_exp2, P.c_exp2);
+                const float2 a = __fmul2_rn(c2, n01), bb = __fmul2_rn(c2, n23);
+                float e = (exp2f(a.x) + exp2f(a.y)) + (exp2f(bb.x) + exp2f(bb.y));
 #pragma unroll
                 for (int w = 1; w < W; w <<= 1) e += __shfl_xor_sync(0xffffffffu, e, w);
-                if (live && lead) pp[k * sP] = e;
+                pp[k * sP] = e;
             }
         }
         fence_proxy_async_smem();
@@ -237,6 +260,7 @@ __global__ void __launch_bounds__(256) leaf_generic(LeafLaunch P, float c_exp, f
         float acc = 0.f;
         for (int d = 0; d < nd; ++d) {
             float n = P.E ? P.E[oct * nd + d] : 0.f;
+            if (P.Sp) n += P.Sp[(oct >> 3) * nd + d];
 #pragma unroll
             for (int s = 0; s < 8; ++s) n = fmaf(rs[s], s_k[(s * nd + d) * 8 + t], n);
             if (P.n_h) P.n_h[leaf * nd + d] = n;
@@ -277,20 +301,20 @@ cd_status launch_leaf(const LeafLaunch &a, cudaStream_t s)
     const float c_exp = -a.shield_k * a.av_per_nh;
     const float inv_nd = 1.0f / (float)nd;
     const bool tma = (nd % 4 == 0) && 2 * nd <= 384 && aligned16(a.n_h) && aligned16(a.a_v) &&
-                     aligned16(a.shield) && aligned16(a.E) && aligned16(a.rho_leaf);
+                     aligned16(a.shield) && aligned16(a.E) && aligned16(a.Sp) && aligned16(a.rho_leaf);
     if (tma) {
-        const int q4 = nd / 4;
-        const int W = (q4 % 4 == 0) ? 4 : (q4 % 2 == 0) ? 2 : 1;
-        auto kern = W == 4 ? leaf_tma<4> : W == 2 ? leaf_tma<2> : leaf_tma<1>;
+        const int W = 1;
+        auto kern = nd == 48 ? leaf_tma<48, 1> : nd == 12 ? leaf_tma<12, 1> : leaf_tma<0, 1>;
         LeafTmaArgs P;
         P.a = a;
         P.G = std::max(1, 384 / (2 * nd));
         P.B = 4 * P.G;
+        P.prows = P.B / 8 + 2;
         P.nbatch = (a.n_oct + P.B - 1) / P.B;
-        P.c_exp = c_exp;
+        P.c_exp2 = (float)(-(double)a.shield_k * (double)a.av_per_nh * 1.4426950408889634);
         P.inv_nd = inv_nd;
         const int threads = P.G * 2 * nd;
-        const size_t smem = 128 + sizeof(float) * ((size_t)kLoadStages * P.B * (nd + 8) + 3 * P.B * 8 +
+        const size_t smem = 128 + sizeof(float) * ((size_t)kLoadStages * (P.B * (nd + 8) + (size_t)P.prows * nd) + 3 * P.B * 8 +
                                                    (size_t)2 * P.B * (2 * nd / W) +
                                                    (a.n_h ? (size_t)2 * P.B * 8 * nd : 0));
         CD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

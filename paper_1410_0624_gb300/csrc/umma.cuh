@@ -98,6 +98,14 @@ __device__ __forceinline__ void cp_async16(void *dst_smem, const void *src, uint
                  : "memory");
 }
 
+// Same, cached in L1 (bricks shared by neighbouring rows hit there).
+__device__ __forceinline__ void cp_async16_ca(void *dst_smem, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst_smem)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+
 // Arrives on the mbarrier (without raising its expected count) once every
 // cp.async this thread issued before has landed.
 __device__ __forceinline__ void cp_async_arrive(uint64_t *bar)
