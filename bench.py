@@ -10,7 +10,10 @@ N_H and shield written).  Geometry tables are built once beforehand, as the
 precalculation module does (§3.3).
 
 Metric: cell-directions/s = n_leaf * n_dir / step time (CUDA events on the
-launching stream, L2 flushed between steps, max over ranks).  With --gpus N
+launching stream, L2 flushed between steps, max over ranks).  The headline
+form is the BF16 tensor-core contraction; the same line reports the FP32
+plain form ("compare"), the speed-up, and both forms' errors against the
+FP64 oracle on a seeded leaf sample.  With --gpus N
 every rank runs an independent replica of the workload (replicas only; the
 value is the sum over ranks).
 
@@ -114,6 +117,30 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+KERNEL_SOURCES = {"leaf": "leaf.cu", "shell": "colden_tc.cu", "restrict": "tree.cu"}
+
+
+def _source_hash(name):
+    import hashlib
+    path = os.path.join(ROOT, "paper_1410_0624_gb300", "csrc", name)
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_traffic(kind, L, nd):
+    """DRAM bytes per launch of a kernel from the committed ncu summary
+    (profiles/traffic.json), or None when the kernel source changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+        e = tr.get("%s/L%d/nd%d" % (kind, L, nd))
+        if e and e.get("source_sha256_16") == _source_hash(KERNEL_SOURCES[kind]):
+            return e["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
 def make_workload(args):
     from paper_1410_0624_gb300 import synth
     n = 1 << args.level
@@ -135,7 +162,7 @@ def _morton(ijk):
     return m
 
 
-def oracle_sample(rho, box, L, nside, target_s, min_leaves=16, max_leaves=20000):
+def oracle_sample(rho, box, L, nside, target_s, min_leaves=16, max_leaves=400000):
     """Times the FP64 oracle on a seeded leaf sample sized for ~target_s seconds.
     Returns (cell-dirs/s, n_leaves, seconds, ijk, N_ref)."""
     import oracle
@@ -185,6 +212,43 @@ def run_reference(args):
     return 0
 
 
+def _time_steps(step, flush, stream, steps):
+    """Mean device time of `steps` calls of step(), L2 flushed before each."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+
+def _kernel_breakdown(colden, step, flush, steps):
+    """Per-kind launches and device ms per step (events on the launching stream)."""
+    import torch
+    colden.stats_reset(timing=True)
+    for _ in range(steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    out = {}
+    for k, name in enumerate(["restrict", "shell", "leaf", "other"]):
+        n, kms = colden.stats_get(k)
+        out[name] = {"launches_per_step": n / steps, "ms_per_step": kms / steps}
+    colden.stats_reset(timing=False)
+    return out
+
+
+def _errors(got_nh, got_sh, ref):
+    import oracle
+    rel = np.abs(got_nh - ref) / ref
+    return {"n_h_rel_max": float(rel.max()), "n_h_rel_p99": float(np.percentile(rel, 99)),
+            "a_v_abs_max": float((np.abs(got_nh - ref) / 1.87e21).max()),
+            "shield_abs_max": float(np.max(np.abs(got_sh - oracle.shield(ref)))), "leaves_checked": int(len(ref))}
+
+
 def run_ours(args):
     import torch
     from paper_1410_0624_gb300 import colden
@@ -196,7 +260,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     colden.load()
-    precision = {"fp32": colden.FP32, "bf16": colden.BF16}[args.precision]
+    forms = {"fp32": colden.FP32, "bf16": colden.BF16}
 
     rho_np, box, gen_s = make_workload(args)
     L = args.level
@@ -211,66 +275,78 @@ def run_ours(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step():
-        colden.tree_update(tree, rho, stream=stream)
-        colden.column_density(tree, geom, n_h=n_h, shield=sh, precision=precision, stream=stream)
+    def make_step(prec):
+        def step():
+            colden.tree_update(tree, rho, stream=stream)
+            colden.column_density(tree, geom, n_h=n_h, shield=sh, precision=forms[prec], stream=stream)
+        return step
 
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- the FP64 oracle on a seeded leaf sample: CPU baseline and reference values ----
+    cpu = sample = None
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        rate, n, dt, ijk, ref = oracle_sample(rho_np, box, L, args.nside, args.cpu_seconds)
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d seeded random leaves x %d dirs (%.1f s)" % (n, nd, dt)}
+        sample = (torch.from_numpy(_morton(ijk)).to(dev), ref)
+
+    def score():
+        if sample is None:
+            return None
+        rows, ref = sample
+        return _errors(n_h.reshape(-1, nd)[rows].double().cpu().numpy(), sh[rows].double().cpu().numpy(), ref)
+
+    # ---- the headline form: warm-up, timed steps with clocks sampled ----
+    step = make_step(args.precision)
     for _ in range(args.warmup):
         flush.zero_()
         step()
     torch.cuda.synchronize()
-
     clocks = ClockSampler(local)
     colden.stats_reset(timing=False)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    for a, b in ev:
-        flush.zero_()
-        a.record(stream)
-        step()
-        b.record(stream)
-    torch.cuda.synchronize()
+    ms = _time_steps(step, flush, stream, args.steps)
     clk = clocks.stop()
-    if dist:
-        dist.barrier()
-    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     launches = sum(colden.stats_get(k)[0] for k in range(4))
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        dist.barrier()
+    ms = max_over_ranks(ms)
     value = n_leaf * nd * world / (ms / 1e3)
+    kern = _kernel_breakdown(colden, step, flush, args.steps)
+    err = score()
 
-    # per-kernel device times (separate pass, events on the launching stream)
-    colden.stats_reset(timing=True)
-    for _ in range(args.steps):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
-    kern = {}
-    for k, name in enumerate(["restrict", "shell", "leaf", "other"]):
-        n, kms = colden.stats_get(k)
-        kern[name] = {"launches_per_step": n / args.steps, "ms_per_step": kms / args.steps}
-    colden.stats_reset(timing=False)
+    # ---- dominant kernel roofline (HBM: the algorithmic bytes of the path) ----
     dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
     dom_ms = kern[dom]["ms_per_step"] / max(kern[dom]["launches_per_step"], 1)
     peak, peak_kind = _peaks()
     bpu = algo_bytes_per_cell_dir(nd)
     achieved = bpu * n_leaf * nd / (dom_ms / 1e3) / 1e9
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            tr = json.load(f)
-        key = "%s/%s/L%d/nd%d" % (args.precision, dom, L, nd)
-        traffic = tr.get(key)
-    except Exception:
-        pass
 
-    # e2e: host density in, host N_H + shield out, through the public API
+    # ---- the other form (FP32 plain vs BF16 tensor cores), same workload ----
+    other = None
+    other_name = "fp32" if args.precision == "bf16" else "bf16"
+    if not args.no_compare:
+        ostep = make_step(other_name)
+        for _ in range(args.warmup):
+            flush.zero_()
+            ostep()
+        torch.cuda.synchronize()
+        oms = max_over_ranks(_time_steps(ostep, flush, stream, args.steps))
+        other = {"precision": other_name, "value": n_leaf * nd * world / (oms / 1e3), "ms_per_step": oms,
+                 "kernels": _kernel_breakdown(colden, ostep, flush, args.steps), "error_vs_oracle": score()}
+
+    # ---- e2e: host density in, host N_H + shield out, through the public API ----
     e2e = None
     if args.e2e_steps > 0:
         h_rho = torch.from_numpy(rho_np.reshape(-1)).pin_memory()
@@ -284,39 +360,16 @@ def run_ours(args):
             a.record(stream)
             d_rho.copy_(h_rho, non_blocking=True)
             colden.tree_update(tree, d_rho, stream=stream)
-            colden.column_density(tree, geom, n_h=n_h, shield=sh, precision=precision, stream=stream)
+            colden.column_density(tree, geom, n_h=n_h, shield=sh, precision=forms[args.precision], stream=stream)
             h_nh.copy_(n_h, non_blocking=True)
             h_sh.copy_(sh, non_blocking=True)
             b.record(stream)
             torch.cuda.synchronize()
             if s > 0:
                 times.append(a.elapsed_time(b))
-        e_ms = float(np.mean(times))
-        if dist:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = max_over_ranks(float(np.mean(times)))
         e2e = {"value": n_leaf * nd * world / (e_ms / 1e3), "unit": UNIT, "ms_per_step": e_ms,
                "h2d_bytes_per_step": 4 * n_leaf, "d2h_bytes_per_step": 4 * n_leaf * nd + 4 * n_leaf}
-
-    # accuracy at a seeded leaf sample and the CPU oracle baseline (rank 0, N = 1)
-    cpu = None
-    err = None
-    if rank == 0 and world == 1 and args.cpu_seconds > 0:
-        rate, n, dt, ijk, ref = oracle_sample(rho_np, box, L, args.nside, args.cpu_seconds)
-        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "%d seeded random leaves x %d dirs (%.1f s)" % (n, nd, dt)}
-        rows = _morton(ijk)
-        got = n_h.reshape(-1, nd)[torch.from_numpy(rows).to(dev)].double().cpu().numpy()
-        rel = np.abs(got - ref) / ref
-        av_abs = np.abs(got - ref) / 1.87e21
-        import oracle
-        err = {"n_h_rel_max": float(rel.max()), "n_h_rel_p99": float(np.percentile(rel, 99)),
-               "a_v_abs_max": float(av_abs.max()),
-               "shield_abs_max": float(np.max(np.abs(sh[torch.from_numpy(rows).to(dev)].double().cpu().numpy()
-                                                      - oracle.shield(ref)))),
-               "leaves_checked": int(n)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -331,12 +384,13 @@ def run_ours(args):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": traffic, "kernel": dom,
-                             "kernel_ms": dom_ms, "peak_kind": peak_kind,
-                             "algo_bytes_per_cell_dir": bpu},
+                             "frac": achieved / peak, "traffic": measured_traffic(dom, L, nd), "kernel": dom,
+                             "kernel_ms": dom_ms, "peak_kind": peak_kind, "algo_bytes_per_cell_dir": bpu},
                 "step_roofline_frac": bpu * n_leaf * nd / (ms / 1e3) / 1e9 / peak,
-                "kernels": kern,
-                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "error_vs_oracle": err}
+                "kernels": kern, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "error_vs_oracle": err}
+        if other is not None:
+            line["compare"] = other
+            line["speedup_vs_" + other_name] = other["ms_per_step"] / ms
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -349,7 +403,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP32-plain comparison run")
     ap.add_argument("--level", type=int, default=8)
     ap.add_argument("--nside", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
