@@ -104,9 +104,25 @@ void cd_opts_default(cd_opts *o);
 cd_status cd_build_tree_uniform(int leaf_level, double box_cm, const float *rho, int rho_on_device,
                                 void *stream, cd_tree *out);
 
-/* Replaces the leaf densities of an existing tree built by
- * cd_build_tree_uniform (same layout and rules as there) and recomputes every
- * coarse level.  This is the per-step call of a simulation whose density
+/* Builds an adaptive (AMR) octree from its leaves (§3 intro: refinement cell
+ * by cell; fully threaded tree).  Leaf i has level level[i] in
+ * [base_level, max_level], integer index (ijk[3i], ijk[3i+1], ijk[3i+2]) at
+ * its own level and density rho[i]; the leaves must tile the box exactly
+ * (no gap, no overlap).  Coarse levels hold volume means of the leaf field: a
+ * region inside a coarser leaf takes that leaf's value (§3.2).
+ *   1 <= base_level <= max_level <= 11; level and ijk are host arrays; rho
+ *   is a device pointer if rho_on_device != 0, else host memory.
+ * Output rows follow the depth-first (Morton) order of the leaves;
+ * cd_tree_leaves() returns it.  The mesh description is built on the host
+ * (synchronous); the density-dependent part runs on `stream`.
+ * Errors: CD_EINVAL (bad level or index, overlap, gap), CD_ENOMEM, CD_ECUDA. */
+cd_status cd_build_tree_amr(int base_level, int max_level, double box_cm, int64_t n_leaf, const int8_t *level,
+                            const int32_t *ijk, const float *rho, int rho_on_device, void *stream, cd_tree *out);
+
+/* Replaces the leaf densities of an existing tree and recomputes every coarse
+ * level.  Uniform trees: same layout and rules as cd_build_tree_uniform.  AMR
+ * trees: n_leaf values in the caller's original leaf order (the order given
+ * to cd_build_tree_amr).  This is the per-step call of a simulation whose density
  * changes but whose mesh does not; it allocates nothing.  Asynchronous for a
  * device pointer; for host memory the data are copied before return. */
 cd_status cd_tree_update(cd_tree tree, const float *rho, int rho_on_device, void *stream);

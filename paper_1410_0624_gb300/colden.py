@@ -24,7 +24,7 @@ _STATUS = {CD_EINVAL: "EINVAL", CD_ENOMEM: "ENOMEM", CD_ECUDA: "ECUDA", CD_ETIME
 
 # every symbol include/colden.h declares (checked by the ABI test)
 EXPORTS = (
-    "cd_opts_default", "cd_build_tree_uniform", "cd_tree_update", "cd_precompute_geometry",
+    "cd_opts_default", "cd_build_tree_uniform", "cd_build_tree_amr", "cd_tree_update", "cd_precompute_geometry",
     "cd_column_density", "cd_tree_info", "cd_tree_leaves", "cd_geom_info", "cd_stats_reset", "cd_stats_get",
     "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_column_density_noalloc", "cd_device_status",
 )
@@ -66,6 +66,7 @@ def load(build_if_missing: bool = False):
     L.cd_opts_default.restype = None
     L.cd_build_tree_uniform.argtypes = [I, D, P, I, P, ctypes.POINTER(P)]
     L.cd_tree_update.argtypes = [P, P, I, P]
+    L.cd_build_tree_amr.argtypes = [I, I, D, I64, P, P, P, I, P, ctypes.POINTER(P)]
     L.cd_stats_reset.argtypes = [I]
     L.cd_stats_reset.restype = None
     L.cd_stats_get.argtypes = [I, ctypes.POINTER(I64), ctypes.POINTER(D)]
@@ -197,6 +198,27 @@ def build_tree_uniform(rho, box_cm: float, stream=None) -> Tree:
     h = ctypes.c_void_p()
     _check(load().cd_build_tree_uniform(L, float(box_cm), ctypes.c_void_p(ptr), on_dev,
                                         ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
+    return Tree(h.value)
+
+
+def build_tree_amr(base_level: int, max_level: int, box_cm: float, level, ijk, rho, stream=None) -> Tree:
+    """cd_build_tree_amr.  level int8 [n], ijk int32 [n, 3] (host); rho float32
+    [n] as a CUDA tensor (device path) or numpy / CPU tensor (host path)."""
+    import torch
+    lv = np.ascontiguousarray(level, dtype=np.int8).reshape(-1)
+    ix = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+    if isinstance(rho, torch.Tensor) and rho.is_cuda:
+        assert rho.dtype == torch.float32 and rho.is_contiguous() and rho.numel() == lv.shape[0]
+        ptr, on_dev = rho.data_ptr(), 1
+    else:
+        keep = np.ascontiguousarray(rho.cpu().numpy() if isinstance(rho, torch.Tensor) else rho, dtype=np.float32)
+        assert keep.size == lv.shape[0]
+        ptr, on_dev = keep.ctypes.data, 0
+    h = ctypes.c_void_p()
+    _check(load().cd_build_tree_amr(int(base_level), int(max_level), float(box_cm), lv.shape[0],
+                                    lv.ctypes.data_as(ctypes.c_void_p), ix.ctypes.data_as(ctypes.c_void_p),
+                                    ctypes.c_void_p(ptr), on_dev, ctypes.c_void_p(_stream_ptr(stream)),
+                                    ctypes.byref(h)))
     return Tree(h.value)
 
 

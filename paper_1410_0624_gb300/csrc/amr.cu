@@ -1,0 +1,510 @@
+// Adaptive (AMR) octrees: leaves at levels base .. lmax that tile the box.
+//
+// Build (host, once per mesh): leaves are validated, ordered depth-first
+// (Morton key of their first finest cell), checked to tile the box exactly,
+// and the mesh is described per level by
+//   - the refined cells of level k (sorted Morton keys, parent index in level
+//     k-1): they receive the far-shell prefix S_k (§3.3, two-level
+//     approximation for Δl >= 3);
+//   - the leaf-bearing octs of level k (refined cells with at least one leaf
+//     child at k+1): they receive the three nearest shells E, and their leaf
+//     children get the internal and local terms (§3.2).
+// Update (device, every step): the leaf densities are permuted into output
+// order, the dense volume-mean arrays of levels 0 .. lmax-1 are rebuilt (a
+// cell inside a coarser leaf takes that leaf's value, a refined cell the mean
+// of its children: the coarse density "corresponds to a mean", §3.2), and the
+// per-oct sibling densities are gathered.
+//
+// Shells and leaves run over these lists with the same tables as the uniform
+// tree; the stencil densities come from the dense level arrays.
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cd {
+namespace {
+
+inline unsigned grid_for(int64_t n, int block, int cap = 152 * 32)
+{
+    int64_t g = (n + block - 1) / block;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, cap));
+}
+
+// ---- update kernels ------------------------------------------------------------
+
+__global__ void gather_leaves(const float *__restrict__ in, const int64_t *__restrict__ src, int64_t n,
+                              float *__restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[src[i]];
+}
+
+// Leaves of level <= lf paint their cells of level lf (= lmax - 1).
+__global__ void paint_level(const float *__restrict__ rho, const int8_t *__restrict__ lvl,
+                            const uint64_t *__restrict__ key, int64_t n, int lf, float *__restrict__ out)
+{
+    const int64_t side = (int64_t)1 << lf;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int l = lvl[i];
+        if (l > lf) continue;
+        const uint64_t m = key[i];
+        const int s = 1 << (lf - l);
+        const int64_t x0 = (int64_t)compact3(m) * s, y0 = (int64_t)compact3(m >> 1) * s, z0 = (int64_t)compact3(m >> 2) * s;
+        const float v = rho[i];
+        for (int dz = 0; dz < s; ++dz)
+            for (int dy = 0; dy < s; ++dy)
+                for (int dx = 0; dx < s; ++dx) out[((z0 + dz) * side + (y0 + dy)) * side + x0 + dx] = v;
+    }
+}
+
+// Octs of level lf whose 8 children are leaves of level lf + 1: the cell value
+// is the mean of the children (same order and rounding as the restriction).
+__global__ void mean_finest(const float *__restrict__ rho, const uint64_t *__restrict__ okey,
+                            const int32_t *__restrict__ oleaf, int64_t n, int lf, float *__restrict__ out)
+{
+    const int64_t side = (int64_t)1 << lf;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t m = okey[i];
+        float s = 0.f;
+#pragma unroll
+        for (int o = 0; o < 8; ++o) s += rho[oleaf[8 * i + o]];
+        out[((int64_t)compact3(m >> 2) * side + compact3(m >> 1)) * side + compact3(m)] = s * 0.125f;
+    }
+}
+
+// Sibling densities of every oct: child o at level k+1 from the dense array,
+// or from the leaves when k+1 is the finest level.
+__global__ void gather_rho8(const uint64_t *__restrict__ okey, const int32_t *__restrict__ oleaf, int64_t n, int k,
+                            const float *__restrict__ dense_k1, const float *__restrict__ rho_leaf,
+                            float *__restrict__ rho8)
+{
+    const int64_t side = (int64_t)1 << (k + 1);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 8 * n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e >> 3;
+        const int o = (int)(e & 7);
+        float v;
+        if (dense_k1) {
+            const uint64_t m = okey[i];
+            const int64_t x = 2 * (int64_t)compact3(m) + (o & 1), y = 2 * (int64_t)compact3(m >> 1) + ((o >> 1) & 1),
+                          z = 2 * (int64_t)compact3(m >> 2) + ((o >> 2) & 1);
+            v = dense_k1[(z * side + y) * side + x];
+        } else {
+            v = rho_leaf[oleaf[e]];
+        }
+        rho8[e] = v;
+    }
+}
+
+// ---- list kernels --------------------------------------------------------------
+
+struct ShellListArgs {
+    int k, nd, tmask;
+    const float *lvl[4];         // dense level arrays of the shell level of table t (k - t + 1)
+    float dx[4];
+    const uint64_t *keys;        // receiving cells (Morton keys at level k)
+    int64_t n;
+    const int32_t *parent;       // index of each receiver's parent in the prefix rows
+    const float *prefix;         // S_{k-1} rows or NULL
+    float *out;                  // [n][nd]
+    const int2 *tab[4];
+    const int *cmax[4];
+};
+
+// Eq. N_discret for a list of receiving cells: thread per (cell, direction),
+// stencil densities read from the dense level arrays (zero outside the box).
+__global__ void __launch_bounds__(256) shell_list_fp32(ShellListArgs P)
+{
+    const int nd = P.nd;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P.n * nd; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / nd;
+        const int d = (int)(e - i * nd);
+        const uint64_t m = P.keys[i];
+        const int64_t cx = compact3(m), cy = compact3(m >> 1), cz = compact3(m >> 2);
+        float acc = P.prefix ? P.prefix[(int64_t)P.parent[i] * nd + d] : 0.f;
+        for (int t = 1; t <= 3; ++t) {
+            if (!(P.tmask & (1 << (t - 1)))) continue;
+            const int64_t side = (int64_t)1 << (P.k - t + 1);
+            const int R = region_side(t);
+            const int64_t ox = 2 * ((cx >> t) - 1), oy = 2 * ((cy >> t) - 1), oz = 2 * ((cz >> t) - 1);
+            const int cfg = (int)(m & ((1u << (3 * t)) - 1));
+            const int2 *row = P.tab[t] + (size_t)cfg * CD_MAXE * nd + d;
+            const int cnt = P.cmax[t][cfg];
+            const float *rho = P.lvl[t];
+            float part = 0.f;
+            for (int q = 0; q < cnt; ++q) {
+                const int2 v = row[(size_t)q * nd];
+                const int a = v.x % R, b = (v.x / R) % R, c = v.x / (R * R);
+                const int64_t gx = ox + a, gy = oy + b, gz = oz + c;
+                if (gx >= 0 && gy >= 0 && gz >= 0 && gx < side && gy < side && gz < side)
+                    part = fmaf(rho[(gz * side + gy) * side + gx], __int_as_float(v.y), part);
+            }
+            acc = fmaf(P.dx[t], part, acc);
+        }
+        P.out[e] = acc;
+    }
+}
+
+struct LeafListArgs {
+    int64_t n;                   // octs of this level
+    int nd;
+    float dx_leaf, av_per_nh, c_exp2, inv_nd;
+    const float *rho8;           // [n][8]
+    const int32_t *oleaf;        // [n][8] leaf rows, -1 for refined children
+    const float *E;              // [n][nd]
+    const float *Sp;             // parent prefix rows or NULL
+    const int32_t *oparent;      // [n]
+    const float *kloc;
+    float *n_h, *a_v, *shield;
+};
+
+// Internal + local terms and the epilogue for the leaf children of a list of
+// octs (one warp per oct); the screening sum is taken in a fixed order.
+__global__ void __launch_bounds__(256) leaf_list(LeafListArgs P)
+{
+    extern __shared__ float sm[];
+    const int nd = P.nd;
+    float *s_k = sm;                          // [8 t][8 s][nd], times dx
+    float *s_e = sm + 64 * nd;                // [8 warps][8 nd]
+    __shared__ int s_row[8][8];
+    for (int i = threadIdx.x; i < 64 * nd; i += blockDim.x) s_k[i] = P.dx_leaf * P.kloc[i];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *e_w = s_e + w * 8 * nd;
+    for (int64_t i = (int64_t)blockIdx.x * 8 + w; i < P.n; i += (int64_t)gridDim.x * 8) {
+        const float r = P.rho8[8 * i + (lane & 7)];
+        float rs[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) rs[s] = __shfl_sync(0xffffffffu, r, s);
+        if (lane < 8) s_row[w][lane] = P.oleaf[8 * i + lane];
+        __syncwarp();
+        const float *E = P.E + i * nd;
+        const float *Sp = P.Sp ? P.Sp + (int64_t)P.oparent[i] * nd : nullptr;
+        for (int f = lane; f < 8 * nd; f += 32) {
+            const int t = f / nd, d = f - t * nd;
+            const int row = s_row[w][t];
+            if (row < 0) continue;
+            float nv = E[d] + (Sp ? Sp[d] : 0.f);
+            const float *kl = s_k + t * 8 * nd + d;
+#pragma unroll
+            for (int s = 0; s < 8; ++s) nv = fmaf(rs[s], kl[s * nd], nv);
+            if (P.n_h) P.n_h[(int64_t)row * nd + d] = nv;
+            if (P.a_v) P.a_v[(int64_t)row * nd + d] = nv * P.av_per_nh;
+            e_w[f] = exp2f(P.c_exp2 * nv);
+        }
+        __syncwarp();
+        if (P.shield && lane < 8 && s_row[w][lane] >= 0) {
+            float acc = 0.f;
+            for (int d = 0; d < nd; ++d) acc += e_w[lane * nd + d];
+            P.shield[s_row[w][lane]] = acc * P.inv_nd;
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace
+
+// ---- host build ------------------------------------------------------------------
+
+cd_status build_amr(cd_tree t, int base, int lmax, int64_t n, const int8_t *level, const int32_t *ijk)
+{
+    if (base < 1 || lmax < base || lmax > 11) {
+        set_error("AMR levels must satisfy 1 <= base <= max_level <= 11 (got %d, %d)", base, lmax);
+        return CD_EINVAL;
+    }
+    if (n < 1) {
+        set_error("no leaves");
+        return CD_EINVAL;
+    }
+    // depth-first order: Morton key of the first finest cell
+    std::vector<uint64_t> fine(n), key(n);
+    for (int64_t i = 0; i < n; ++i) {
+        const int l = level[i];
+        if (l < base || l > lmax) {
+            set_error("leaf %lld has level %d outside [%d, %d]", (long long)i, l, base, lmax);
+            return CD_EINVAL;
+        }
+        const int64_t side = (int64_t)1 << l;
+        const int64_t x = ijk[3 * i], y = ijk[3 * i + 1], z = ijk[3 * i + 2];
+        if (x < 0 || y < 0 || z < 0 || x >= side || y >= side || z >= side) {
+            set_error("leaf %lld index (%lld, %lld, %lld) outside its level", (long long)i, (long long)x, (long long)y,
+                      (long long)z);
+            return CD_EINVAL;
+        }
+        key[i] = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+        fine[i] = key[i] << (3 * (lmax - l));
+    }
+    std::vector<int64_t> ord(n);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return fine[a] < fine[b]; });
+    // exact tiling: consecutive leaves abut and cover 8^lmax finest cells
+    uint64_t expect = 0;
+    for (int64_t r = 0; r < n; ++r) {
+        const int64_t i = ord[r];
+        if (fine[i] != expect) {
+            set_error(fine[i] < expect ? "leaves overlap (near leaf %lld)" : "leaves leave a gap (near leaf %lld)",
+                      (long long)i);
+            return CD_EINVAL;
+        }
+        expect += (uint64_t)1 << (3 * (lmax - level[i]));
+    }
+    if (expect != (uint64_t)1 << (3 * lmax)) {
+        set_error("leaves do not cover the box");
+        return CD_EINVAL;
+    }
+    // output-order arrays (host)
+    t->leaf_level_h = new int8_t[n];
+    t->leaf_ijk_h = new int32_t[3 * n];
+    t->leaf_src_h = new int64_t[n];
+    std::vector<uint64_t> okey(n);
+    std::vector<int8_t> olvl(n);
+    for (int64_t r = 0; r < n; ++r) {
+        const int64_t i = ord[r];
+        t->leaf_level_h[r] = level[i];
+        for (int a = 0; a < 3; ++a) t->leaf_ijk_h[3 * r + a] = ijk[3 * i + a];
+        t->leaf_src_h[r] = i;
+        okey[r] = key[i];
+        olvl[r] = level[i];
+    }
+    // refined cells per level: all cells below base; ancestors of deeper leaves from base on
+    std::vector<std::vector<uint64_t>> ref(lmax + 1);
+    for (int k = 0; k < base; ++k) {
+        ref[k].resize((size_t)1 << (3 * k));
+        std::iota(ref[k].begin(), ref[k].end(), (uint64_t)0);
+    }
+    for (int64_t r = 0; r < n; ++r)
+        for (int k = base; k < olvl[r]; ++k) {
+            const uint64_t a = okey[r] >> (3 * (olvl[r] - k));
+            if (ref[k].empty() || ref[k].back() != a) ref[k].push_back(a);   // leaves are in depth-first order
+        }
+    for (int k = base; k <= lmax; ++k) {
+        std::sort(ref[k].begin(), ref[k].end());
+        ref[k].erase(std::unique(ref[k].begin(), ref[k].end()), ref[k].end());
+    }
+    // leaf-bearing octs, grouped by level, depth-first within a level
+    std::vector<std::vector<uint64_t>> oct(lmax + 1);
+    std::vector<std::vector<int32_t>> oleaf(lmax + 1);
+    {
+        std::vector<std::vector<std::pair<uint64_t, int64_t>>> tmp(lmax + 1);
+        for (int64_t r = 0; r < n; ++r) tmp[olvl[r] - 1].push_back({okey[r], r});
+        for (int k = 0; k < lmax; ++k) {
+            auto &v = tmp[k];
+            std::sort(v.begin(), v.end());
+            for (size_t j = 0; j < v.size(); ++j) {
+                const uint64_t p = v[j].first >> 3;
+                if (oct[k].empty() || oct[k].back() != p) {
+                    oct[k].push_back(p);
+                    oleaf[k].insert(oleaf[k].end(), 8, -1);
+                }
+                oleaf[k][8 * (oct[k].size() - 1) + (v[j].first & 7)] = (int32_t)v[j].second;
+            }
+        }
+    }
+    // parents
+    auto parent_index = [&](int k, uint64_t cellkey) -> int32_t {
+        if (k < 1) return -1;
+        const auto &v = ref[k - 1];
+        auto it = std::lower_bound(v.begin(), v.end(), cellkey >> 3);
+        return (it != v.end() && *it == (cellkey >> 3)) ? (int32_t)(it - v.begin()) : -1;
+    };
+    // upload
+    cd_status st = CD_OK;
+    auto up = [&](void **dst, const void *src, size_t bytes) -> bool {
+        if (bytes == 0) return true;
+        if (cudaMalloc(dst, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("AMR tree allocation failed (%zu bytes)", bytes);
+            st = CD_ENOMEM;
+            return false;
+        }
+        if (src && cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            set_error("AMR tree upload failed");
+            st = CD_ECUDA;
+            return false;
+        }
+        return true;
+    };
+    for (int k = 0; k <= lmax; ++k) {
+        t->n_ref[k] = (int64_t)ref[k].size();
+        if (!t->n_ref[k]) continue;
+        std::vector<int32_t> par(ref[k].size());
+        for (size_t j = 0; j < ref[k].size(); ++j) par[j] = parent_index(k, ref[k][j]);
+        if (!up((void **)&t->ref_key[k], ref[k].data(), ref[k].size() * 8)) return st;
+        if (!up((void **)&t->ref_parent[k], par.data(), par.size() * 4)) return st;
+    }
+    std::vector<uint64_t> allkey;
+    std::vector<int32_t> allpar, allleaf;
+    for (int k = 0; k <= lmax; ++k) {
+        t->oct_begin[k] = (int64_t)allkey.size();
+        for (size_t j = 0; j < oct[k].size(); ++j) {
+            allkey.push_back(oct[k][j]);
+            allpar.push_back(parent_index(k, oct[k][j]));
+        }
+        allleaf.insert(allleaf.end(), oleaf[k].begin(), oleaf[k].end());
+    }
+    t->oct_begin[lmax + 1] = (int64_t)allkey.size();
+    t->n_oct = (int64_t)allkey.size();
+    if (!up((void **)&t->oct_key, allkey.data(), allkey.size() * 8)) return st;
+    if (!up((void **)&t->oct_parent, allpar.data(), allpar.size() * 4)) return st;
+    if (!up((void **)&t->oct_leaf, allleaf.data(), allleaf.size() * 4)) return st;
+    if (!up((void **)&t->oct_rho8, nullptr, allkey.size() * 8 * 4)) return st;
+    if (!up((void **)&t->leaf_key, okey.data(), n * 8)) return st;
+    if (!up((void **)&t->leaf_lvl, olvl.data(), n)) return st;
+    if (!up((void **)&t->leaf_src, t->leaf_src_h, n * 8)) return st;
+    if (!up((void **)&t->rho_leaf, nullptr, n * 4)) return st;
+    for (int l = 0; l <= lmax - 1; ++l) {
+        const size_t cells = (size_t)1 << (3 * l);
+        if (!up((void **)&t->rho_lvl[l], nullptr, cells * 4)) return st;
+        if (l >= 1 && !up((void **)&t->rho_brick[l], nullptr, cells * 2)) return st;
+    }
+    t->amr = 1;
+    t->L = lmax;
+    t->base = base;
+    t->n_leaf = n;
+    return CD_OK;
+}
+
+// rho: leaf densities in the caller's order (device).
+cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s)
+{
+    const int lmax = t->L, lf = lmax - 1;
+    {
+        LaunchScope ls(CD_K_RESTRICT, s);
+        gather_leaves<<<grid_for(t->n_leaf, 256), 256, 0, s>>>(rho_dev, t->leaf_src, t->n_leaf, t->rho_leaf);
+    }
+    CD_CHECK_LAUNCH();
+    {
+        LaunchScope ls(CD_K_RESTRICT, s);
+        paint_level<<<grid_for(t->n_leaf, 256), 256, 0, s>>>(t->rho_leaf, t->leaf_lvl, t->leaf_key, t->n_leaf, lf,
+                                                             t->rho_lvl[lf]);
+    }
+    CD_CHECK_LAUNCH();
+    const int64_t nfin = t->oct_begin[lf + 1] - t->oct_begin[lf];
+    if (nfin > 0) {
+        LaunchScope ls(CD_K_RESTRICT, s);
+        mean_finest<<<grid_for(nfin, 256), 256, 0, s>>>(t->rho_leaf, t->oct_key + t->oct_begin[lf],
+                                                        t->oct_leaf + 8 * t->oct_begin[lf], nfin, lf, t->rho_lvl[lf]);
+    }
+    CD_CHECK_LAUNCH();
+    cd_status st = restrict_dense(t, lf, s);
+    if (st != CD_OK) return st;
+    for (int k = 0; k < lmax; ++k) {
+        const int64_t no = t->oct_begin[k + 1] - t->oct_begin[k];
+        if (!no) continue;
+        LaunchScope ls(CD_K_RESTRICT, s);
+        gather_rho8<<<grid_for(8 * no, 256), 256, 0, s>>>(t->oct_key + t->oct_begin[k], t->oct_leaf + 8 * t->oct_begin[k],
+                                                          no, k, k + 1 <= lf ? t->rho_lvl[k + 1] : nullptr,
+                                                          t->rho_leaf, t->oct_rho8 + 8 * t->oct_begin[k]);
+        CD_CHECK_LAUNCH();
+    }
+    return CD_OK;
+}
+
+cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n_h, float *a_v, float *shield,
+                             cudaStream_t s)
+{
+    const int nd = g->n_dir, L = t->L;
+    // workspace: S_k over the refined cells of levels 3 .. L-2, E over all octs
+    if (t->ws.ndir != nd) {
+        for (int k = 0; k <= CD_MAXL; ++k) {
+            if (t->ws.S[k]) cudaFree(t->ws.S[k]);
+            t->ws.S[k] = nullptr;
+        }
+        if (t->ws.E) cudaFree(t->ws.E);
+        t->ws.E = nullptr;
+        t->ws.ndir = 0;
+        for (int k = 3; k <= L - 2; ++k)
+            if (t->n_ref[k] && cudaMalloc(&t->ws.S[k], sizeof(float) * t->n_ref[k] * nd) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("AMR workspace allocation failed");
+                return CD_ENOMEM;
+            }
+        if (cudaMalloc(&t->ws.E, sizeof(float) * std::max<int64_t>(t->n_oct, 1) * nd) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("AMR workspace allocation failed");
+            return CD_ENOMEM;
+        }
+        t->ws.ndir = nd;
+    }
+    const auto dx = [&](int l) { return (float)(t->box_cm / (double)((int64_t)1 << l)); };
+    ShellListArgs A;
+    for (int q = 0; q < 4; ++q) {
+        A.tab[q] = g->tab[q];
+        A.cmax[q] = g->cmax[q];
+    }
+    A.nd = nd;
+    // far-shell prefixes of the refined cells
+    for (int k = 3; k <= L - 2; ++k) {
+        if (!t->n_ref[k]) continue;
+        A.k = k;
+        A.tmask = 4;
+        for (int q = 0; q < 4; ++q) {
+            A.lvl[q] = nullptr;
+            A.dx[q] = 0.f;
+        }
+        A.lvl[3] = t->rho_lvl[k - 2];
+        A.dx[3] = dx(k - 2);
+        A.keys = t->ref_key[k];
+        A.n = t->n_ref[k];
+        A.parent = t->ref_parent[k];
+        A.prefix = (k - 1 >= 3) ? t->ws.S[k - 1] : nullptr;
+        A.out = t->ws.S[k];
+        LaunchScope ls(CD_K_SHELL, s);
+        shell_list_fp32<<<grid_for(A.n * nd, 256), 256, 0, s>>>(A);
+        CD_CHECK_LAUNCH();
+    }
+    // the three nearest shells of every oct, level by level
+    for (int k = 0; k <= L - 1; ++k) {
+        const int64_t no = t->oct_begin[k + 1] - t->oct_begin[k];
+        if (!no) continue;
+        A.k = k;
+        A.tmask = 0;
+        for (int q = 0; q < 4; ++q) {
+            A.lvl[q] = nullptr;
+            A.dx[q] = 0.f;
+        }
+        for (int q = 1; q <= 3 && q <= k; ++q) {
+            A.tmask |= 1 << (q - 1);
+            A.lvl[q] = t->rho_lvl[k - q + 1];
+            A.dx[q] = dx(k - q + 1);
+        }
+        A.keys = t->oct_key + t->oct_begin[k];
+        A.n = no;
+        A.parent = nullptr;
+        A.prefix = nullptr;
+        A.out = t->ws.E + t->oct_begin[k] * nd;
+        LaunchScope ls(CD_K_SHELL, s);
+        shell_list_fp32<<<grid_for(no * nd, 256), 256, 0, s>>>(A);
+        CD_CHECK_LAUNCH();
+    }
+    // leaves
+    const size_t smem = sizeof(float) * (64 * nd + 64 * nd);
+    if (smem > 48 * 1024) CD_CUDA(cudaFuncSetAttribute(leaf_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    for (int k = 0; k <= L - 1; ++k) {
+        const int64_t no = t->oct_begin[k + 1] - t->oct_begin[k];
+        if (!no) continue;
+        LeafListArgs B;
+        B.n = no;
+        B.nd = nd;
+        B.dx_leaf = dx(k + 1);
+        B.av_per_nh = (float)opts.av_per_nh;
+        B.c_exp2 = (float)(-opts.shield_k * opts.av_per_nh * 1.4426950408889634);
+        B.inv_nd = 1.0f / (float)nd;
+        B.rho8 = t->oct_rho8 + 8 * t->oct_begin[k];
+        B.oleaf = t->oct_leaf + 8 * t->oct_begin[k];
+        B.E = t->ws.E + t->oct_begin[k] * nd;
+        B.Sp = (k - 1 >= 3) ? t->ws.S[k - 1] : nullptr;
+        B.oparent = t->oct_parent + t->oct_begin[k];
+        B.kloc = g->kloc;
+        B.n_h = n_h;
+        B.a_v = a_v;
+        B.shield = shield;
+        LaunchScope ls(CD_K_LEAF, s);
+        leaf_list<<<grid_for(no, 8, 152 * 16), 256, smem, s>>>(B);
+        CD_CHECK_LAUNCH();
+    }
+    return CD_OK;
+}
+
+}  // namespace cd

@@ -175,26 +175,51 @@ cd_status cd_build_tree_uniform(int leaf_level, double box_cm, const float *rho,
     return CD_OK;
 }
 
+cd_status cd_build_tree_amr(int base_level, int max_level, double box_cm, int64_t n_leaf, const int8_t *level,
+                            const int32_t *ijk, const float *rho, int rho_on_device, void *stream, cd_tree *out)
+{
+    if (!out) {
+        set_error("out is NULL");
+        return CD_EINVAL;
+    }
+    *out = nullptr;
+    if (!level || !ijk || !rho) {
+        set_error("level, ijk or rho is NULL");
+        return CD_EINVAL;
+    }
+    if (!(box_cm > 0.0) || !isfinite(box_cm)) {
+        set_error("box_cm must be finite and > 0");
+        return CD_EINVAL;
+    }
+    cd_tree t = new cd_tree_s();
+    cudaGetDevice(&t->dev);
+    t->box_cm = box_cm;
+    cd_status st = build_amr(t, base_level, max_level, n_leaf, level, ijk);
+    if (st == CD_OK) st = cd_tree_update(t, rho, rho_on_device, stream);
+    if (st != CD_OK) {
+        cd_tree_free(t);
+        return st;
+    }
+    *out = t;
+    return CD_OK;
+}
+
 cd_status cd_tree_update(cd_tree t, const float *rho, int rho_on_device, void *stream)
 {
     if (!t || !rho) {
         set_error("tree or rho is NULL");
         return CD_EINVAL;
     }
-    if (t->amr) {
-        set_error("cd_tree_update serves uniform trees");
-        return CD_EINVAL;
-    }
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t N = t->n_leaf;
-    if (rho_on_device) return restrict_uniform(t, rho, s);
+    const auto apply = [&](const float *dev) { return t->amr ? update_amr(t, dev, s) : restrict_uniform(t, dev, s); };
+    if (rho_on_device) return apply(rho);
     for (int64_t i = 0; i < N; ++i)
         if (!(rho[i] >= 0.f) || !isfinite(rho[i])) {
             set_error("rho[%lld] = %g is negative or not finite", (long long)i, (double)rho[i]);
             return CD_EINVAL;
         }
-    // host data: stage through the workspace-independent leaf buffer is not
-    // possible (the restriction reads row-major input), so use a temporary
+    // host data goes through a temporary device buffer
     float *staging = nullptr;
     if (cudaMallocAsync(&staging, sizeof(float) * N, s) != cudaSuccess) {
         cudaGetLastError();
@@ -206,7 +231,7 @@ cd_status cd_tree_update(cd_tree t, const float *rho, int rho_on_device, void *s
         set_error("upload failed: %s", cudaGetErrorString(cudaGetLastError()));
         st = CD_ECUDA;
     }
-    if (st == CD_OK) st = restrict_uniform(t, staging, s);
+    if (st == CD_OK) st = apply(staging);
     cudaFreeAsync(staging, s);
     if (st == CD_OK && cudaStreamSynchronize(s) != cudaSuccess) {
         set_error("tree update failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -291,6 +316,7 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
     }
     if (!n_h && !a_v && !shield) return CD_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    if (tree->amr) return column_density_amr(tree, geom, opts, n_h, a_v, shield, s);
     const int nd = geom->n_dir, L = tree->L;
     cd_status st = ensure_workspace(tree, nd);
     if (st != CD_OK) return st;
@@ -369,6 +395,11 @@ cd_status cd_tree_leaves(cd_tree t, int8_t *level, int32_t *ijk)
         set_error("tree is NULL");
         return CD_EINVAL;
     }
+    if (t->amr) {
+        if (level) memcpy(level, t->leaf_level_h, t->n_leaf);
+        if (ijk) memcpy(ijk, t->leaf_ijk_h, sizeof(int32_t) * 3 * t->n_leaf);
+        return CD_OK;
+    }
     for (int64_t i = 0; i < t->n_leaf; ++i) {
         if (level) level[i] = (int8_t)t->L;
         if (ijk) {
@@ -401,6 +432,16 @@ void cd_tree_free(cd_tree t)
         if (t->rho_brick[l]) cudaFree(t->rho_brick[l]);
     }
     if (t->rho_leaf) cudaFree(t->rho_leaf);
+    for (int l = 0; l <= CD_MAXL; ++l) {
+        if (t->ref_key[l]) cudaFree(t->ref_key[l]);
+        if (t->ref_parent[l]) cudaFree(t->ref_parent[l]);
+    }
+    for (void *p : {(void *)t->oct_key, (void *)t->oct_parent, (void *)t->oct_leaf, (void *)t->oct_rho8,
+                    (void *)t->leaf_key, (void *)t->leaf_lvl, (void *)t->leaf_src})
+        if (p) cudaFree(p);
+    delete[] t->leaf_level_h;
+    delete[] t->leaf_ijk_h;
+    delete[] t->leaf_src_h;
     delete t;
 }
 

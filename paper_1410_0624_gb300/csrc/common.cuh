@@ -96,6 +96,21 @@ struct cd_tree_s {
     float *rho_leaf = nullptr;          // leaf densities, Morton order
     cd::Workspace ws;
     int dev = 0;
+    // AMR meshes (amr != 0); see amr.cu
+    int64_t n_ref[CD_MAXL + 1] = {};      // refined cells of level k
+    uint64_t *ref_key[CD_MAXL + 1] = {};  // their sorted Morton keys (device)
+    int32_t *ref_parent[CD_MAXL + 1] = {};// index of each one's parent in level k-1 (device)
+    int64_t oct_begin[CD_MAXL + 2] = {};  // leaf-bearing octs of level k: [oct_begin[k], oct_begin[k+1])
+    uint64_t *oct_key = nullptr;          // (device) Morton key of every oct at its level
+    int32_t *oct_parent = nullptr;        // (device) index of the oct's parent among the refined cells
+    int32_t *oct_leaf = nullptr;          // (device) [n_oct][8] output row of child o, -1 if refined
+    float *oct_rho8 = nullptr;            // (device) [n_oct][8] volume-mean density of child o
+    uint64_t *leaf_key = nullptr;         // (device) output order: Morton key at the leaf's level
+    int8_t *leaf_lvl = nullptr;           // (device) output order: level
+    int64_t *leaf_src = nullptr;          // (device) output order: index in the caller's leaf arrays
+    int8_t *leaf_level_h = nullptr;       // host copies of the output order
+    int32_t *leaf_ijk_h = nullptr;
+    int64_t *leaf_src_h = nullptr;
 };
 
 struct cd_geom_s {
@@ -135,6 +150,14 @@ class LaunchScope {
 
 // tree.cu
 cd_status restrict_uniform(cd_tree t, const float *rho_dev, cudaStream_t s);
+// levels top-1 .. 0 as means of top .. 1, then BF16 bricks of levels 1 .. top
+cd_status restrict_dense(cd_tree t, int top, cudaStream_t s);
+
+// amr.cu
+cd_status build_amr(cd_tree t, int base, int lmax, int64_t n, const int8_t *level, const int32_t *ijk);
+cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s);
+cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n_h, float *a_v, float *shield,
+                             cudaStream_t s);
 
 // geometry.cu
 int make_directions(int scheme, int p0, int p1, const double *custom, int n_custom, double *out);

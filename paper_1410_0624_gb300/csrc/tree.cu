@@ -98,13 +98,18 @@ cd_status restrict_uniform(cd_tree t, const float *rho_dev, cudaStream_t s)
         restrict_from_leaves<<<grid_for(np * np * np, 256), 256, 0, s>>>(rho_dev, L, t->rho_leaf, t->rho_lvl[L - 1]);
     }
     CD_CHECK_LAUNCH();
-    for (int l = L - 1; l >= 1; --l) {
+    return restrict_dense(t, L - 1, s);
+}
+
+cd_status restrict_dense(cd_tree t, int top, cudaStream_t s)
+{
+    for (int l = top; l >= 1; --l) {
         const int64_t n = (int64_t)1 << (l - 1);
         LaunchScope ls(CD_K_RESTRICT, s);
         restrict_level<<<grid_for(n * n * n, 256), 256, 0, s>>>(t->rho_lvl[l], l, t->rho_lvl[l - 1]);
         CD_CHECK_LAUNCH();
     }
-    for (int l = 1; l <= L - 1; ++l) {
+    for (int l = 1; l <= top; ++l) {
         const int64_t n = (int64_t)1 << (l - 1);
         LaunchScope ls(CD_K_RESTRICT, s);
         to_bricks<<<grid_for(n * n * n, 256), 256, 0, s>>>(t->rho_lvl[l], l, t->rho_brick[l]);

@@ -109,3 +109,51 @@ def amr_leaves(fine: np.ndarray, base_level: int, thresholds) -> dict:
         refined = split
     return dict(level=np.concatenate(levels), ijk=np.concatenate(ijks),
                 rho=np.concatenate(rhos), base=base_level, lmax=lmax)
+
+
+def amr_leaves_grf_torch(lmax: int, base_level: int, thresholds, mean: float, sigma_ln: float, seed: int,
+                         device="cuda") -> dict:
+    """The recipe of ``lognormal_grf`` + ``amr_leaves`` at sizes numpy cannot
+    hold comfortably (a 1024^3 finest field), generated with torch on a GPU
+    from a seeded torch.Generator.  Deterministic for a given device type."""
+    import torch
+    n = 1 << lmax
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    w = torch.randn((n, n, n), generator=g, device=device, dtype=torch.float32)
+    wk = torch.fft.rfftn(w)
+    del w
+    kz = torch.fft.fftfreq(n, device=device) * n
+    kx = torch.fft.rfftfreq(n, device=device) * n
+    for i in range(n):          # one z plane at a time keeps the amplitude array small
+        k2 = kz[i] ** 2 + kz[:, None] ** 2 + kx[None, :] ** 2
+        amp = k2.clamp_min(1e-30) ** (-11.0 / 12.0)
+        if i == 0:
+            amp[0, 0] = 0.0
+        wk[i] *= amp
+    f = torch.fft.irfftn(wk, s=(n, n, n))
+    del wk
+    f -= f.mean()
+    f /= f.std()
+    mu = float(np.log(mean) - 0.5 * sigma_ln * sigma_ln)
+    f = torch.exp(mu + sigma_ln * f)
+    f *= mean / float(f.double().mean())
+    levels, ijks, rhos = [], [], []
+    refined = None
+    x = f[None, None]
+    for l in range(base_level, lmax + 1):
+        b = 1 << (lmax - l)
+        m = torch.nn.functional.avg_pool3d(x, b)[0, 0] if b > 1 else f
+        if refined is None:
+            exists = torch.ones_like(m, dtype=torch.bool)
+        else:
+            exists = refined.repeat_interleave(2, 0).repeat_interleave(2, 1).repeat_interleave(2, 2)
+        split = exists & (m > thresholds[l - base_level]) if l < lmax else torch.zeros_like(exists)
+        leaf = exists & ~split
+        idx = torch.nonzero(leaf)
+        levels.append(np.full(idx.shape[0], l, dtype=np.int8))
+        ijks.append(idx.flip(1).to(torch.int32).cpu().numpy())
+        rhos.append(m[leaf].float().cpu().numpy())
+        refined = split
+    return dict(level=np.concatenate(levels), ijk=np.concatenate(ijks), rho=np.concatenate(rhos),
+                base=base_level, lmax=lmax)
