@@ -46,6 +46,7 @@ extern "C" {
 
 typedef struct cd_tree_s *cd_tree;
 typedef struct cd_geom_s *cd_geom;
+typedef struct cd_batch_s *cd_batch;
 
 typedef enum {
     CD_OK = 0,
@@ -153,6 +154,30 @@ cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs,
  * Scratch (per-level partial sums) is owned by the tree and reused. */
 cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts, float *n_h, float *a_v,
                             float *shield, void *stream);
+
+/* Batched evaluation of n independent boxes (trees of any kind and size,
+ * each with its own geometry and outputs, all with the same opts): the boxes
+ * one after another on `stream`.  Entries of n_h / a_v / shield may be NULL;
+ * the arrays themselves may be NULL when no box wants that output. */
+cd_status cd_column_density_batch(int n, const cd_tree *trees, const cd_geom *geoms, const cd_opts *opts,
+                                  float *const *n_h, float *const *a_v, float *const *shield, void *stream);
+
+/* A batch captured once into a single CUDA graph.  cd_batch_create evaluates
+ * the batch eagerly to tune it (the number W of concurrent branches in
+ * {1, 2, 4, 8}, boxes placed largest first on the least loaded branch), then
+ * captures every box's kernels on W forked streams; it synchronises and
+ * returns with the outputs of one evaluation.  cd_batch_run launches the graph
+ * on `stream`: one launch evaluates every box with its tree's current
+ * densities (cd_tree_update between runs is seen).  The trees, geometries and
+ * output buffers given at creation must stay alive and must not be resized
+ * until cd_batch_free.  Creation must not happen while `stream` is capturing. */
+cd_status cd_batch_create(int n, const cd_tree *trees, const cd_geom *geoms, const cd_opts *opts, float *const *n_h,
+                          float *const *a_v, float *const *shield, void *stream, cd_batch *out);
+cd_status cd_batch_run(cd_batch batch, void *stream);
+/* Chosen branch count, eager milliseconds measured for W = 1, 2, 4, 8 (-1 where
+ * not tried; any pointer may be NULL) and kernel launches one run contains. */
+cd_status cd_batch_info(cd_batch batch, int *width, double *ms_tried, int64_t *kernel_nodes);
+void cd_batch_free(cd_batch batch);
 
 /* Same evaluation as cd_column_density (FP32, uniform trees), but its scratch
  * lives in a fixed 16 MiB device array compiled into the library, so the call

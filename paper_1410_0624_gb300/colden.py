@@ -27,6 +27,7 @@ EXPORTS = (
     "cd_opts_default", "cd_build_tree_uniform", "cd_build_tree_amr", "cd_tree_update", "cd_precompute_geometry",
     "cd_column_density", "cd_tree_info", "cd_tree_leaves", "cd_geom_info", "cd_stats_reset", "cd_stats_get",
     "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_column_density_noalloc", "cd_device_status",
+    "cd_column_density_batch", "cd_batch_create", "cd_batch_run", "cd_batch_info", "cd_batch_free",
 )
 K_RESTRICT, K_SHELL, K_LEAF, K_OTHER = 0, 1, 2, 3
 
@@ -74,6 +75,12 @@ def load(build_if_missing: bool = False):
     L.cd_column_density.argtypes = [P, P, ctypes.POINTER(Opts), P, P, P, P]
     L.cd_column_density_noalloc.argtypes = [P, P, ctypes.POINTER(Opts), P, P, P, P]
     L.cd_device_status.argtypes = [P]
+    L.cd_column_density_batch.argtypes = [I, P, P, ctypes.POINTER(Opts), P, P, P, P]
+    L.cd_batch_create.argtypes = [I, P, P, ctypes.POINTER(Opts), P, P, P, P, ctypes.POINTER(P)]
+    L.cd_batch_run.argtypes = [P, P]
+    L.cd_batch_info.argtypes = [P, ctypes.POINTER(I), P, ctypes.POINTER(I64)]
+    L.cd_batch_free.argtypes = [P]
+    L.cd_batch_free.restype = None
     L.cd_tree_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I64)]
     L.cd_tree_leaves.argtypes = [P, P, P]
     L.cd_geom_info.argtypes = [P, ctypes.POINTER(I), P]
@@ -84,7 +91,8 @@ def load(build_if_missing: bool = False):
     L.cd_last_error.argtypes = []
     L.cd_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("cd_opts_default", "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_stats_reset"):
+        if name not in ("cd_opts_default", "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_stats_reset",
+                        "cd_batch_free"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -294,3 +302,66 @@ def column_density_noalloc(tree: Tree, geom: Geometry, n_h=None, a_v=None, shiel
     _check(load().cd_column_density_noalloc(tree.handle, geom.handle, ctypes.byref(o), _dptr(n_h), _dptr(a_v),
                                             _dptr(shield), ctypes.c_void_p(_stream_ptr(stream))))
     return n_h, a_v, shield
+
+
+def _ptr_array(items, get):
+    arr = (ctypes.c_void_p * len(items))()
+    for i, x in enumerate(items):
+        arr[i] = get(x)
+    return arr
+
+
+def _out_array(ts, n):
+    if ts is None:
+        return None
+    return _ptr_array(ts, lambda t: _dptr(t) if t is not None else None)
+
+
+def column_density_batch(trees, geoms, n_h=None, a_v=None, shield=None, precision: int = FP32,
+                         av_per_nh: float = 1.0 / 1.87e21, shield_k: float = 2.5, stream=None):
+    """cd_column_density_batch: the boxes one after another (per-box launches)."""
+    n = len(trees)
+    o = opts_default()
+    o.precision, o.av_per_nh, o.shield_k = int(precision), float(av_per_nh), float(shield_k)
+    _check(load().cd_column_density_batch(n, _ptr_array(trees, lambda t: t.handle.value),
+                                          _ptr_array(geoms, lambda g: g.handle.value), ctypes.byref(o),
+                                          _out_array(n_h, n), _out_array(a_v, n), _out_array(shield, n),
+                                          ctypes.c_void_p(_stream_ptr(stream))))
+
+
+class Batch:
+    """cd_batch: the boxes captured once into one CUDA graph (see include/colden.h)."""
+
+    def __init__(self, trees, geoms, n_h=None, a_v=None, shield=None, precision: int = FP32,
+                 av_per_nh: float = 1.0 / 1.87e21, shield_k: float = 2.5, stream=None):
+        self._keep = (list(trees), list(geoms), n_h, a_v, shield)
+        n = len(trees)
+        o = opts_default()
+        o.precision, o.av_per_nh, o.shield_k = int(precision), float(av_per_nh), float(shield_k)
+        h = ctypes.c_void_p()
+        _check(load().cd_batch_create(n, _ptr_array(trees, lambda t: t.handle.value),
+                                      _ptr_array(geoms, lambda g: g.handle.value), ctypes.byref(o),
+                                      _out_array(n_h, n), _out_array(a_v, n), _out_array(shield, n),
+                                      ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
+        self._h = h
+
+    def run(self, stream=None):
+        _check(load().cd_batch_run(self._h, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def info(self):
+        w, nodes = ctypes.c_int(), ctypes.c_int64()
+        ms = (ctypes.c_double * 4)()
+        _check(load().cd_batch_info(self._h, ctypes.byref(w), ms, ctypes.byref(nodes)))
+        return {"width": w.value, "ms_tried": {W: ms[i] for i, W in enumerate((1, 2, 4, 8)) if ms[i] >= 0},
+                "kernel_nodes": nodes.value}
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().cd_batch_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
