@@ -18,6 +18,10 @@ Recipes (numpy PCG64, seed s):
     the way the paper's runs refine on density.
   * ``sphere``: the uniform spherical cloud of §4.1 (n_in inside radius R,
     n_out elsewhere) sampled at cell centres.
+  * ``mlp_init`` / ``mlp_inputs``: seeded initial weights of the learned
+    correction's network (uniform in +-1/sqrt(fan_in), packed W1 b1 W2 b2 W3
+    b3) and seeded stand-in input rows, so that both sides start from the same
+    numbers.
 Arrays are float32 and indexed [z, y, x] (x fastest).
 """
 from __future__ import annotations
@@ -111,6 +115,75 @@ def amr_leaves(fine: np.ndarray, base_level: int, thresholds) -> dict:
                 rho=np.concatenate(rhos), base=base_level, lmax=lmax)
 
 
+def _grf_torch(n: int, seed: int, device):
+    """The field g of ``gaussian_random_field`` drawn from a seeded
+    torch.Generator on ``device`` (zero mean, unit variance)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    w = torch.randn((n, n, n), generator=g, device=device, dtype=torch.float32)
+    wk = torch.fft.rfftn(w)
+    del w
+    kz = torch.fft.fftfreq(n, device=device) * n
+    kx = torch.fft.rfftfreq(n, device=device) * n
+    for i in range(n):          # one z plane at a time keeps the amplitude array small
+        k2 = kz[i] ** 2 + kz[:, None] ** 2 + kx[None, :] ** 2
+        amp = k2.clamp_min(1e-30) ** (-11.0 / 12.0)
+        if i == 0:
+            amp[0, 0] = 0.0
+        wk[i] *= amp
+    f = torch.fft.irfftn(wk, s=(n, n, n))
+    del wk
+    f -= f.mean()
+    f /= f.std()
+    return f
+
+
+def _lognormal_torch(f, mean: float, sigma_ln: float):
+    import torch
+    mu = float(np.log(mean) - 0.5 * sigma_ln * sigma_ln)
+    f = torch.exp(mu + sigma_ln * f)
+    f *= mean / float(f.double().mean())
+    return f
+
+
+def lognormal_grf_torch(n: int, mean: float, sigma_ln: float, seed: int, device="cuda"):
+    """The recipe of ``lognormal_grf`` with torch on a GPU, for sizes numpy
+    handles slowly (512^3).  Returns a float32 torch tensor [z, y, x] on
+    ``device``.  Deterministic for a given device type."""
+    return _lognormal_torch(_grf_torch(n, seed, device), mean, sigma_ln)
+
+
+def amr_leaves_grf_torch(lmax: int, base_level: int, thresholds, mean: float, sigma_ln: float, seed: int,
+                         device="cuda") -> dict:
+    """The recipe of ``lognormal_grf`` + ``amr_leaves`` at sizes numpy cannot
+    hold comfortably (a 1024^3 finest field), generated with torch on a GPU
+    from a seeded torch.Generator.  Deterministic for a given device type."""
+    import torch
+    f = lognormal_grf_torch(1 << lmax, mean, sigma_ln, seed, device)
+    levels, ijks, rhos = [], [], []
+    refined = None  # boolean mask of refined cells at the current level
+    for l in range(base_level, lmax + 1):
+        m = _block_mean(fine, 1 << (lmax - l))
+        n = 1 << l
+        if refined is None:
+            exists = np.ones((n, n, n), dtype=bool)
+        else:
+            exists = np.repeat(np.repeat(np.repeat(refined, 2, 0), 2, 1), 2, 2)
+        if l < lmax:
+            split = exists & (m > thresholds[l - base_level])
+        else:
+            split = np.zeros_like(exists)
+        leaf = exists & ~split
+        z, y, x = np.nonzero(leaf)
+        levels.append(np.full(z.shape[0], l, dtype=np.int8))
+        ijks.append(np.stack([x, y, z], axis=1).astype(np.int32))
+        rhos.append(m[leaf].astype(np.float32))
+        refined = split
+    return dict(level=np.concatenate(levels), ijk=np.concatenate(ijks),
+                rho=np.concatenate(rhos), base=base_level, lmax=lmax)
+
+
 def amr_leaves_grf_torch(lmax: int, base_level: int, thresholds, mean: float, sigma_ln: float, seed: int,
                          device="cuda") -> dict:
     """The recipe of ``lognormal_grf`` + ``amr_leaves`` at sizes numpy cannot
@@ -157,3 +230,25 @@ def amr_leaves_grf_torch(lmax: int, base_level: int, thresholds, mean: float, si
         refined = split
     return dict(level=np.concatenate(levels), ijk=np.concatenate(ijks), rho=np.concatenate(rhos),
                 base=base_level, lmax=lmax)
+
+
+def mlp_init(n_dir: int, hidden: int, seed: int, out_scale: float = 1.0, slots: int = 8) -> np.ndarray:
+    """Seeded initial parameters of the learned correction's network, packed
+    W1 [hidden, slots*n_dir+1], b1, W2 [hidden, hidden], b2, W3 [n_dir, hidden],
+    b3; every entry U(-1/sqrt(fan_in), 1/sqrt(fan_in)), the last layer scaled
+    by out_scale.  float32."""
+    rng = np.random.default_rng(seed)
+    n_in = slots * n_dir + 1
+    parts = []
+    for rows, fan_in, scale in ((hidden, n_in, 1.0), (hidden, hidden, 1.0), (n_dir, hidden, out_scale)):
+        b = 1.0 / np.sqrt(fan_in)
+        parts.append(rng.uniform(-b, b, size=rows * fan_in) * scale)
+        parts.append(rng.uniform(-b, b, size=rows) * scale)
+    return np.concatenate(parts).astype(np.float32)
+
+
+def mlp_inputs(n: int, n_in: int, seed: int, centre: float = 42.0, spread: float = 3.0) -> np.ndarray:
+    """Seeded stand-in input rows [n, n_in] (float32) with the scale of log
+    column densities in cm^-2: N(centre, spread^2) per entry."""
+    rng = np.random.default_rng(seed)
+    return (centre + spread * rng.standard_normal((n, n_in))).astype(np.float32)
