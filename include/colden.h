@@ -62,11 +62,11 @@ enum {
     CD_DIRS_HEALPIX = 0,   /* HEALPix ring-scheme pixel centres (Gorski et al. 2005): p0 = Nside, 12 Nside^2 dirs */
     CD_DIRS_MXN = 1,       /* the paper's equal-area set: p0 = M, p1 = N; theta_m = arccos(1 + (1-2m)/M),
                               phi_n = 2 pi (n-1)/N, direction index (m-1) N + (n-1) */
-    CD_DIRS_AXES = 2,      /* the six-ray set of §4.4: +x, -x, +y, -y, +z, -z */
+    CD_DIRS_AXES = 2,      /* the six-ray set of §4.3: +x, -x, +y, -y, +z, -z */
     CD_DIRS_CUSTOM = 3     /* caller's list of n_custom vectors (normalised by the library) */
 };
 
-/* Reference point of the external rays (§3.3 vs §4.4). */
+/* Reference point of the external rays (§3.3 vs §4.3). */
 enum {
     CD_MODE_PREC = 0,      /* precalculation module, two-level approximation: the shell at level l is seen from
                               the centre of the target's ancestor at level min(l+2, l0-1) */
@@ -84,7 +84,7 @@ typedef struct {
     int reserved0;
     double av_per_nh;      /* A_V = N_H * av_per_nh; default 1 / 1.87e21 cm^2 */
     double shield_k;       /* shield = <exp(-shield_k A_V)>; default 2.5 */
-    const void *net;       /* reserved for the learned correction; NULL */
+    const void *net;       /* NULL, or a cd_net (colden_learned.h): the learned correction */
 } cd_opts;
 
 /* Fills *o with the defaults above. */
@@ -151,7 +151,10 @@ cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs,
  *   a_v[t * n_dir + d]   N_H * av_per_nh (or NULL)
  *   shield[t]            (1/n_dir) sum_d exp(-shield_k * A_V) (or NULL)
  * All three are caller-owned DEVICE buffers.  opts may be NULL (defaults).
- * Scratch (per-level partial sums) is owned by the tree and reused. */
+ * Scratch (per-level partial sums) is owned by the tree and reused.
+ * With opts->net set, N_H is the learned form N_tree exp(delta) of
+ * colden_learned.h (uniform trees; the network's n_dir must equal the
+ * geometry's, else CD_EINVAL; an AMR tree returns CD_EUNSUPPORTED). */
 cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts, float *n_h, float *a_v,
                             float *shield, void *stream);
 
@@ -226,7 +229,10 @@ enum {
     CD_K_SHELL = 1,        /* shell contraction of one level (FP32 or tensor core) */
     CD_K_LEAF = 2,         /* per-leaf combine + epilogue */
     CD_K_OTHER = 3,        /* geometry precompute and the rest */
-    CD_K_COUNT = 4
+    CD_K_NET = 4,          /* the learned correction's network (FP32 GEMMs, fused tensor-core inference, Adam) */
+    CD_K_FEATURES = 5,     /* per-level inputs of the network and the learned combine */
+    CD_K_RAYMARCH = 6,     /* exact ray-marcher */
+    CD_K_COUNT = 7
 };
 /* Resets the counters; with timing != 0 later launches also record CUDA
  * events on their stream (a synchronisation happens in cd_stats_get). */

@@ -26,7 +26,7 @@ _lock = threading.Lock()
 _lib = None
 
 MODE_PREC = 0     # two-level approximation of the precalculation module (§3.3)
-MODE_INSITU = 1   # every contribution from the oct centre, no approximation (§4.4)
+MODE_INSITU = 1   # every contribution from the oct centre, no approximation (§4.3)
 
 # Extinction constants of the hot path: A_V = N_H / 1.87e21 cm^-2 and the
 # screening factor <exp(-2.5 A_V)>; the paper's own attenuation uses
@@ -85,7 +85,7 @@ def _p(a: np.ndarray):
 
 
 # ----------------------------------------------------------------------------
-# Directions (§3.2 eqs. theta and phi; §4.4 six rays; HEALPix, Gorski et al. 2005)
+# Directions (§3.2 eqs. theta and phi; §4.3 six rays; HEALPix, Gorski et al. 2005)
 # ----------------------------------------------------------------------------
 
 def dirs_mxn(M: int, N: int) -> np.ndarray:
@@ -103,7 +103,7 @@ def dirs_healpix(nside: int) -> np.ndarray:
 
 
 def dirs_axes() -> np.ndarray:
-    """The six-ray set +x, -x, +y, -y, +z, -z (§4.4)."""
+    """The six-ray set +x, -x, +y, -y, +z, -z (§4.3)."""
     out = np.zeros((6, 3))
     lib().or_dirs_axes(_p(out))
     return out

@@ -12,7 +12,7 @@
  *     field over that cell (the coarse-level density "corresponds to a mean",
  *     §3.2); a region inside a coarser leaf takes that leaf's value;
  *   - directions: the equal-area M x N set (§3.2, eqs. theta/phi), HEALPix ring
- *     pixel centres (Gorski et al. 2005), the six axis rays (§4.4), or a list;
+ *     pixel centres (Gorski et al. 2005), the six axis rays (§4.3), or a list;
  *   - for every target leaf t at level l0 and direction d, the column
  *     N(m,n) = sum_i n_i dx_i(m,n)  (Eq. N_discret1):
  *       internal + local: a ray from the centre of t through t and its seven
@@ -24,7 +24,7 @@
  *         the others), each weighted by the length of a ray from the reference
  *         point p_ref(l) through it.  p_ref(l) is the centre of
  *         A_{min(l+2, l0-1)} under the two-level approximation of §3.3, and the
- *         centre of A_{l0-1} (the oct centre) in the in-situ variant of §4.4.
+ *         centre of A_{l0-1} (the oct centre) in the in-situ variant of §4.3.
  *     The oracle loops over the cells of each shell directly: no table, no
  *     GEMM, no sharing between targets.
  *   - the brute-force reference: an exact line integral of the leaf field from
@@ -108,7 +108,7 @@ int or_dirs_healpix(int nside, double *out)
     return p;
 }
 
-/* The six-ray set of §4.4: +x, -x, +y, -y, +z, -z. */
+/* The six-ray set of §4.3: +x, -x, +y, -y, +z, -z. */
 int or_dirs_axes(double *out)
 {
     static const double ax[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0},

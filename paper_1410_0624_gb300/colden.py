@@ -28,14 +28,25 @@ EXPORTS = (
     "cd_column_density", "cd_tree_info", "cd_tree_leaves", "cd_geom_info", "cd_stats_reset", "cd_stats_get",
     "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_column_density_noalloc", "cd_device_status",
     "cd_column_density_batch", "cd_batch_create", "cd_batch_run", "cd_batch_info", "cd_batch_free",
+    # include/colden_learned.h
+    "cd_adam_default", "cd_net_num_params", "cd_raymarch", "cd_learned_features", "cd_learned_targets",
+    "cd_net_create", "cd_net_fit_normaliser", "cd_net_forward", "cd_net_loss_grad", "cd_net_train_step",
+    "cd_net_get_state", "cd_net_set_state", "cd_net_info", "cd_net_free",
 )
-K_RESTRICT, K_SHELL, K_LEAF, K_OTHER = 0, 1, 2, 3
+_VOID = ("cd_opts_default", "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_stats_reset", "cd_batch_free",
+         "cd_adam_default", "cd_net_free", "cd_net_num_params")
+K_RESTRICT, K_SHELL, K_LEAF, K_OTHER, K_NET, K_FEATURES, K_RAYMARCH = 0, 1, 2, 3, 4, 5, 6
 
 
 class ColdenError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("%s: %s" % (_STATUS.get(code, code), msg))
         self.code = code
+
+
+class Adam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double)]
 
 
 class Opts(ctypes.Structure):
@@ -90,9 +101,25 @@ def load(build_if_missing: bool = False):
     L.cd_geom_free.restype = None
     L.cd_last_error.argtypes = []
     L.cd_last_error.restype = ctypes.c_char_p
+    L.cd_adam_default.argtypes = [ctypes.POINTER(Adam)]
+    L.cd_adam_default.restype = None
+    L.cd_net_num_params.argtypes = [I, I]
+    L.cd_net_num_params.restype = I64
+    L.cd_raymarch.argtypes = [P, P, I64, P, P, P]
+    L.cd_learned_features.argtypes = [P, P, I64, P, P, P, P]
+    L.cd_learned_targets.argtypes = [I64, P, P, P, P]
+    L.cd_net_create.argtypes = [I, I, P, ctypes.POINTER(P)]
+    L.cd_net_fit_normaliser.argtypes = [P, I64, P, P]
+    L.cd_net_forward.argtypes = [P, I64, P, P, P]
+    L.cd_net_loss_grad.argtypes = [P, I64, P, P, P, P, P, P]
+    L.cd_net_train_step.argtypes = [P, I64, P, P, P, ctypes.POINTER(Adam), P, P]
+    L.cd_net_get_state.argtypes = [P, P, P, P, P, P, ctypes.POINTER(I64)]
+    L.cd_net_set_state.argtypes = [P, P, P, P, P, P, I64]
+    L.cd_net_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I64)]
+    L.cd_net_free.argtypes = [P]
+    L.cd_net_free.restype = None
     for name in EXPORTS:
-        if name not in ("cd_opts_default", "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_stats_reset",
-                        "cd_batch_free"):
+        if name not in _VOID:
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -278,9 +305,11 @@ def precompute_geometry(scheme="healpix", p0: int = 1, p1: int = 0, dirs=None, m
 
 
 def column_density(tree: Tree, geom: Geometry, n_h=None, a_v=None, shield=None, precision: int = FP32,
-                   av_per_nh: float = 1.0 / 1.87e21, shield_k: float = 2.5, stream=None):
-    """cd_column_density into caller-owned CUDA float32 tensors (any may be None)."""
+                   av_per_nh: float = 1.0 / 1.87e21, shield_k: float = 2.5, net=None, stream=None):
+    """cd_column_density into caller-owned CUDA float32 tensors (any may be
+    None).  net: a Net for the learned form."""
     o = opts_default()
+    o.net = net.handle.value if net is not None else None
     o.precision = int(precision)
     o.av_per_nh = float(av_per_nh)
     o.shield_k = float(shield_k)
@@ -365,3 +394,157 @@ class Batch:
             self.free()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Learned correction (include/colden_learned.h)
+# ---------------------------------------------------------------------------
+
+SLOTS = 8
+
+
+def _iptr(t):
+    """Device pointer of an int64 CUDA tensor (or None)."""
+    if t is None:
+        return None
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and t.dtype == torch.int64
+    return t.data_ptr()
+
+
+def net_num_params(n_dir: int, hidden: int) -> int:
+    return int(load().cd_net_num_params(int(n_dir), int(hidden)))
+
+
+def adam_default() -> Adam:
+    a = Adam()
+    load().cd_adam_default(ctypes.byref(a))
+    return a
+
+
+def raymarch(tree: Tree, geom: Geometry, n_ray, leaves=None, stream=None):
+    """cd_raymarch: exact columns [n, n_dir] from the centres of `leaves`
+    (int64 CUDA tensor, or None for the first n_ray.shape[0] leaves)."""
+    n = n_ray.shape[0]
+    _check(load().cd_raymarch(tree.handle, geom.handle, n, _iptr(leaves), _dptr(n_ray),
+                              ctypes.c_void_p(_stream_ptr(stream))))
+    return n_ray
+
+
+def learned_features(tree: Tree, geom: Geometry, x, n_tree=None, leaves=None, stream=None):
+    """cd_learned_features: network inputs x [n, 8 n_dir + 1] and (optionally)
+    the plain column n_tree [n, n_dir] of `leaves` (None: the first n)."""
+    n = x.shape[0]
+    _check(load().cd_learned_features(tree.handle, geom.handle, n, _iptr(leaves), _dptr(x), _dptr(n_tree),
+                                      ctypes.c_void_p(_stream_ptr(stream))))
+    return x, n_tree
+
+
+def learned_targets(n_ray, n_tree, y, stream=None):
+    """cd_learned_targets: y = ln(n_ray / n_tree)."""
+    _check(load().cd_learned_targets(n_ray.numel(), _dptr(n_ray), _dptr(n_tree), _dptr(y),
+                                     ctypes.c_void_p(_stream_ptr(stream))))
+    return y
+
+
+class Net:
+    """cd_net: the learned correction's network (weights on the device)."""
+
+    def __init__(self, n_dir: int, hidden: int, params):
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        if p.size != net_num_params(n_dir, hidden):
+            raise ValueError("expected %d parameters, got %d" % (net_num_params(n_dir, hidden), p.size))
+        h = ctypes.c_void_p()
+        _check(load().cd_net_create(int(n_dir), int(hidden), p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)))
+        self._h = h
+        self.n_dir, self.hidden = int(n_dir), int(hidden)
+        self.n_params = p.size
+        self.n_in = SLOTS * self.n_dir + 1
+
+    @property
+    def handle(self):
+        return self._h
+
+    def fit_normaliser(self, x, stream=None):
+        _check(load().cd_net_fit_normaliser(self._h, x.shape[0], _dptr(x), ctypes.c_void_p(_stream_ptr(stream))))
+
+    def forward(self, x, delta, stream=None):
+        _check(load().cd_net_forward(self._h, x.shape[0], _dptr(x), _dptr(delta),
+                                     ctypes.c_void_p(_stream_ptr(stream))))
+        return delta
+
+    def loss_grad(self, x, y, loss, grad=None, rows=None, batch=None, stream=None):
+        B = int(batch if batch is not None else (rows.numel() if rows is not None else x.shape[0]))
+        _check(load().cd_net_loss_grad(self._h, B, _dptr(x), _dptr(y), _iptr(rows), _dptr(loss), _dptr(grad),
+                                       ctypes.c_void_p(_stream_ptr(stream))))
+
+    def train_step(self, x, y, rows=None, batch=None, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, loss=None,
+                   stream=None):
+        B = int(batch if batch is not None else (rows.numel() if rows is not None else x.shape[0]))
+        hp = Adam(float(lr), float(beta1), float(beta2), float(eps))
+        _check(load().cd_net_train_step(self._h, B, _dptr(x), _dptr(y), _iptr(rows), ctypes.byref(hp),
+                                        _dptr(loss), ctypes.c_void_p(_stream_ptr(stream))))
+
+    def state(self) -> dict:
+        """Checkpoint of the whole state (host numpy arrays)."""
+        P, I = self.n_params, self.n_in
+        out = {k: np.zeros(n, dtype=np.float32) for k, n in
+               (("params", P), ("mu", I), ("sinv", I), ("adam_m", P), ("adam_v", P))}
+        step = ctypes.c_int64()
+        c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(load().cd_net_get_state(self._h, c(out["params"]), c(out["mu"]), c(out["sinv"]), c(out["adam_m"]),
+                                       c(out["adam_v"]), ctypes.byref(step)))
+        out["step"] = step.value
+        return out
+
+    def load_state(self, st: dict):
+        arr = {k: np.ascontiguousarray(st[k], dtype=np.float32) for k in ("params", "mu", "sinv", "adam_m", "adam_v")}
+        c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(load().cd_net_set_state(self._h, c(arr["params"]), c(arr["mu"]), c(arr["sinv"]), c(arr["adam_m"]),
+                                       c(arr["adam_v"]), int(st.get("step", 0))))
+
+    def save(self, path: str):
+        np.savez(path, n_dir=self.n_dir, hidden=self.hidden, **self.state())
+
+    @classmethod
+    def load(cls, path: str) -> "Net":
+        z = np.load(path)
+        net = cls(int(z["n_dir"]), int(z["hidden"]), z["params"])
+        net.load_state({k: z[k] for k in z.files})
+        return net
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().cd_net_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def train(net: Net, x, y, steps: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0, lr_final: float = None,
+          stream=None):
+    """Adam training loop over the rows of (x, y) (CUDA tensors): a seeded
+    permutation per epoch, minibatches of `batch` rows, optional cosine decay
+    of the step size to lr_final.  Returns the per-step loss (host array).
+    Orchestration only: every step is cd_net_train_step."""
+    import math
+    import torch
+    n = x.shape[0]
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    loss = torch.zeros(steps, device=x.device, dtype=torch.float32)
+    perm = None
+    pos = n
+    for it in range(steps):
+        if pos + batch > n:
+            perm = torch.randperm(n, generator=g).to(device=x.device, dtype=torch.int64)
+            pos = 0
+        rows = perm[pos:pos + min(batch, n)]
+        pos += batch
+        cur = lr if lr_final is None else lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * it / steps))
+        net.train_step(x, y, rows=rows, lr=cur, loss=loss[it:it + 1], stream=stream)
+    return loss.cpu().numpy()

@@ -10,12 +10,13 @@
 //   3. leaves: N_H = E[oct] + S_{L-2}[parent oct] + internal + local, then A_V
 //      and the shield.
 // Every shell l = 1 .. L-1 enters exactly once (Eq. N_discret).
+#include <atomic>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
 #include <math.h>
 
-#include "common.cuh"
+#include "learned.cuh"
 
 namespace cd {
 
@@ -212,6 +213,7 @@ cd_status cd_tree_update(cd_tree t, const float *rho, int rho_on_device, void *s
     }
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t N = t->n_leaf;
+    ++t->rho_version;
     const auto apply = [&](const float *dev) { return t->amr ? update_amr(t, dev, s) : restrict_uniform(t, dev, s); };
     if (rho_on_device) return apply(rho);
     for (int64_t i = 0; i < N; ++i)
@@ -264,6 +266,8 @@ cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs,
     }
     cudaStream_t s = (cudaStream_t)stream;
     cd_geom g = new cd_geom_s();
+    static std::atomic<int64_t> next_uid{1};
+    g->uid = next_uid++;
     cudaGetDevice(&g->dev);
     g->n_dir = nd;
     g->mode = mode;
@@ -310,12 +314,9 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
         set_error("unknown precision %d", opts.precision);
         return CD_EINVAL;
     }
-    if (opts.net) {
-        set_error("learned correction not available");
-        return CD_EUNSUPPORTED;
-    }
     if (!n_h && !a_v && !shield) return CD_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    if (opts.net) return column_density_learned(tree, geom, opts, n_h, a_v, shield, s);
     if (tree->amr) return column_density_amr(tree, geom, opts, n_h, a_v, shield, s);
     const int nd = geom->n_dir, L = tree->L;
     cd_status st = ensure_workspace(tree, nd);
@@ -427,6 +428,7 @@ void cd_tree_free(cd_tree t)
     if (!t) return;
     cudaDeviceSynchronize();
     free_workspace(t);
+    free_level_sums(t);
     for (int l = 0; l <= CD_MAXL; ++l) {
         if (t->rho_lvl[l]) cudaFree(t->rho_lvl[l]);
         if (t->rho_brick[l]) cudaFree(t->rho_brick[l]);

@@ -82,6 +82,16 @@ struct Workspace {
     float *E = nullptr;          // external column of every oct, Morton order, [n_oct][ndir]
 };
 
+// The learned form's per-level sums (learned.cu): every shell kept apart.
+struct LevelSums {
+    int ndir = 0;
+    int64_t geom_uid = 0, rho_version = -1;   // what the sums were computed for
+    float *C[CD_MAXL + 1] = {};   // shell of level k-2 seen from level-k cells, no prefix, [8^k][ndir]
+    float *Et[4] = {};            // oct level, table t alone (shell of level L-t), [n_oct][ndir]
+    float *x = nullptr, *n_tree = nullptr, *delta = nullptr;   // chunk buffers of the FP32 learned path
+    int64_t rows = 0;
+};
+
 }  // namespace cd
 
 struct cd_tree_s {
@@ -95,6 +105,8 @@ struct cd_tree_s {
     __nv_bfloat16 *rho_brick[CD_MAXL + 1] = {};  // BF16 copies in brick order (tensor path)
     float *rho_leaf = nullptr;          // leaf densities, Morton order
     cd::Workspace ws;
+    cd::LevelSums lv;
+    int64_t rho_version = 0;            // bumped by every density update
     int dev = 0;
     // AMR meshes (amr != 0); see amr.cu
     int64_t n_ref[CD_MAXL + 1] = {};      // refined cells of level k
@@ -114,6 +126,7 @@ struct cd_tree_s {
 };
 
 struct cd_geom_s {
+    int64_t uid = 0;                    // process-unique id (learned.cu caches per geometry)
     int n_dir = 0;
     int mode = 0;
     double *dirs_host = nullptr;        // n_dir x 3
@@ -147,6 +160,9 @@ class LaunchScope {
     cudaStream_t s_;
     cudaEvent_t a_ = nullptr, b_ = nullptr;
 };
+
+// learned.cu: frees the tree's LevelSums
+void free_level_sums(cd_tree t);
 
 // tree.cu
 cd_status restrict_uniform(cd_tree t, const float *rho_dev, cudaStream_t s);

@@ -1,0 +1,397 @@
+"""The learned correction through the C ABI against the FP64 oracle
+(oracle/learned.py, oracle.c's ray-marcher and per-level sums).
+
+Tolerances.
+  * Ray-marcher (FP32 DDA, boundaries recomputed per crossing): each crossing
+    time carries one or two roundings (2^-24 relative of t <= 1.8 * 2^L
+    cells), the segment differences telescope, and the FP32 sum of <= 3 * 2^L
+    positive terms adds <= 3 * 2^L * 2^-24 relative in the worst case
+    (~1e-5 at 512^3, ~1e-6 in practice): held to 2e-5 relative.
+  * Features: every slot is a sum of positive FP32 terms (<= 1e-5 relative,
+    as the plain FP32 path); ln is 1-Lipschitz in the relative error and
+    ln max(., floor) cannot enlarge it: x is held to 3e-5 absolute, N_tree to
+    1e-5 relative.
+  * Network (FP32 GEMMs, K <= 385): delta to 1e-4 absolute; gradients to
+    1e-4 of the largest component; the loss to 1e-5 relative.
+  * Learned N = N_tree exp(delta): relative error = error of N_tree + absolute
+    error of delta: held to 1e-4 relative; shield to 2e-5 absolute.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import learned as ol
+from paper_1410_0624_gb300 import colden, synth
+
+PC = synth.PC_CM
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    colden.load(build_if_missing=True)
+
+
+def _compact(v):
+    v = v.astype(np.uint64) & np.uint64(0x1249249249249249)
+    for sh, mask in ((2, 0x10c30c30c30c30c3), (4, 0x100f00f00f00f00f), (8, 0x1f0000ff0000ff),
+                     (16, 0x1f00000000ffff), (32, 0x1fffff)):
+        v = (v ^ (v >> np.uint64(sh))) & np.uint64(mask)
+    return v.astype(np.int64)
+
+
+def _ijk_of(m):
+    m = np.asarray(m, dtype=np.uint64)
+    return np.stack([_compact(m), _compact(m >> np.uint64(1)), _compact(m >> np.uint64(2))], axis=1)
+
+
+def _field(L, seed, sigma=2.0, mean=30.0):
+    if L >= 8:
+        return synth.lognormal_grf_torch(1 << L, mean, sigma, seed, device="cuda").contiguous()
+    return torch.from_numpy(synth.lognormal_grf(1 << L, mean, sigma, seed)).cuda()
+
+
+def _setup(L, seed, dirs=("healpix", 2, 0, None), box=10 * PC):
+    rho = _field(L, seed)
+    tree = colden.build_tree_uniform(rho, box)
+    geom = colden.precompute_geometry(dirs[0], dirs[1], dirs[2], dirs=dirs[3])
+    T = oracle.Tree.uniform(rho.cpu().numpy(), box)
+    return rho, tree, geom, T
+
+
+def _sample(n_leaf, k, seed):
+    rng = np.random.default_rng(seed)
+    m = rng.choice(n_leaf, size=min(k, n_leaf), replace=False)
+    m[:2] = [0, n_leaf - 1]                      # box corners
+    return np.sort(m)
+
+
+def _oracle_slots(T, L, dirs, m):
+    ijk = _ijk_of(m)
+    _, pl = T.column_density(dirs, np.full(len(m), L), ijk, per_level=L)
+    return ol.slots_from_levels(pl)
+
+
+# ---------------------------------------------------------------------------
+# Ray-marcher
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L,dset", [(4, ("healpix", 2, 0, None)), (5, ("axes", 0, 0, None)),
+                                    (7, ("healpix", 2, 0, None)), (9, ("healpix", 2, 0, None)),
+                                    (6, ("custom", 0, 0, np.random.default_rng(11).normal(size=(9, 3))))])
+def test_raymarch_matches_oracle(L, dset):
+    _, tree, geom, T = _setup(L, 40 + L, dset)
+    m = _sample(tree.n_leaf, 400 if L < 9 else 120, L)
+    out = torch.full((len(m), geom.n_dir), -1.0, device="cuda")
+    colden.raymarch(tree, geom, out, leaves=torch.from_numpy(m).cuda())
+    got = out.cpu().numpy().astype(np.float64)
+    want = T.raymarch(geom.dirs, np.full(len(m), L), _ijk_of(m))
+    assert np.all(want > 0)
+    assert np.max(np.abs(got - want) / want) < 2e-5
+
+
+def test_raymarch_uniform_density_is_distance_to_edge():
+    L, n0, box = 5, 3.0, 10 * PC
+    tree = colden.build_tree_uniform(torch.full((32, 32, 32), n0, device="cuda"), box)
+    geom = colden.precompute_geometry("healpix", 2)
+    out = torch.zeros((tree.n_leaf, geom.n_dir), device="cuda")
+    colden.raymarch(tree, geom, out)
+    got = out.cpu().numpy().astype(np.float64)
+    ijk = _ijk_of(np.arange(tree.n_leaf))
+    x0 = (ijk + 0.5) * box / 32
+    d = geom.dirs
+    with np.errstate(divide="ignore"):
+        tx = np.where(d[None, :, 0] > 0, (box - x0[:, None, 0]) / d[None, :, 0],
+                      np.where(d[None, :, 0] < 0, -x0[:, None, 0] / d[None, :, 0], np.inf))
+        ty = np.where(d[None, :, 1] > 0, (box - x0[:, None, 1]) / d[None, :, 1],
+                      np.where(d[None, :, 1] < 0, -x0[:, None, 1] / d[None, :, 1], np.inf))
+        tz = np.where(d[None, :, 2] > 0, (box - x0[:, None, 2]) / d[None, :, 2],
+                      np.where(d[None, :, 2] < 0, -x0[:, None, 2] / d[None, :, 2], np.inf))
+    want = n0 * np.minimum(np.minimum(tx, ty), tz)
+    assert np.max(np.abs(got - want) / want) < 2e-6
+
+
+# ---------------------------------------------------------------------------
+# Features
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L,k", [(3, 512), (5, 600), (8, 300), (9, 100)])
+def test_features_match_oracle(L, k):
+    rho, tree, geom, T = _setup(L, 60 + L)
+    m = _sample(tree.n_leaf, k, 100 + L)
+    nd = geom.n_dir
+    x = torch.full((len(m), 8 * nd + 1), -7.0, device="cuda")
+    nt = torch.full((len(m), nd), -7.0, device="cuda")
+    colden.learned_features(tree, geom, x, nt, leaves=torch.from_numpy(m).cuda())
+    slots = _oracle_slots(T, L, geom.dirs, m)
+    rho_m = rho.reshape(-1).cpu().numpy()        # row-major [z, y, x]
+    ijk = _ijk_of(m)
+    n_leaf_vals = rho_m[(ijk[:, 2] * (1 << L) + ijk[:, 1]) * (1 << L) + ijk[:, 0]]
+    want_x = ol.features(slots, n_leaf_vals)
+    want_nt = ol.tree_total(slots)
+    gx = x.cpu().numpy().astype(np.float64)
+    gnt = nt.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(gx - want_x)) < 3e-5
+    assert np.max(np.abs(gnt - want_nt) / want_nt) < 1e-5
+    # the plain method's column equals the sum of the slots
+    plain = torch.zeros(tree.n_leaf * nd, device="cuda")
+    colden.column_density(tree, geom, n_h=plain)
+    p = plain.reshape(-1, nd)[torch.from_numpy(m).cuda()].cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(p - gnt) / gnt) < 2e-5
+
+
+def test_features_see_tree_update():
+    rho, tree, geom, T = _setup(5, 71)
+    nd = geom.n_dir
+    x1 = torch.zeros((tree.n_leaf, 8 * nd + 1), device="cuda")
+    colden.learned_features(tree, geom, x1)
+    colden.tree_update(tree, rho * 2.0)
+    x2 = torch.zeros_like(x1)
+    colden.learned_features(tree, geom, x2)
+    d = (x2 - x1).cpu().numpy()
+    # every slot above the floor and ln n move by ln 2
+    above = x1.cpu().numpy() > np.log(1e16) + 1.0
+    assert np.allclose(d[above], np.log(2.0), atol=3e-5)
+
+
+# ---------------------------------------------------------------------------
+# Network: forward, gradient, Adam, checkpoint
+# ---------------------------------------------------------------------------
+
+def _net(nd=48, H=128, seed=1, scale=1.0):
+    p = synth.mlp_init(nd, H, seed, out_scale=scale)
+    return colden.Net(nd, H, p), p.astype(np.float64)
+
+
+@pytest.mark.parametrize("nd,H,n", [(48, 128, 1000), (12, 40, 77), (3, 5, 1)])
+def test_normaliser_and_forward_match_oracle(nd, H, n):
+    net, p = _net(nd, H)
+    x_np = synth.mlp_inputs(n, 8 * nd + 1, seed=nd + n)
+    x = torch.from_numpy(x_np).cuda()
+    net.fit_normaliser(x)
+    st = net.state()
+    mu, sinv = ol.normaliser(x_np.astype(np.float64))
+    assert np.allclose(st["mu"], mu, rtol=1e-6, atol=0)
+    assert np.allclose(st["sinv"], sinv, rtol=1e-5, atol=0)
+    delta = torch.zeros((n, nd), device="cuda")
+    net.forward(x, delta)
+    want, _ = ol.forward(ol.unpack(p, nd, H), mu, sinv, x_np.astype(np.float64))
+    assert np.max(np.abs(delta.cpu().numpy() - want)) < 1e-4
+
+
+def _batch(nd, B, seed):
+    x_np = synth.mlp_inputs(B, 8 * nd + 1, seed=seed)
+    y_np = (0.3 * np.random.default_rng(seed + 1).standard_normal((B, nd))).astype(np.float32)
+    return x_np, y_np
+
+
+@pytest.mark.parametrize("nd,H,B", [(48, 128, 300), (12, 40, 1), (48, 128, 5000)])
+def test_loss_gradient_match_oracle(nd, H, B):
+    net, p = _net(nd, H, seed=2)
+    x_np, y_np = _batch(nd, B, seed=B)
+    x, y = torch.from_numpy(x_np).cuda(), torch.from_numpy(y_np).cuda()
+    mu, sinv = ol.normaliser(x_np.astype(np.float64))
+    st = net.state()
+    st["mu"], st["sinv"] = mu.astype(np.float32), sinv.astype(np.float32)
+    net.load_state(st)
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.zeros(net.n_params, device="cuda")
+    net.loss_grad(x, y, loss, grad)
+    L_or, g_or = ol.loss_grad(ol.unpack(p, nd, H), st["mu"].astype(np.float64), st["sinv"].astype(np.float64),
+                              x_np.astype(np.float64), y_np.astype(np.float64))
+    g_or = ol.pack(g_or)
+    assert loss.item() == pytest.approx(L_or, rel=1e-5)
+    g = grad.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(g - g_or)) < 1e-4 * np.max(np.abs(g_or))
+    # repeatable to the bit
+    grad2 = torch.zeros_like(grad)
+    net.loss_grad(x, y, loss, grad2)
+    assert torch.equal(grad, grad2)
+
+
+def test_row_gather_equals_explicit_batch():
+    nd, H = 12, 32
+    net, _ = _net(nd, H, seed=3)
+    x_np, y_np = _batch(nd, 500, seed=9)
+    x, y = torch.from_numpy(x_np).cuda(), torch.from_numpy(y_np).cuda()
+    rows = torch.tensor([5, 499, 0, 17, 17, 250], device="cuda", dtype=torch.int64)
+    l1, g1 = torch.zeros(1, device="cuda"), torch.zeros(net.n_params, device="cuda")
+    net.loss_grad(x, y, l1, g1, rows=rows)
+    l2, g2 = torch.zeros(1, device="cuda"), torch.zeros(net.n_params, device="cuda")
+    net.loss_grad(x[rows].contiguous(), y[rows].contiguous(), l2, g2)
+    assert torch.equal(l1, l2) and torch.equal(g1, g2)
+
+
+def test_adam_steps_match_oracle():
+    nd, H, B = 48, 128, 256
+    net, p = _net(nd, H, seed=4)
+    x_np, y_np = _batch(nd, B, seed=44)
+    x, y = torch.from_numpy(x_np).cuda(), torch.from_numpy(y_np).cuda()
+    mu, sinv = ol.normaliser(x_np.astype(np.float64))
+    st = net.state()
+    st["mu"], st["sinv"] = mu.astype(np.float32), sinv.astype(np.float32)
+    net.load_state(st)
+    mu64, sinv64 = st["mu"].astype(np.float64), st["sinv"].astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    q = p.copy()
+    lr = 1e-3
+    for t in range(1, 4):
+        net.train_step(x, y, lr=lr)
+        _, g = ol.loss_grad(ol.unpack(q, nd, H), mu64, sinv64, x_np.astype(np.float64), y_np.astype(np.float64))
+        g = ol.pack(g)
+        q_new, m, v = ol.adam(q, g, m, v, t, lr)
+        got = net.state()["params"].astype(np.float64)
+        # parameters whose gradient is well above FP32 noise follow the oracle
+        sure = np.abs(g) > 1e-3 * np.max(np.abs(g))
+        assert np.max(np.abs(got - q_new)[sure]) < 2e-2 * lr * t
+        assert np.max(np.abs(got - q_new)) <= 7.0 * lr * t
+        q = q_new
+    assert net.state()["step"] == 3
+
+
+def test_checkpoint_roundtrip_and_resume(tmp_path):
+    nd, H = 12, 32
+    x_np, y_np = _batch(nd, 2048, seed=5)
+    x, y = torch.from_numpy(x_np).cuda(), torch.from_numpy(y_np).cuda()
+    a, _ = _net(nd, H, seed=6)
+    a.fit_normaliser(x)
+    la = colden.train(a, x, y, steps=20, batch=256, seed=1)
+    path = str(tmp_path / "net.npz")
+    a.save(path)
+    b = colden.Net.load(path)
+    sa, sb = a.state(), b.state()
+    for k in ("params", "mu", "sinv", "adam_m", "adam_v"):
+        assert np.array_equal(sa[k], sb[k])
+    assert sb["step"] == 20
+    # continuing both gives identical weights (training is deterministic)
+    colden.train(a, x, y, steps=5, batch=256, seed=2)
+    colden.train(b, x, y, steps=5, batch=256, seed=2)
+    assert np.array_equal(a.state()["params"], b.state()["params"])
+    assert np.all(np.isfinite(la)) and la[-1] < la[0]
+
+
+# ---------------------------------------------------------------------------
+# Learned column density (FP32) against the oracle chain
+# ---------------------------------------------------------------------------
+
+def _learned_case(L, seed, k, nd_set=("healpix", 2, 0, None)):
+    rho, tree, geom, T = _setup(L, seed, nd_set)
+    nd = geom.n_dir
+    net, p = _net(nd, 64, seed=seed, scale=0.2)
+    # the standardisation comes from the oracle's own features of a sample
+    ms = _sample(tree.n_leaf, 2000, seed + 1)
+    slots_s = _oracle_slots(T, L, geom.dirs, ms)
+    rho_m = rho.reshape(-1).cpu().numpy().astype(np.float64)
+    ij = _ijk_of(ms)
+    n_s = rho_m[(ij[:, 2] * (1 << L) + ij[:, 1]) * (1 << L) + ij[:, 0]]
+    mu, sinv = ol.normaliser(ol.features(slots_s, n_s))
+    st = net.state()
+    st["mu"], st["sinv"] = mu.astype(np.float32), sinv.astype(np.float32)
+    net.load_state(st)
+    n_h = torch.full((tree.n_leaf * nd,), -1.0, device="cuda")
+    sh = torch.full((tree.n_leaf,), -1.0, device="cuda")
+    colden.column_density(tree, geom, n_h=n_h, shield=sh, net=net)
+    torch.cuda.synchronize()
+    m = _sample(tree.n_leaf, k, seed + 2)
+    slots = _oracle_slots(T, L, geom.dirs, m)
+    ij = _ijk_of(m)
+    nv = rho_m[(ij[:, 2] * (1 << L) + ij[:, 1]) * (1 << L) + ij[:, 0]]
+    delta, _ = ol.forward(ol.unpack(p, nd, 64), st["mu"].astype(np.float64), st["sinv"].astype(np.float64),
+                          ol.features(slots, nv))
+    want = ol.apply(ol.tree_total(slots), delta)
+    got = n_h.reshape(-1, nd)[torch.from_numpy(m).cuda()].cpu().numpy().astype(np.float64)
+    got_sh = sh[torch.from_numpy(m).cuda()].cpu().numpy().astype(np.float64)
+    return got, want, got_sh, oracle.shield(want), delta
+
+
+@pytest.mark.parametrize("L,k", [(5, 800), (7, 400)])
+def test_learned_fp32_column_density_matches_oracle(L, k):
+    got, want, gsh, wsh, delta = _learned_case(L, 80 + L, k)
+    assert np.abs(delta).max() > 1e-3          # the correction is not trivially zero
+    assert np.max(np.abs(got - want) / want) < 1e-4
+    assert np.max(np.abs(gsh - wsh)) < 2e-5
+
+
+def test_learned_falls_back_to_tree_where_delta_is_not_finite():
+    L = 4
+    rho, tree, geom, T = _setup(L, 90)
+    nd = geom.n_dir
+    p = synth.mlp_init(nd, 16, 7)
+    lay = ol.shapes(nd, 16)
+    off_b3 = sum(int(np.prod(s)) for _, s in lay[:-1])
+    p[off_b3 + 3] = np.nan
+    p[off_b3 + 5] = np.inf
+    net = colden.Net(nd, 16, p)
+    n_h = torch.zeros(tree.n_leaf * nd, device="cuda")
+    colden.column_density(tree, geom, n_h=n_h, net=net)
+    plain = torch.zeros_like(n_h)
+    colden.column_density(tree, geom, n_h=plain)
+    g = n_h.reshape(-1, nd).cpu().numpy()
+    q = plain.reshape(-1, nd).cpu().numpy()
+    assert np.all(np.isfinite(g))
+    assert np.allclose(g[:, [3, 5]], q[:, [3, 5]], rtol=2e-5)
+    assert not np.allclose(g[:, 0], q[:, 0], rtol=1e-3)
+
+
+def test_learned_rejects_mismatched_directions_and_amr():
+    rho, tree, geom, T = _setup(4, 91)
+    net, _ = _net(12, 16)
+    with pytest.raises(colden.ColdenError) as e:
+        colden.column_density(tree, geom, n_h=torch.zeros(tree.n_leaf * geom.n_dir, device="cuda"), net=net)
+    assert e.value.code == colden.CD_EINVAL
+    a = synth.amr_leaves(synth.lognormal_grf(16, 30.0, 2.0, 5), 2, [20.0, 60.0])
+    amr = colden.build_tree_amr(a["base"], a["lmax"], 10 * PC, a["level"], a["ijk"], a["rho"])
+    net48, _ = _net(geom.n_dir, 16)
+    with pytest.raises(colden.ColdenError) as e:
+        colden.column_density(amr, geom, n_h=torch.zeros(amr.n_leaf * geom.n_dir, device="cuda"), net=net48)
+    assert e.value.code == colden.CD_EUNSUPPORTED
+    with pytest.raises(colden.ColdenError) as e:
+        colden.raymarch(amr, geom, torch.zeros((4, geom.n_dir), device="cuda"))
+    assert e.value.code == colden.CD_EUNSUPPORTED
+
+
+# ---------------------------------------------------------------------------
+# What the trained network gains over the plain tree method
+# ---------------------------------------------------------------------------
+
+def _dataset(L, seed, geom, n_rows):
+    rho = _field(L, seed)
+    tree = colden.build_tree_uniform(rho, 10 * PC)
+    nd = geom.n_dir
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    rows = torch.randperm(tree.n_leaf, generator=g)[:n_rows].cuda()
+    x = torch.zeros((len(rows), 8 * nd + 1), device="cuda")
+    nt = torch.zeros((len(rows), nd), device="cuda")
+    nr = torch.zeros((len(rows), nd), device="cuda")
+    colden.learned_features(tree, geom, x, nt, leaves=rows)
+    colden.raymarch(tree, geom, nr, leaves=rows)
+    y = torch.zeros_like(nr)
+    colden.learned_targets(nr, nt, y)
+    return x, y, nt, nr
+
+
+def test_trained_network_beats_plain_tree_on_held_out_field():
+    L, nd_geom = 6, ("healpix", 2)
+    geom = colden.precompute_geometry(*nd_geom)
+    parts = [_dataset(L, 300 + i, geom, 40000) for i in range(4)]
+    x = torch.cat([p[0] for p in parts])
+    y = torch.cat([p[1] for p in parts])
+    net, _ = _net(geom.n_dir, 128, seed=12, scale=0.1)
+    net.fit_normaliser(x)
+    losses = colden.train(net, x, y, steps=1500, batch=4096, lr=2e-3, lr_final=1e-4, seed=3)
+    assert np.all(np.isfinite(losses))
+    xe, ye, nte, nre = _dataset(L, 399, geom, 40000)
+    de = torch.zeros_like(ye)
+    net.forward(xe, de)
+    mse_plain = float((ye ** 2).mean())
+    mse_learned = float(((de - ye) ** 2).mean())
+    av = 1.0 / 1.87e21
+    dav_plain = float((nte * av - nre * av).abs().mean())
+    dav_learned = float((nte * torch.exp(de) * av - nre * av).abs().mean())
+    print("held-out: mse plain %.4g learned %.4g; <|dA_V|> plain %.4g learned %.4g"
+          % (mse_plain, mse_learned, dav_plain, dav_learned))
+    assert mse_learned < 0.5 * mse_plain
+    assert dav_learned < dav_plain

@@ -277,7 +277,7 @@ def test_insitu_uniform_is_distance_to_box_edge_telescoped():
 
 
 # ---------------------------------------------------------------------------
-# Six axis rays: one-dimensional sums, no geometric correction (§4.4) (P4)
+# Six axis rays: one-dimensional sums, no geometric correction (§4.3) (P4)
 # ---------------------------------------------------------------------------
 
 def _axis_row_sum(levels, box, l0, ijk, axis, sign):
@@ -504,7 +504,7 @@ def test_extinction_error_within_ten_percent_vs_raymarch():
 
 
 def test_prec_vs_insitu_extinction_difference_small():
-    """§4.4, Table 1: <|chi_prec - chi_insitu|> below ~0.004 on the paper's
+    """§4.3, Table 1: <|chi_prec - chi_insitu|> below ~0.004 on the paper's
     cloud; on a synthetic turbulent-like field we require < 0.01."""
     L = 6
     box = 10 * PC
