@@ -98,7 +98,8 @@ cd_status cd_learned_targets(int64_t n, const float *n_ray, const float *n_tree,
 cd_status cd_net_create(int n_dir, int hidden, const float *params, cd_net *out);
 
 /* Sets mu and sinv to the column mean and 1 / standard deviation of the n
- * rows of x (device [n][n_in]); a column with zero spread gets sinv = 1.
+ * rows of x (device [n][n_in]); a column whose standard deviation is at most
+ * 1e-3 (an empty slot: ln of the floor in every row) gets sinv = 1.
  * Deterministic.  Errors: CD_EINVAL (n < 1), CD_ENOMEM, CD_ECUDA. */
 cd_status cd_net_fit_normaliser(cd_net net, int64_t n, const float *x, void *stream);
 

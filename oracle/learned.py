@@ -106,12 +106,17 @@ def targets(n_ray: np.ndarray, n_tree: np.ndarray) -> np.ndarray:
     return np.log(n_ray / n_tree)
 
 
+SD_MIN = 1e-3       # columns with less spread than this (ln units) are not scaled
+
+
 def normaliser(x: np.ndarray):
-    """Column mean and inverse standard deviation of a training set (constant
-    columns get sinv = 1)."""
+    """Column mean and inverse standard deviation of a training set.  A column
+    whose standard deviation is at most SD_MIN carries no information at the
+    inputs' FP32 resolution (an empty slot is ln of the floor in every row) and
+    gets sinv = 1, so that rounding noise is not amplified."""
     mu = x.mean(axis=0)
     sd = np.sqrt(((x - mu) ** 2).mean(axis=0))
-    sinv = np.where(sd > 0, 1.0 / np.where(sd > 0, sd, 1.0), 1.0)
+    sinv = np.where(sd > SD_MIN, 1.0 / np.where(sd > SD_MIN, sd, 1.0), 1.0)
     return mu, sinv
 
 

@@ -253,7 +253,10 @@ __global__ void __launch_bounds__(256) column_moments(int64_t n, int n_in, const
     }
 }
 
-// pass 0: mu = sum / n; pass 1: sinv = 1 / sqrt(sum / n), 1 where that is 0
+// pass 0: mu = sum / n; pass 1: sinv = 1 / sqrt(sum / n), or 1 for a column
+// whose spread is at most kSdMin (no information at FP32 resolution)
+constexpr double kSdMin = 1e-3;
+
 __global__ void finish_moments(int n_in, int splits, int64_t n, const double *__restrict__ partial, int pass,
                                float *__restrict__ mu, float *__restrict__ sinv)
 {
@@ -266,7 +269,7 @@ __global__ void finish_moments(int n_in, int splits, int64_t n, const double *__
         mu[col] = (float)t;
     } else {
         const double sd = sqrt(t);
-        sinv[col] = sd > 0.0 ? (float)(1.0 / sd) : 1.f;
+        sinv[col] = sd > kSdMin ? (float)(1.0 / sd) : 1.f;
     }
 }
 

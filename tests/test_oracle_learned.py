@@ -130,10 +130,10 @@ def test_apply_falls_back_where_delta_is_not_finite():
 
 
 def test_normaliser_moments():
-    x = np.array([[1.0, 5.0], [2.0, 5.0], [3.0, 5.0], [4.0, 5.0]])
+    x = np.array([[1.0, 5.0, 7.0], [2.0, 5.0, 7.0 + 1e-4], [3.0, 5.0, 7.0], [4.0, 5.0, 7.0 + 1e-4]])
     mu, sinv = ol.normaliser(x)
-    assert np.allclose(mu, [2.5, 5.0])
-    assert np.allclose(sinv, [1.0 / math.sqrt(1.25), 1.0])
+    assert np.allclose(mu, [2.5, 5.0, 7.00005])
+    assert np.allclose(sinv, [1.0 / math.sqrt(1.25), 1.0, 1.0])
 
 
 # ---------------------------------------------------------------------------
