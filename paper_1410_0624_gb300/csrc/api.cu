@@ -374,7 +374,8 @@ cd_status cd_device_status(void *stream)
     CD_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     cd_status a = leaf_fault_check();
     cd_status b = tc_fault_check();
-    return a != CD_OK ? a : b;
+    cd_status c = learned_tc_fault_check();
+    return a != CD_OK ? a : b != CD_OK ? b : c;
 }
 
 cd_status cd_tree_info(cd_tree t, int64_t *n_leaf, int *max_level, int *base_level, int64_t *n_oct)

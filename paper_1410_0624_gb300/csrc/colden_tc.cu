@@ -54,7 +54,7 @@ static __device__ int g_tc_fault;
 struct TcArgs {
     int k;                       // receiving level (>= 4)
     int nd, N, Nt;               // directions, N = 8 nd, Nt = N / 2 columns per tile (children 4h .. 4h+3)
-    int c0, c1;                  // chunk range (tables 1..3 -> 0..15, table 3 only -> 10..15)
+    int c0, c1;                  // chunk range: table t is chunks 5 (t-1) .. 5 t
     const __nv_bfloat16 *brick[4];   // brick arrays of levels k, k-1, k-2 (tables 1, 2, 3)
     const __nv_bfloat16 *B;      // [64 class][15 chunk][N/8][6][8][8]
     float *out;                  // [8^k][nd]: the shell sum of this launch (no far-field prefix)
@@ -376,20 +376,28 @@ cd_status launch_ext_tc(const ExtLaunch &a, const __nv_bfloat16 *const *brick, c
     P.nd = a.nd;
     P.N = 8 * a.nd;
     P.Nt = 4 * a.nd;
-    const bool all3 = (a.tmask & 7) == 7;
-    if (!all3 && a.tmask != 4) {
-        set_error("tensor-core shell serves tables {1,2,3} or {3}");
+    // any contiguous run of tables t0..t1: chunks [(t0-1) 5, t1 5)
+    int t0 = 0, t1 = 0;
+    for (int t = 1; t <= 3; ++t)
+        if (a.tmask & (1 << (t - 1))) {
+            if (!t0) t0 = t;
+            t1 = t;
+        }
+    const int run = t0 ? ((1 << t1) - 1) & ~((1 << (t0 - 1)) - 1) : 0;
+    if (!t0 || a.tmask != run) {
+        set_error("tensor-core shell serves a contiguous run of tables (mask %d)", a.tmask);
         return CD_EUNSUPPORTED;
     }
-    P.c0 = all3 ? 0 : 2 * kBricksPerTable / kChunkBricks;
-    P.c1 = kChunks;
+    constexpr int kChunksPerTable = kBricksPerTable / kChunkBricks;
+    P.c0 = (t0 - 1) * kChunksPerTable;
+    P.c1 = t1 * kChunksPerTable;
     P.brick[0] = nullptr;
     P.brick[1] = brick[a.k];
     P.brick[2] = brick[a.k - 1];
     P.brick[3] = brick[a.k - 2];
     P.B = g->wb;
     P.out = a.out;
-    P.dx_k = a.dx[1] > 0.f ? a.dx[1] : a.dx[3] * 0.25f;
+    P.dx_k = a.dx[t0] / (float)(1 << (t0 - 1));   // dx of table t's level = 2^(t-1) dx_k
     P.nG = (int64_t)1 << (3 * (a.k - 3));
     P.ntiles = 2 * 64 * ((P.nG + 127) / 128);
     const size_t bstage = (size_t)P.Nt * kChunkBricks * 16;

@@ -85,6 +85,7 @@ struct Workspace {
 // The learned form's per-level sums (learned.cu): every shell kept apart.
 struct LevelSums {
     int ndir = 0;
+    int precision = -1;                       // CD_FP32, or CD_BF16 (tensor cores for levels >= 4)
     int64_t geom_uid = 0, rho_version = -1;   // what the sums were computed for
     float *C[CD_MAXL + 1] = {};   // shell of level k-2 seen from level-k cells, no prefix, [8^k][ndir]
     float *Et[4] = {};            // oct level, table t alone (shell of level L-t), [n_oct][ndir]

@@ -70,10 +70,10 @@ __global__ void __launch_bounds__(kThreads) learned_features(FeatArgs A)
             loc = fmaf(A.rho_leaf[oct * 8 + sib], A.kloc[(t * 8 + sib) * nd + d], loc);
         c[0] = A.dx_leaf * loc;
         for (int sl = 1; sl < kSlots; ++sl) c[sl] = 0.f;
-        for (int dl = 1; dl <= 3 && dl <= A.L - 1; ++dl) c[dl] = A.Et[dl][oct * nd + d];
-        for (int dl = 4; dl <= A.L - 1; ++dl) {
-            const int k = A.L - dl + 2;
-            const float v = A.C[k][(m >> (3 * (dl - 2))) * nd + d];
+#pragma unroll
+        for (int dl = 1; dl < CD_MAXL; ++dl) {      // dl constant after unrolling
+            if (dl > A.L - 1) break;
+            const float v = dl <= 3 ? A.Et[dl][oct * nd + d] : A.C[A.L - dl + 2][(m >> (3 * (dl - 2))) * nd + d];
             c[dl < kSlots ? dl : kSlots - 1] += v;
         }
         float tot = 0.f;
@@ -242,11 +242,14 @@ cd_status check_net(cd_net net)
 
 // Computes (or reuses) every shell's sum kept apart: C[k] for k = 3 .. L-2 and
 // Et[t] at the oct level.
-cd_status ensure_level_sums(cd_tree t, cd_geom g, cudaStream_t s)
+cd_status ensure_level_sums(cd_tree t, cd_geom g, int precision, cudaStream_t s)
 {
     LevelSums &lv = t->lv;
     const int nd = g->n_dir, L = t->L;
-    if (lv.ndir == nd && lv.geom_uid == g->uid && lv.rho_version == t->rho_version) return CD_OK;
+    if (lv.ndir == nd && lv.geom_uid == g->uid && lv.rho_version == t->rho_version && lv.precision == precision)
+        return CD_OK;
+    // BF16: the tensor-core contraction (one table per launch) where it serves
+    const bool tc = precision == CD_BF16 && tc_supported(nd) && g->wb != nullptr;
     if (lv.ndir != nd) {
         free_level_sums(t);
         for (int k = 3; k <= L - 2; ++k)
@@ -264,7 +267,7 @@ cd_status ensure_level_sums(cd_tree t, cd_geom g, cudaStream_t s)
         a.rho[3] = t->rho_lvl[k - 2];
         a.dx[3] = dx_of(t, k - 2);
         a.out = lv.C[k];
-        cd_status st = launch_ext_fp32(a, g, s);
+        cd_status st = tc && k >= 4 ? launch_ext_tc(a, t->rho_brick, g, s) : launch_ext_fp32(a, g, s);
         if (st != CD_OK) return st;
     }
     const int k = L - 1;
@@ -276,11 +279,12 @@ cd_status ensure_level_sums(cd_tree t, cd_geom g, cudaStream_t s)
         a.rho[tt] = t->rho_lvl[k - tt + 1];
         a.dx[tt] = dx_of(t, k - tt + 1);
         a.out = lv.Et[tt];
-        cd_status st = launch_ext_fp32(a, g, s);
+        cd_status st = tc && k >= 4 ? launch_ext_tc(a, t->rho_brick, g, s) : launch_ext_fp32(a, g, s);
         if (st != CD_OK) return st;
     }
     lv.geom_uid = g->uid;
     lv.rho_version = t->rho_version;
+    lv.precision = precision;
     return CD_OK;
 }
 
@@ -303,6 +307,7 @@ void free_level_sums(cd_tree t)
     lv.ndir = 0;
     lv.geom_uid = 0;
     lv.rho_version = -1;
+    lv.precision = -1;
 }
 
 cd_status column_density_learned(cd_tree t, cd_geom g, const cd_opts &o, float *n_h, float *a_v, float *shield,
@@ -321,7 +326,7 @@ cd_status column_density_learned(cd_tree t, cd_geom g, const cd_opts &o, float *
         set_error("the network has %d directions, the geometry %d", net->lay.nd, nd);
         return CD_EINVAL;
     }
-    if ((st = ensure_level_sums(t, g, s)) != CD_OK) return st;
+    if ((st = ensure_level_sums(t, g, CD_FP32, s)) != CD_OK) return st;
     LevelSums &lv = t->lv;
     const int64_t chunk = std::min<int64_t>(kChunkRows, t->n_leaf);
     if (lv.rows < chunk) {
@@ -405,7 +410,7 @@ cd_status cd_learned_features(cd_tree tree, cd_geom geom, int64_t n, const int64
         return CD_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    if ((st = ensure_level_sums(tree, geom, s)) != CD_OK) return st;
+    if ((st = ensure_level_sums(tree, geom, CD_FP32, s)) != CD_OK) return st;
     return launch_features(tree, geom, n, 0, leaves, x, n_tree, s);
 }
 

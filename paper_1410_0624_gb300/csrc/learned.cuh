@@ -77,9 +77,14 @@ cd_status mlp_fit_normaliser(cd_net net, int64_t n, const float *x, cudaStream_t
 cd_status column_density_learned_tc(cd_tree t, cd_geom g, const cd_opts &o, float *n_h, float *a_v, float *shield,
                                     cudaStream_t s);
 void net_free_tc(cd_net net);
+bool learned_tc_supported(int nd, int hidden);
+// CD_ETIMEOUT if a learned tensor-core kernel gave up a bounded wait (clears it)
+cd_status learned_tc_fault_check();
 
 // learned.cu
-cd_status ensure_level_sums(cd_tree t, cd_geom g, cudaStream_t s);
+// every shell's sum kept apart; precision CD_BF16 uses the tensor-core
+// contraction for receiving levels >= 4
+cd_status ensure_level_sums(cd_tree t, cd_geom g, int precision, cudaStream_t s);
 cd_status column_density_learned(cd_tree t, cd_geom g, const cd_opts &o, float *n_h, float *a_v, float *shield,
                                  cudaStream_t s);
 

@@ -1,17 +1,792 @@
-// The learned form of cd_column_density in BF16 on the tcgen05 tensor cores.
+// The learned form of cd_column_density in BF16 on the tcgen05 tensor cores
+// (weights and activations BF16, accumulation FP32 in tensor memory).
+//
+// Layer 1 is split along its inputs.  The external slots (Delta_l = 1..7, 7
+// n_dir inputs) are the same for the 8 leaves of an oct, so
+//   z1[leaf] = W1c u_cell[leaf] + h[oct],   h[oct] = W1e u_ext[oct] + b1
+// with u_cell = the standardised own-oct slot (n_dir inputs) and ln n.  Two
+// kernels:
+//   learned_oct_tc   one GEMM row per oct: builds u_ext from the per-level
+//                    sums (ln, standardise, BF16) straight into the operand
+//                    layout in shared memory, one MMA chain of K = 7 n_dir
+//                    against the resident W1e, writes h (BF16) and the oct's
+//                    external column sum_s c[s] (FP32).
+//   learned_cell_tc  one GEMM row per leaf, 128 leaves per tile: the internal +
+//                    local term and u_cell on the CUDA cores, then
+//                    MMA1 (W1c) -> + h, GELU -> MMA2 (W2) -> + b2, GELU ->
+//                    MMA3 (W3) -> + b3 = delta -> N = N_tree exp(delta), A_V,
+//                    shield; N is staged in shared memory and written out by
+//                    coalesced stores.
+//                    Two independent groups of four warps share the weights,
+//                    so one group's CUDA-core work overlaps the other's MMAs.
+// Every operand is K-major without swizzle: element (row, k) of a [rows x K]
+// tile sits at byte (row/8) (K/8) 128 + (k/8) 128 + (row%8) 16 + (k%8) 2,
+// i.e. LBO = 128 bytes along K and SBO = 16 K bytes between 8-row groups.
+// Waits on the tensor cores are bounded; a timeout sets a device flag
+// (cd_device_status) and the kernel leaves its loop with all threads together.
+#include <algorithm>
+#include <vector>
+
 #include "learned.cuh"
+#include "umma.cuh"
 
 namespace cd {
+namespace {
 
-cd_status column_density_learned_tc(cd_tree, cd_geom, const cd_opts &, float *, float *, float *, cudaStream_t)
+constexpr int kH = 128;                     // hidden width of the tensor-core form
+constexpr int kMaxNd = 48;
+constexpr uint32_t kMaxPolls = 1u << 26;
+constexpr float kGeluC = 0.7978845608028654f;
+constexpr float kGeluA = 0.044715f;
+
+static __device__ int g_ltc_fault;
+
+__host__ __device__ constexpr int round16(int v) { return (v + 15) & ~15; }
+__host__ __device__ constexpr size_t align128(size_t v) { return (v + 127) & ~(size_t)127; }
+
+__host__ __device__ inline uint32_t op_off(int row, int k, int K)
 {
-    set_error("the BF16 learned form is not built yet");
-    return CD_EUNSUPPORTED;
+    return (uint32_t)((row >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Byte offsets of the packed tensor-core weights in one device buffer.
+struct TcLayout {
+    int nd, NP, KC, KE, n_in;
+    size_t w1c, w1e, w2, w3;           // BF16 operand images [128 x KC], [128 x KE], [128 x 128], [NP x 128]
+    size_t b1, b2, b3;                 // FP32 [128], [128], [NP]
+    size_t muc, sic, mue, sie;         // FP32 standardisation of the cell inputs [KC] and external inputs [KE]
+    size_t total;
+};
+
+TcLayout make_layout(int nd)
+{
+    TcLayout T;
+    T.nd = nd;
+    T.NP = round16(nd);
+    T.KC = round16(nd + 1);
+    T.KE = round16(7 * nd);
+    T.n_in = kSlots * nd + 1;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t r = o; o = align128(o + bytes); return r; };
+    T.w1c = take((size_t)kH * T.KC * 2);
+    T.w1e = take((size_t)kH * T.KE * 2);
+    T.w2 = take((size_t)kH * kH * 2);
+    T.w3 = take((size_t)T.NP * kH * 2);
+    T.b1 = take(kH * 4);
+    T.b2 = take(kH * 4);
+    T.b3 = take((size_t)T.NP * 4);
+    T.muc = take((size_t)T.KC * 4);
+    T.sic = take((size_t)T.KC * 4);
+    T.mue = take((size_t)T.KE * 4);
+    T.sie = take((size_t)T.KE * 4);
+    T.total = o;
+    return T;
+}
+
+struct TcState {
+    TcLayout lay;
+    unsigned char *buf = nullptr;
+    __nv_bfloat16 *h = nullptr;        // [n_oct][128] per-oct layer-1 part
+    float *ext = nullptr;              // [n_oct][nd] external column
+    int64_t cap = 0;                   // octs h / ext hold
+};
+
+// ---- packing of the FP32 master parameters ----------------------------------
+
+struct PackArgs {
+    TcLayout T;
+    const float *p;        // packed FP32 parameters
+    const float *mu, *sinv;
+    NetLayout N;
+    unsigned char *buf;
+};
+
+__global__ void pack_tc(PackArgs A)
+{
+    const TcLayout &T = A.T;
+    const NetLayout &N = A.N;
+    const int nd = T.nd;
+    const float *W1 = A.p + N.W1, *W2 = A.p + N.W2, *W3 = A.p + N.W3;
+    const int64_t n1c = (int64_t)kH * T.KC, n1e = (int64_t)kH * T.KE, n2 = (int64_t)kH * kH, n3 = (int64_t)T.NP * kH;
+    const int64_t total = n1c + n1e + n2 + n3 + 2 * kH + T.NP + 2 * T.KC + 2 * T.KE;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = e;
+        if (i < n1c) {
+            const int n = (int)(i / T.KC), k = (int)(i % T.KC);
+            const float v = k < nd ? W1[(int64_t)n * N.n_in + k] : (k == nd ? W1[(int64_t)n * N.n_in + kSlots * nd] : 0.f);
+            reinterpret_cast<__nv_bfloat16 *>(A.buf + T.w1c + op_off(n, k, T.KC))[0] = __float2bfloat16_rn(v);
+            continue;
+        }
+        i -= n1c;
+        if (i < n1e) {
+            const int n = (int)(i / T.KE), k = (int)(i % T.KE);
+            const float v = k < 7 * nd ? W1[(int64_t)n * N.n_in + nd + k] : 0.f;
+            reinterpret_cast<__nv_bfloat16 *>(A.buf + T.w1e + op_off(n, k, T.KE))[0] = __float2bfloat16_rn(v);
+            continue;
+        }
+        i -= n1e;
+        if (i < n2) {
+            const int n = (int)(i / kH), k = (int)(i % kH);
+            reinterpret_cast<__nv_bfloat16 *>(A.buf + T.w2 + op_off(n, k, kH))[0] =
+                __float2bfloat16_rn(W2[(int64_t)n * kH + k]);
+            continue;
+        }
+        i -= n2;
+        if (i < n3) {
+            const int n = (int)(i / kH), k = (int)(i % kH);
+            const float v = n < nd ? W3[(int64_t)n * kH + k] : 0.f;
+            reinterpret_cast<__nv_bfloat16 *>(A.buf + T.w3 + op_off(n, k, kH))[0] = __float2bfloat16_rn(v);
+            continue;
+        }
+        i -= n3;
+        if (i < kH) { reinterpret_cast<float *>(A.buf + T.b1)[i] = A.p[N.b1 + i]; continue; }
+        i -= kH;
+        if (i < kH) { reinterpret_cast<float *>(A.buf + T.b2)[i] = A.p[N.b2 + i]; continue; }
+        i -= kH;
+        if (i < T.NP) { reinterpret_cast<float *>(A.buf + T.b3)[i] = i < nd ? A.p[N.b3 + i] : 0.f; continue; }
+        i -= T.NP;
+        if (i < 2 * T.KC) {
+            const int k = (int)(i % T.KC);
+            const int src = k < nd ? k : (k == nd ? kSlots * nd : -1);
+            const bool is_mu = i < T.KC;
+            const float v = src < 0 ? (is_mu ? 0.f : 1.f) : (is_mu ? A.mu[src] : A.sinv[src]);
+            reinterpret_cast<float *>(A.buf + (is_mu ? T.muc : T.sic))[k] = v;
+            continue;
+        }
+        i -= 2 * T.KC;
+        {
+            const int k = (int)(i % T.KE);
+            const bool is_mu = i < T.KE;
+            const float v = k < 7 * nd ? (is_mu ? A.mu[nd + k] : A.sinv[nd + k]) : (is_mu ? 0.f : 1.f);
+            reinterpret_cast<float *>(A.buf + (is_mu ? T.mue : T.sie))[k] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ float fast_tanh(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float gelu_fast(float z)
+{
+    const float inner = z * fmaf(kGeluC * kGeluA, z * z, kGeluC);
+    const float hz = 0.5f * z;
+    return fmaf(hz, fast_tanh(inner), hz);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void named_barrier(int id, int threads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// MMA chain D (+)= A[128 x K] * B[N x K]^T, K in steps of 16.
+__device__ __forceinline__ void mma_chain(uint32_t tmem_d, uint32_t a0, uint32_t b0, int K, int N)
+{
+    const uint32_t idesc = umma_idesc_bf16(128, N);
+    const uint32_t sbo = (uint32_t)K * 16;
+    for (int ks = 0; ks < K / 16; ++ks)
+        umma_bf16(tmem_d, umma_smem_desc(a0 + ks * 256, 128, sbo), umma_smem_desc(b0 + ks * 256, 128, sbo), idesc,
+                  ks > 0 ? 1u : 0u);
+}
+
+// ---- per-oct part ---------------------------------------------------------------
+
+struct OctArgs {
+    TcLayout T;
+    const unsigned char *tc;
+    int64_t n_oct, ntiles;
+    int L;
+    const float *Et[4];
+    const float *C[CD_MAXL + 1];
+    __nv_bfloat16 *h;      // [n_oct][128]
+    float *ext;            // [n_oct][nd]
+};
+
+constexpr int kOctThreads = 256;
+
+__global__ void __launch_bounds__(kOctThreads, 1) learned_oct_tc(OctArgs A)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const TcLayout &T = A.T;
+    const int nd = T.nd, KE = T.KE;
+    unsigned char *sA = smem;                                    // [128 x KE] BF16
+    unsigned char *sB = sA + align128((size_t)128 * KE * 2);     // W1e image
+    unsigned char *sO = sB + align128((size_t)128 * KE * 2);     // [128][128] BF16 output rows
+    float *sMu = reinterpret_cast<float *>(sO + 128 * kH * 2);   // [KE]
+    float *sSi = sMu + KE;                                       // [KE]
+    float *sB1 = sSi + KE;                                       // [128]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sB1 + kH);      // [0] weights, [1] MMA
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
+    int *sflag = reinterpret_cast<int *>(tslot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        *sflag = 0;
+    }
+    for (int i = tid; i < KE; i += kOctThreads) {
+        sMu[i] = reinterpret_cast<const float *>(A.tc + T.mue)[i];
+        sSi[i] = reinterpret_cast<const float *>(A.tc + T.sie)[i];
+    }
+    for (int i = tid; i < kH; i += kOctThreads) sB1[i] = reinterpret_cast<const float *>(A.tc + T.b1)[i];
+    if (warp == 0) tmem_alloc(tslot, 128);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    if (tid == 0) {
+        const uint32_t bytes = (uint32_t)(128 * KE * 2);
+        mbar_expect_tx(&bar[0], bytes);
+        bulk_g2s(sB, A.tc + T.w1e, bytes, &bar[0]);
+    }
+    bool weights_ready = false;
+    uint32_t phase = 0;
+
+    for (int64_t tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+        const int64_t o0 = tile * 128;
+        const int rows = (int)std::min<int64_t>(128, A.n_oct - o0);
+        // build u_ext (one warp per oct row, lanes over directions)
+        for (int r = warp; r < 128; r += kOctThreads / 32) {
+            const int64_t oct = o0 + r;
+            const bool valid = r < rows;
+            for (int d = lane; d < nd; d += 32) {
+                float c[7];
+#pragma unroll
+                for (int s = 0; s < 7; ++s) c[s] = 0.f;
+                if (valid) {
+                    // slot Delta_l (tail summed into slot 7); dl is a constant
+                    // after unrolling, so c stays in registers
+#pragma unroll
+                    for (int dl = 1; dl < CD_MAXL; ++dl) {
+                        if (dl > A.L - 1) break;
+                        const float v = dl <= 3 ? A.Et[dl][oct * nd + d]
+                                                : A.C[A.L - dl + 2][(oct >> (3 * (dl - 3))) * nd + d];
+                        c[(dl < kSlots ? dl : kSlots - 1) - 1] += v;
+                    }
+                    float tot = 0.f;
+#pragma unroll
+                    for (int s = 0; s < 7; ++s) tot += c[s];
+                    A.ext[oct * nd + d] = tot;
+                }
+#pragma unroll
+                for (int s = 0; s < 7; ++s) {
+                    const int k = s * nd + d;
+                    const float u = valid ? (__logf(fmaxf(c[s], kCFloor)) - sMu[k]) * sSi[k] : 0.f;
+                    *reinterpret_cast<__nv_bfloat16 *>(sA + op_off(r, k, KE)) = __float2bfloat16_rn(u);
+                }
+            }
+            for (int k = 7 * nd + lane; k < KE; k += 32)
+                *reinterpret_cast<__nv_bfloat16 *>(sA + op_off(r, k, KE)) = __float2bfloat16_rn(0.f);
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            bool ok = true;
+            if (!weights_ready) ok = weights_ready = mbar_wait_bounded(&bar[0], 0, kMaxPolls);
+            if (ok) {
+                tc_fence_after();
+                mma_chain(tbase, smem_u32(sA), smem_u32(sB), KE, kH);
+                umma_commit(&bar[1]);
+                ok = mbar_wait_bounded(&bar[1], phase, kMaxPolls);
+            }
+            if (!ok) *sflag = 1;
+            // the previous tile's output copy must have read sO
+            bulk_wait_read<0>();
+        }
+        phase ^= 1;
+        __syncthreads();
+        if (*sflag) break;
+        tc_fence_after();
+        if (warp < 4) {
+            const int r = warp * 32 + lane;
+#pragma unroll 1
+            for (int c = 0; c < kH; c += 32) {
+                uint32_t v[32];
+                tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+                tmem_ld_wait();
+                uint4 *dst = reinterpret_cast<uint4 *>(sO + (size_t)r * kH * 2 + c * 2);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint4 w;
+                    w.x = pack_bf16x2(__uint_as_float(v[8 * q + 0]) + sB1[c + 8 * q + 0],
+                                      __uint_as_float(v[8 * q + 1]) + sB1[c + 8 * q + 1]);
+                    w.y = pack_bf16x2(__uint_as_float(v[8 * q + 2]) + sB1[c + 8 * q + 2],
+                                      __uint_as_float(v[8 * q + 3]) + sB1[c + 8 * q + 3]);
+                    w.z = pack_bf16x2(__uint_as_float(v[8 * q + 4]) + sB1[c + 8 * q + 4],
+                                      __uint_as_float(v[8 * q + 5]) + sB1[c + 8 * q + 5]);
+                    w.w = pack_bf16x2(__uint_as_float(v[8 * q + 6]) + sB1[c + 8 * q + 6],
+                                      __uint_as_float(v[8 * q + 7]) + sB1[c + 8 * q + 7]);
+                    dst[q] = w;
+                }
+            }
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            bulk_s2g(A.h + o0 * kH, sO, (uint32_t)(rows * kH * 2));
+            bulk_commit();
+        }
+    }
+    if (*sflag && tid == 0) {
+        atomicExch(&g_ltc_fault, 1);
+        mbar_wait_bounded(&bar[1], phase ^ 1, kMaxPolls);   // let an issued chain finish
+    }
+    if (tid == 0) bulk_wait_all<0>();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 128);
+    }
+}
+
+// ---- per-leaf part --------------------------------------------------------------
+
+struct CellArgs {
+    TcLayout T;
+    const unsigned char *tc;
+    int64_t n_leaf, ntiles;
+    float dx_leaf, av_per_nh, shield_k;
+    const float *rho_leaf;       // Morton
+    const float *kloc;           // [8][8][nd]
+    const __nv_bfloat16 *h;      // [n_oct][128]
+    const float *ext;            // [n_oct][nd]
+    float *n_h, *a_v, *shield;
+};
+
+constexpr int kCellThreads = 256;   // two groups of 128
+
+// Row stride (floats) of the staged N rows: odd, so that the 32 rows a warp
+// writes at one direction fall in 32 different banks.
+__host__ __device__ constexpr int nstride(int nd) { return nd | 1; }
+
+struct CellSmem {
+    size_t w1c, w2, w3, kloc, muc, sic, b2, b3, grp, grp_stride, x, a2, n, bar, total;
+    int kstride;                      // floats between kloc[t] rows
+};
+
+__host__ __device__ inline CellSmem cell_smem(const TcLayout &T)
+{
+    CellSmem S;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t r = o; o = align128(o + bytes); return r; };
+    S.kstride = 8 * T.nd + 4;
+    S.w1c = take((size_t)kH * T.KC * 2);
+    S.w2 = take((size_t)kH * kH * 2);
+    S.w3 = take((size_t)T.NP * kH * 2);
+    S.kloc = take((size_t)8 * S.kstride * 4);
+    S.muc = take((size_t)T.KC * 4);
+    S.sic = take((size_t)T.KC * 4);
+    S.b2 = take(kH * 4);
+    S.b3 = take((size_t)T.NP * 4);
+    S.bar = take(64);
+    S.grp = o;
+    const size_t x = 0, a2 = align128((size_t)128 * T.KC * 2), n = a2 + align128((size_t)128 * kH * 2);
+    S.x = x;
+    S.a2 = a2;
+    S.n = n;
+    S.grp_stride = align128(n + (size_t)128 * nstride(T.nd) * 4);
+    S.total = S.grp + 2 * S.grp_stride;
+    return S;
+}
+
+__global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const TcLayout &T = A.T;
+    const CellSmem S = cell_smem(T);
+    const int nd = T.nd, KC = T.KC, NP = T.NP;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int g = warp >> 2, quarter = warp & 3, i = tid & 127;   // group, TMEM lane quarter, row
+    float *sK = reinterpret_cast<float *>(smem + S.kloc);
+    const float *sMu = reinterpret_cast<const float *>(smem + S.muc);
+    const float *sSi = reinterpret_cast<const float *>(smem + S.sic);
+    const float *sB2 = reinterpret_cast<const float *>(smem + S.b2);
+    const float *sB3 = reinterpret_cast<const float *>(smem + S.b3);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S.bar);     // [0] weights, [1 + g] group MMAs
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 3);
+    int *sflag = reinterpret_cast<int *>(tslot + 1);                  // [2] per-group fault flags
+    unsigned char *G = smem + S.grp + g * S.grp_stride;
+    unsigned char *sX = G + S.x;
+    unsigned char *sA2 = G + S.a2;
+    float *sN = reinterpret_cast<float *>(G + S.n);
+
+    if (tid == 0) {
+        for (int b = 0; b < 3; ++b) mbar_init(&bar[b], 1);
+        fence_mbar_init();
+        sflag[0] = sflag[1] = 0;
+    }
+    for (int e = tid; e < 64 * nd; e += kCellThreads) {
+        const int ts = e / nd, d = e - ts * nd;      // ts = t * 8 + s
+        sK[(ts >> 3) * S.kstride + (ts & 7) * nd + d] = A.kloc[e];
+    }
+    for (int k = tid; k < KC; k += kCellThreads) {
+        reinterpret_cast<float *>(smem + S.muc)[k] = reinterpret_cast<const float *>(A.tc + T.muc)[k];
+        reinterpret_cast<float *>(smem + S.sic)[k] = reinterpret_cast<const float *>(A.tc + T.sic)[k];
+    }
+    for (int k = tid; k < kH; k += kCellThreads)
+        reinterpret_cast<float *>(smem + S.b2)[k] = reinterpret_cast<const float *>(A.tc + T.b2)[k];
+    for (int k = tid; k < NP; k += kCellThreads)
+        reinterpret_cast<float *>(smem + S.b3)[k] = reinterpret_cast<const float *>(A.tc + T.b3)[k];
+    if (warp == 0) tmem_alloc(tslot, 512);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    if (tid == 0) {
+        const uint32_t b1 = (uint32_t)(kH * KC * 2), b2 = (uint32_t)(kH * kH * 2), b3 = (uint32_t)(NP * kH * 2);
+        mbar_expect_tx(&bar[0], b1 + b2 + b3);
+        bulk_g2s(smem + S.w1c, A.tc + T.w1c, b1, &bar[0]);
+        bulk_g2s(smem + S.w2, A.tc + T.w2, b2, &bar[0]);
+        bulk_g2s(smem + S.w3, A.tc + T.w3, b3, &bar[0]);
+    }
+    const uint32_t tD1 = tbase + (uint32_t)(g * 256), tD2 = tD1 + 128;   // D3 reuses D1's columns
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    const int bid = 1 + g;                                               // named barrier of the group
+    bool weights_ready = false;
+    uint32_t phase = 0;
+    bool fault = false;
+
+    // leader of the group: issue, commit and wait (bounded); everyone learns
+    // the outcome after the group barrier
+    auto issue_and_wait = [&](int layer) {
+        if (i == 0) {
+            bool ok = true;
+            if (!weights_ready) ok = weights_ready = mbar_wait_bounded(&bar[0], 0, kMaxPolls);
+            if (ok) {
+                tc_fence_after();
+                if (layer == 1) mma_chain(tD1, smem_u32(sX), smem_u32(smem + S.w1c), KC, kH);
+                else if (layer == 2) mma_chain(tD2, smem_u32(sA2), smem_u32(smem + S.w2), kH, kH);
+                else mma_chain(tD1, smem_u32(sA2), smem_u32(smem + S.w3), kH, NP);
+                umma_commit(&bar[1 + g]);
+                ok = mbar_wait_bounded(&bar[1 + g], phase, kMaxPolls);
+            }
+            if (!ok) sflag[g] = 1;
+        }
+        phase ^= 1;
+        named_barrier(bid, 128);
+        fault = sflag[g] != 0;
+        tc_fence_after();
+    };
+
+    for (int64_t tile = 2 * (int64_t)blockIdx.x + g; tile < A.ntiles && !fault; tile += 2 * (int64_t)gridDim.x) {
+        const int64_t c0 = tile * 128;
+        const int rows = (int)std::min<int64_t>(128, A.n_leaf - c0);
+        const int64_t m = c0 + i;
+        const bool valid = i < rows;
+        const int64_t oct = valid ? m >> 3 : 0;
+
+        // ---- inputs of the leaf: internal + local term, u_cell, N_tree ----
+        {
+            float rho8[8];
+            const int t = (int)(m & 7);
+#pragma unroll
+            for (int s = 0; s < 8; ++s) rho8[s] = valid ? A.rho_leaf[oct * 8 + s] : 0.f;
+            const float *Kt = sK + t * S.kstride;
+            float *nrow = sN + (size_t)i * nstride(nd);
+            for (int d0 = 0; d0 < KC; d0 += 8) {
+                float u[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int d = d0 + j;
+                    float v = 0.f;
+                    if (d < nd) {
+                        float loc = 0.f;
+#pragma unroll
+                        for (int s = 0; s < 8; ++s) loc = fmaf(rho8[s], Kt[s * nd + d], loc);
+                        loc *= A.dx_leaf;
+                        nrow[d] = valid ? loc + A.ext[oct * nd + d] : 0.f;
+                        v = (__logf(fmaxf(loc, kCFloor)) - sMu[d]) * sSi[d];
+                    } else if (d == nd) {
+                        v = (__logf(fmaxf(valid ? A.rho_leaf[m] : 0.f, kNFloor)) - sMu[d]) * sSi[d];
+                    }
+                    u[j] = valid ? v : 0.f;
+                }
+                uint4 w;
+                w.x = pack_bf16x2(u[0], u[1]);
+                w.y = pack_bf16x2(u[2], u[3]);
+                w.z = pack_bf16x2(u[4], u[5]);
+                w.w = pack_bf16x2(u[6], u[7]);
+                *reinterpret_cast<uint4 *>(sX + op_off(i, d0, KC)) = w;
+            }
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        named_barrier(bid, 128);
+        issue_and_wait(1);
+        if (fault) break;
+
+        // ---- z1 = D1 + h[oct], a1 = gelu(z1) -> A2 ----
+        {
+            const uint4 *hrow = reinterpret_cast<const uint4 *>(A.h + oct * kH);
+#pragma unroll 1
+            for (int c = 0; c < kH; c += 32) {
+                uint32_t v[32];
+                tmem_ld32(tD1 + lane_off + (uint32_t)c, v);
+                tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 hv = hrow[(c >> 3) + q];
+                    const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+                    uint32_t o[4];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162 *>(&hw[p]);
+                        const float2 hf = __bfloat1622float2(hb);
+                        o[p] = pack_bf16x2(gelu_fast(__uint_as_float(v[8 * q + 2 * p]) + hf.x),
+                                           gelu_fast(__uint_as_float(v[8 * q + 2 * p + 1]) + hf.y));
+                    }
+                    *reinterpret_cast<uint4 *>(sA2 + op_off(i, c + 8 * q, kH)) = make_uint4(o[0], o[1], o[2], o[3]);
+                }
+            }
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        named_barrier(bid, 128);
+        issue_and_wait(2);
+        if (fault) break;
+
+        // ---- a2 = gelu(D2 + b2) -> A2 (MMA2 has finished reading it) ----
+#pragma unroll 1
+        for (int c = 0; c < kH; c += 32) {
+            uint32_t v[32];
+            tmem_ld32(tD2 + lane_off + (uint32_t)c, v);
+            tmem_ld_wait();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t o[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const int n = c + 8 * q + 2 * p;
+                    o[p] = pack_bf16x2(gelu_fast(__uint_as_float(v[8 * q + 2 * p]) + sB2[n]),
+                                       gelu_fast(__uint_as_float(v[8 * q + 2 * p + 1]) + sB2[n + 1]));
+                }
+                *reinterpret_cast<uint4 *>(sA2 + op_off(i, c + 8 * q, kH)) = make_uint4(o[0], o[1], o[2], o[3]);
+            }
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        named_barrier(bid, 128);
+        issue_and_wait(3);
+        if (fault) break;
+
+        // ---- delta = D3 + b3; N = N_tree exp(delta); shield ----
+        {
+            float *nrow = sN + (size_t)i * nstride(nd);
+            float acc = 0.f;
+#pragma unroll 1
+            for (int c = 0; c < NP; c += 32) {
+                uint32_t v[32];
+                tmem_ld32(tD1 + lane_off + (uint32_t)c, v);
+                tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int d = c + j;
+                    if (d < nd) {
+                        const float dl = __uint_as_float(v[j]) + sB3[d];
+                        const float nt = nrow[d];
+                        const float N = isfinite(dl) ? nt * __expf(dl) : nt;
+                        nrow[d] = N;
+                        acc += __expf(-A.shield_k * (N * A.av_per_nh));
+                    }
+                }
+            }
+            if (A.shield && valid) A.shield[m] = acc / (float)nd;
+        }
+        tc_fence_before();
+        named_barrier(bid, 128);
+        // ---- the tile's rows of N and A_V, element e = r nd + d, coalesced ----
+        if (A.n_h || A.a_v) {
+            const int total = rows * nd, step_r = 128 / nd, step_d = 128 - (128 / nd) * nd;
+            int r = i / nd, d = i - (i / nd) * nd;
+            float *nh = A.n_h ? A.n_h + c0 * nd : nullptr;
+            float *av = A.a_v ? A.a_v + c0 * nd : nullptr;
+            for (int e = i; e < total; e += 128) {
+                const float N = sN[r * nstride(nd) + d];
+                if (nh) nh[e] = N;
+                if (av) av[e] = N * A.av_per_nh;
+                r += step_r;
+                d += step_d;
+                if (d >= nd) {
+                    d -= nd;
+                    ++r;
+                }
+            }
+        }
+        named_barrier(bid, 128);     // sN is rewritten by the next tile
+    }
+    if (fault && i == 0) {
+        atomicExch(&g_ltc_fault, 1);
+        mbar_wait_bounded(&bar[1 + g], phase ^ 1, kMaxPolls);   // let an issued chain finish
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, 512);
+    }
+}
+
+int num_sms()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 152;
+}
+
+size_t oct_smem(const TcLayout &T)
+{
+    return 2 * align128((size_t)128 * T.KE * 2) + 128 * kH * 2 + (size_t)(2 * T.KE + kH) * 4 + 2 * 8 + 16;
+}
+
+// Packs the BF16 operands when the master weights changed since the last pack.
+cd_status ensure_packed(cd_net net, cudaStream_t s)
+{
+    TcState *st = static_cast<TcState *>(net->tc);
+    if (!st) {
+        st = new TcState();
+        st->lay = make_layout(net->lay.nd);
+        if (cudaMalloc(&st->buf, st->lay.total) != cudaSuccess) {
+            cudaGetLastError();
+            delete st;
+            set_error("cannot allocate the packed tensor-core weights");
+            return CD_ENOMEM;
+        }
+        net->tc = st;
+        net->tc_version = 0;
+    }
+    if (net->tc_version == net->version) return CD_OK;
+    PackArgs P;
+    P.T = st->lay;
+    P.p = net->p;
+    P.mu = net->mu;
+    P.sinv = net->sinv;
+    P.N = net->lay;
+    P.buf = st->buf;
+    LaunchScope ls(CD_K_NET, s);
+    pack_tc<<<num_sms() * 4, 256, 0, s>>>(P);
+    CD_CHECK_LAUNCH();
+    net->tc_version = net->version;
+    return CD_OK;
+}
+
+}  // namespace
+
+bool learned_tc_supported(int nd, int hidden) { return hidden == kH && nd >= 1 && nd <= kMaxNd; }
+
+cd_status column_density_learned_tc(cd_tree t, cd_geom g, const cd_opts &o, float *n_h, float *a_v, float *shield,
+                                    cudaStream_t s)
+{
+    cd_net net = (cd_net)o.net;
+    const int nd = g->n_dir;
+    if (!learned_tc_supported(nd, net->lay.H)) {
+        set_error("the BF16 learned form needs hidden = %d and 1 <= n_dir <= %d (got %d, %d); use CD_FP32", kH,
+                  kMaxNd, net->lay.H, nd);
+        return CD_EUNSUPPORTED;
+    }
+    if (t->L < 2) {
+        set_error("the BF16 learned form needs at least two tree levels");
+        return CD_EUNSUPPORTED;
+    }
+    cd_status st = ensure_level_sums(t, g, CD_BF16, s);
+    if (st != CD_OK) return st;
+    if ((st = ensure_packed(net, s)) != CD_OK) return st;
+    TcState *ts = static_cast<TcState *>(net->tc);
+    const TcLayout &T = ts->lay;
+    if (ts->cap < t->n_oct) {
+        if (ts->h) cudaFree(ts->h);
+        if (ts->ext) cudaFree(ts->ext);
+        ts->h = nullptr;
+        ts->ext = nullptr;
+        ts->cap = 0;
+        if (cudaMalloc(&ts->h, (size_t)t->n_oct * kH * 2) != cudaSuccess ||
+            cudaMalloc(&ts->ext, (size_t)t->n_oct * nd * 4) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cannot allocate the per-oct buffers of the learned form");
+            return CD_ENOMEM;
+        }
+        ts->cap = t->n_oct;
+    }
+    const int sms = num_sms();
+    {
+        OctArgs A = {};
+        A.T = T;
+        A.tc = ts->buf;
+        A.n_oct = t->n_oct;
+        A.ntiles = (t->n_oct + 127) / 128;
+        A.L = t->L;
+        for (int i = 0; i < 4; ++i) A.Et[i] = t->lv.Et[i];
+        for (int k = 0; k <= CD_MAXL; ++k) A.C[k] = t->lv.C[k];
+        A.h = ts->h;
+        A.ext = ts->ext;
+        const size_t smem = oct_smem(T);
+        CD_CUDA(cudaFuncSetAttribute(learned_oct_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int grid = (int)std::min<int64_t>(A.ntiles, sms);
+        LaunchScope ls(CD_K_NET, s);
+        learned_oct_tc<<<grid, kOctThreads, smem, s>>>(A);
+        CD_CHECK_LAUNCH();
+    }
+    {
+        CellArgs A = {};
+        A.T = T;
+        A.tc = ts->buf;
+        A.n_leaf = t->n_leaf;
+        A.ntiles = (t->n_leaf + 127) / 128;
+        A.dx_leaf = (float)(t->box_cm / (double)((int64_t)1 << t->L));
+        A.av_per_nh = (float)o.av_per_nh;
+        A.shield_k = (float)o.shield_k;
+        A.rho_leaf = t->rho_leaf;
+        A.kloc = g->kloc;
+        A.h = ts->h;
+        A.ext = ts->ext;
+        A.n_h = n_h;
+        A.a_v = a_v;
+        A.shield = shield;
+        const size_t smem = cell_smem(T).total;
+        CD_CUDA(cudaFuncSetAttribute(learned_cell_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int grid = (int)std::min<int64_t>((A.ntiles + 1) / 2, sms);
+        LaunchScope ls(CD_K_FEATURES, s);
+        learned_cell_tc<<<grid, kCellThreads, smem, s>>>(A);
+        CD_CHECK_LAUNCH();
+    }
+    return CD_OK;
+}
+
+cd_status learned_tc_fault_check()
+{
+    int v = 0;
+    CD_CUDA(cudaMemcpyFromSymbol(&v, g_ltc_fault, sizeof(int)));
+    if (v) {
+        const int zero = 0;
+        CD_CUDA(cudaMemcpyToSymbol(g_ltc_fault, &zero, sizeof(int)));
+        set_error("a learned tensor-core kernel gave up a bounded wait");
+        return CD_ETIMEOUT;
+    }
+    return CD_OK;
 }
 
 void net_free_tc(cd_net net)
 {
-    if (net->tc) cudaFree(net->tc);
+    TcState *st = static_cast<TcState *>(net->tc);
+    if (!st) return;
+    if (st->buf) cudaFree(st->buf);
+    if (st->h) cudaFree(st->h);
+    if (st->ext) cudaFree(st->ext);
+    delete st;
     net->tc = nullptr;
 }
 
