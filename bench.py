@@ -234,9 +234,10 @@ def _kernel_breakdown(colden, step, flush, steps):
         step()
     torch.cuda.synchronize()
     out = {}
-    for k, name in enumerate(["restrict", "shell", "leaf", "other"]):
+    for k, name in enumerate(colden.KERNEL_KINDS):
         n, kms = colden.stats_get(k)
-        out[name] = {"launches_per_step": n / steps, "ms_per_step": kms / steps}
+        if n:
+            out[name] = {"launches_per_step": n / steps, "ms_per_step": kms / steps}
     colden.stats_reset(timing=False)
     return out
 
@@ -318,7 +319,7 @@ def run_ours(args):
     time.sleep(0.3)
     ms = _time_steps(step, flush, stream, args.steps)
     clk = clocks.stop()
-    launches = sum(colden.stats_get(k)[0] for k in range(4))
+    launches = sum(colden.stats_get(k)[0] for k in range(len(colden.KERNEL_KINDS)))
     if dist:
         dist.barrier()
     ms = max_over_ranks(ms)
@@ -436,7 +437,7 @@ def run_amr(args):
     colden.stats_reset(timing=False)
     ms = _time_steps(step, flush, stream, args.steps)
     clk = clocks.stop()
-    launches = sum(colden.stats_get(k)[0] for k in range(4))
+    launches = sum(colden.stats_get(k)[0] for k in range(len(colden.KERNEL_KINDS)))
     kern = _kernel_breakdown(colden, step, flush, args.steps)
     units = tree.n_leaf * nd
     peak, peak_kind = _peaks()
@@ -539,6 +540,257 @@ def run_batch(args):
     return 0
 
 
+def _learned_dataset(colden, synth, geom, L, seed, n_rows, x_out, y_out):
+    """Rows of one seeded training field: network inputs and ray-marched
+    targets of a random leaf subset, written into x_out / y_out."""
+    import torch
+    rho = synth.lognormal_grf_torch(1 << L, 30.0, 2.0, seed, device="cuda").contiguous()
+    tree = colden.build_tree_uniform(rho, 10 * synth.PC_CM)
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    rows = torch.randperm(tree.n_leaf, generator=g)[:n_rows].cuda()
+    nd = geom.n_dir
+    nt = torch.empty((len(rows), nd), device="cuda")
+    nr = torch.empty_like(nt)
+    colden.learned_features(tree, geom, x_out, nt, leaves=rows)
+    colden.raymarch(tree, geom, nr, leaves=rows)
+    colden.learned_targets(nr, nt, y_out)
+    tree.free()
+
+
+def _ray_scores(n_h, sh, nd, rows, n_ray):
+    """A_V and screening-factor errors of a form against the exact ray-marcher
+    on sampled leaves."""
+    import torch
+    av = 1.0 / 1.87e21
+    got = n_h.reshape(-1, nd)[rows].double()
+    ray = n_ray.double()
+    dav = (got - ray).abs() * av
+    chi_ray = torch.exp(-2.5 * ray * av).mean(dim=1)
+    return {"a_v_abs_mean": float(dav.mean()), "a_v_abs_p99": float(torch.quantile(dav.reshape(-1)[:10_000_000], 0.99)),
+            "ln_err_mse": float(((got / ray).log() ** 2).mean()),
+            "shield_abs_mean": float((sh[rows].double() - chi_ray).abs().mean()), "leaves": int(len(rows))}
+
+
+def run_learned(args):
+    """Learned correction: the network trained on 16 seeded 128^3 fields
+    (1M leaves each, ray-marched targets), evaluated on a 512^3 field of the
+    same recipe (seed 200).  One step = restriction + the BF16 learned form
+    (per-level sums, per-oct layer 1, fused per-leaf network, N_H + shield)."""
+    import torch
+    from paper_1410_0624_gb300 import colden, synth
+    rank, world, local = _rank()
+    torch.cuda.set_device(local)
+    colden.load()
+    geom = colden.precompute_geometry("healpix", 2)
+    nd = geom.n_dir
+    H = 128
+    # ---- training set and training (one-off, timed apart) ----
+    n_fields, rows_per = 16, args.train_rows
+    t0 = time.time()
+    x = torch.empty((n_fields * rows_per, 8 * nd + 1), device="cuda")
+    y = torch.empty((n_fields * rows_per, nd), device="cuda")
+    for i in range(n_fields):
+        _learned_dataset(colden, synth, geom, 7, 100 + i, rows_per, x[i * rows_per:(i + 1) * rows_per],
+                         y[i * rows_per:(i + 1) * rows_per])
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    net = colden.Net(nd, H, synth.mlp_init(nd, H, 12, out_scale=0.1))
+    t0 = time.time()
+    net.fit_normaliser(x)
+    losses = colden.train(net, x, y, steps=args.train_steps, batch=8192, lr=2e-3, lr_final=1e-4, seed=3)
+    torch.cuda.synchronize()
+    train_s = time.time() - t0
+    del x, y
+    torch.cuda.empty_cache()
+
+    # ---- evaluation field ----
+    L = 9
+    rho = synth.lognormal_grf_torch(1 << L, 30.0, 2.0, 200, device="cuda").contiguous()
+    box = 10 * synth.PC_CM
+    tree = colden.build_tree_uniform(rho, box)
+    torch.cuda.empty_cache()
+    n_leaf = tree.n_leaf
+    n_h = torch.empty(n_leaf * nd, device="cuda")
+    sh = torch.empty(n_leaf, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda")
+    stream = torch.cuda.current_stream()
+    P = {"fp32": colden.FP32, "bf16": colden.BF16}
+
+    def make_step(prec, learned):
+        def step():
+            colden.tree_update(tree, rho, stream=stream)
+            colden.column_density(tree, geom, n_h=n_h, shield=sh, precision=P[prec], net=net if learned else None,
+                                  stream=stream)
+        return step
+
+    step = make_step("bf16", True)
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    colden.device_status()
+    clocks = ClockSampler(local)
+    colden.stats_reset(timing=False)
+    clocks.start()
+    time.sleep(0.3)
+    ms = _time_steps(step, flush, stream, args.steps)
+    clk = clocks.stop()
+    launches = sum(colden.stats_get(k)[0] for k in range(len(colden.KERNEL_KINDS)))
+    kern = _kernel_breakdown(colden, step, flush, args.steps)
+    units = n_leaf * nd
+
+    # ---- accuracy against the exact ray-marcher on sampled leaves ----
+    g = torch.Generator(device="cpu")
+    g.manual_seed(7)
+    rows = torch.randperm(n_leaf, generator=g)[:args.ray_leaves].cuda()
+    n_ray = torch.empty((len(rows), nd), device="cuda")
+    colden.raymarch(tree, geom, n_ray, leaves=rows)
+    forms = {}
+    step()
+    torch.cuda.synchronize()
+    forms["bf16_learned"] = {"ms_per_step": ms, "value": units / (ms / 1e3),
+                             "vs_ray_marcher": _ray_scores(n_h, sh, nd, rows, n_ray)}
+    for name, prec, learned, k in (("bf16_plain", "bf16", False, args.steps), ("fp32_plain", "fp32", False, args.steps),
+                                   ("fp32_learned", "fp32", True, 1)):
+        if args.no_compare and name != "bf16_plain":
+            continue
+        st = make_step(prec, learned)
+        flush.zero_()
+        st()
+        torch.cuda.synchronize()
+        oms = _time_steps(st, flush, stream, k)
+        st()
+        torch.cuda.synchronize()
+        forms[name] = {"ms_per_step": oms, "value": units / (oms / 1e3),
+                       "vs_ray_marcher": _ray_scores(n_h, sh, nd, rows, n_ray)}
+
+    # ---- parity with the FP64 oracle on sampled leaves (seeded weights) ----
+    parity = cpu = None
+    if args.cpu_seconds > 0:
+        parity, cpu = _learned_oracle_checks(colden, synth, tree, geom, rho, box, L, args.cpu_seconds)
+
+    # ---- dominant kernel: the fused per-leaf kernel ----
+    dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
+    dom_ms = kern[dom]["ms_per_step"] / max(kern[dom]["launches_per_step"], 1)
+    hbm_peak, peak_kind = _peaks()
+    tflops_peak, tpk = _tensor_peak()
+    # algorithmic work per leaf of learned_cell_tc: tensor FLOPs of the three
+    # per-leaf products (unpadded) and the HBM bytes it must move
+    flop_leaf = 2.0 * H * ((nd + 1) + H + nd)
+    bytes_leaf = 4.0 * nd + 4 + 4 + (2.0 * H + 4.0 * nd) / 8
+    t_achieved = flop_leaf * n_leaf / (kern["learned"]["ms_per_step"] / 1e3) / 1e12 if "learned" in kern else None
+    h_achieved = bytes_leaf * n_leaf / (kern["learned"]["ms_per_step"] / 1e3) / 1e9 if "learned" in kern else None
+    roof = {"bound": "tensor", "achieved": t_achieved, "peak": tflops_peak, "unit": "TFLOP/s",
+            "frac": t_achieved / tflops_peak if t_achieved else None, "traffic": None, "kernel": "learned",
+            "kernel_ms": kern.get("learned", {}).get("ms_per_step"), "peak_kind": tpk,
+            "algo_flop_per_leaf": flop_leaf,
+            "hbm": {"achieved": h_achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": h_achieved / hbm_peak if h_achieved else None, "algo_bytes_per_leaf": bytes_leaf}}
+    if roof["hbm"]["frac"] and roof["frac"] and roof["hbm"]["frac"] > roof["frac"]:
+        roof.update({"bound": "hbm", "achieved": h_achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": roof["hbm"]["frac"]})
+    line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "learned correction (48 dirs x 8 slots + ln n -> 2 x 128 GELU -> 48) trained on "
+                                   "16 seeded 128^3 fields, evaluated on a 512^3 uniform field (10 pc, k^-11/3 "
+                                   "log-normal, mean 30, sigma_ln 2, seed 200), N_H + shield out",
+                       "precision": "bf16", "l2": "512 MB buffer written between timed steps; N_H output %.1f GB"
+                                                  % (4 * units / 1e9),
+                       "training": {"fields": n_fields, "rows_per_field": rows_per, "steps": args.train_steps,
+                                    "batch": 8192, "data_s": gen_s, "train_s": train_s,
+                                    "loss_first": float(losses[:20].mean()), "loss_last": float(losses[-200:].mean())}},
+            "gpu_launches": int(launches), "kernels": kern, "roofline": roof, "forms": forms,
+            "speedup_vs_fp32_plain": forms["fp32_plain"]["ms_per_step"] / ms if "fp32_plain" in forms else None,
+            "clocks": clk, "cpu_baseline": cpu, "error_vs_oracle": parity}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _tensor_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["bf16_tflops"]), "measured burst"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def _learned_oracle_checks(colden, synth, tree, geom, rho, box, L, cpu_seconds):
+    """Learned form vs the FP64 oracle on sampled leaves of the evaluation
+    field, with seeded weights and the oracle's own standardisation, and the
+    oracle's learned inference timed on the host cores."""
+    import torch
+    import oracle
+    from oracle import learned as ol
+    nd = geom.n_dir
+    T = oracle.Tree.uniform(rho.cpu().numpy(), box)
+    rho_np = rho.reshape(-1).cpu().numpy().astype(np.float64)
+    n_side = 1 << L
+
+    def oracle_rows(m):
+        ijk = np.stack([_compact_np(m), _compact_np(m >> 1), _compact_np(m >> 2)], axis=1)
+        _, pl = T.column_density(geom.dirs, np.full(len(m), L), ijk, per_level=L)
+        slots = ol.slots_from_levels(pl)
+        nv = rho_np[(ijk[:, 2] * n_side + ijk[:, 1]) * n_side + ijk[:, 0]]
+        return slots, nv
+
+    rng = np.random.default_rng(5)
+    ms = rng.choice(tree.n_leaf, 1000, replace=False)
+    slots, nv = oracle_rows(ms)
+    mu, sinv = ol.normaliser(ol.features(slots, nv))
+    p = synth.mlp_init(nd, 128, 21, out_scale=0.5)
+    net = colden.Net(nd, 128, p)
+    st = net.state()
+    st["mu"], st["sinv"] = mu.astype(np.float32), sinv.astype(np.float32)
+    net.load_state(st)
+    pd = ol.unpack(p.astype(np.float64), nd, 128)
+    m = np.sort(rng.choice(tree.n_leaf, 200, replace=False))
+    slots, nv = oracle_rows(m)
+    delta, _ = ol.forward(pd, st["mu"].astype(np.float64), st["sinv"].astype(np.float64), ol.features(slots, nv))
+    want = ol.apply(ol.tree_total(slots), delta)
+    out = {}
+    n_h = torch.empty(tree.n_leaf * nd, device="cuda")
+    shd = torch.empty(tree.n_leaf, device="cuda")
+    rows = torch.from_numpy(m).cuda()
+    for name, prec in (("bf16_learned", colden.BF16), ("fp32_learned", colden.FP32)):
+        colden.column_density(tree, geom, n_h=n_h, shield=shd, precision=prec, net=net)
+        torch.cuda.synchronize()
+        got = n_h.reshape(-1, nd)[rows].double().cpu().numpy()
+        rel = np.abs(got - want) / want
+        out[name] = {"n_h_rel_max": float(rel.max()), "n_h_rel_mean": float(rel.mean()),
+                     "shield_abs_max": float(np.abs(shd[rows].double().cpu().numpy() - oracle.shield(want)).max()),
+                     "delta_abs_max": float(np.abs(delta).max()), "leaves_checked": int(len(m))}
+    del n_h
+    net.free()
+    # the oracle's learned inference (per-level walk, features, FP64 network), bounded sample
+    n = 16
+    while True:
+        mm = rng.choice(tree.n_leaf, n, replace=False)
+        t0 = time.perf_counter()
+        slots, nv = oracle_rows(mm)
+        d, _ = ol.forward(pd, mu, sinv, ol.features(slots, nv))
+        ol.apply(ol.tree_total(slots), d)
+        dt = time.perf_counter() - t0
+        if dt >= cpu_seconds or n >= 2_000_000:
+            break
+        n = int(min(2_000_000, max(2 * n, n * cpu_seconds / max(dt, 1e-3) * 1.1)))
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cpu = {"value": n * nd / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "%d seeded random leaves of the 512^3 field x %d dirs: per-level walk, features, FP64 "
+                     "network (%.1f s)" % (n, nd, dt)}
+    return out, cpu
+
+
+def _compact_np(v):
+    v = np.asarray(v, dtype=np.uint64) & np.uint64(0x1249249249249249)
+    for sh, mask in ((2, 0x10c30c30c30c30c3), (4, 0x100f00f00f00f00f), (8, 0x1f0000ff0000ff),
+                     (16, 0x1f00000000ffff), (32, 0x1fffff)):
+        v = (v ^ (v >> np.uint64(sh))) & np.uint64(mask)
+    return v.astype(np.int64)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -550,7 +802,10 @@ def main():
     ap.add_argument("--level", type=int, default=8)
     ap.add_argument("--nside", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--workload", default="uniform", choices=["uniform", "amr", "batch"])
+    ap.add_argument("--workload", default="uniform", choices=["uniform", "amr", "batch", "learned"])
+    ap.add_argument("--train-rows", type=int, default=1_000_000, help="learned: training leaves per field")
+    ap.add_argument("--train-steps", type=int, default=3000, help="learned: Adam steps")
+    ap.add_argument("--ray-leaves", type=int, default=100_000, help="learned: leaves scored against the ray-marcher")
     ap.add_argument("--boxes", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=3)
     args = ap.parse_args()
@@ -562,6 +817,8 @@ def main():
         return run_batch(args)
     if args.workload == "amr":
         return run_amr(args)
+    if args.workload == "learned":
+        return run_learned(args)
     return run_ours(args)
 
 

@@ -229,10 +229,11 @@ enum {
     CD_K_SHELL = 1,        /* shell contraction of one level (FP32 or tensor core) */
     CD_K_LEAF = 2,         /* per-leaf combine + epilogue */
     CD_K_OTHER = 3,        /* geometry precompute and the rest */
-    CD_K_NET = 4,          /* the learned correction's network (FP32 GEMMs, fused tensor-core inference, Adam) */
-    CD_K_FEATURES = 5,     /* per-level inputs of the network and the learned combine */
+    CD_K_NET = 4,          /* the learned correction's network: FP32 GEMMs, Adam, per-oct tensor-core layer 1 */
+    CD_K_FEATURES = 5,     /* per-level inputs of the network and the FP32 learned combine */
     CD_K_RAYMARCH = 6,     /* exact ray-marcher */
-    CD_K_COUNT = 7
+    CD_K_LEARNED = 7,      /* fused per-leaf learned kernel (BF16 tensor cores) */
+    CD_K_COUNT = 8
 };
 /* Resets the counters; with timing != 0 later launches also record CUDA
  * events on their stream (a synchronisation happens in cd_stats_get). */

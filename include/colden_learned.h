@@ -15,7 +15,7 @@
  *            the sum of every coarser shell.
  *   x        x[s * n_dir + d] = ln max(c[s][d], 1e16 cm^-2) for s = 0..7,
  *            x[8 n_dir] = ln max(n_t, 1e-10 cm^-3)         (n_in = 8 n_dir + 1)
- *   u        (x - mu) * sinv           (fixed per-input standardisation)
+ *   u        clip((x - mu) * sinv, -8, 8)   (fixed per-input standardisation)
  *   delta    W3 gelu(W2 gelu(W1 u + b1) + b2) + b3       (n_dir values)
  *            gelu(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))
  *   N        N_tree[d] exp(delta[d]),  N_tree[d] = sum_s c[s][d] (the plain
@@ -99,7 +99,8 @@ cd_status cd_net_create(int n_dir, int hidden, const float *params, cd_net *out)
 
 /* Sets mu and sinv to the column mean and 1 / standard deviation of the n
  * rows of x (device [n][n_in]); a column whose standard deviation is at most
- * 1e-3 (an empty slot: ln of the floor in every row) gets sinv = 1.
+ * 1e-3 (an empty slot: ln of the floor in every row) gets sinv = 0, so the
+ * network ignores that input.
  * Deterministic.  Errors: CD_EINVAL (n < 1), CD_ENOMEM, CD_ECUDA. */
 cd_status cd_net_fit_normaliser(cd_net net, int64_t n, const float *x, void *stream);
 

@@ -15,7 +15,7 @@ per-direction log correction toward the exactly ray-traced column:
               of every coarser shell)
     x         [ln max(c[s, d], C_FLOOR) for s in 0..7, d in 0..n_dir-1 (s-major),
                ln max(n_t, N_FLOOR)]
-    u         (x - mu) * sinv                      (fixed input standardisation)
+    u         clip((x - mu) * sinv, -8, 8)          (fixed input standardisation)
     z1 = W1 u + b1,  a1 = gelu(z1)
     z2 = W2 a1 + b2, a2 = gelu(z2)
     delta = W3 a2 + b3                              (one value per direction)
@@ -106,18 +106,25 @@ def targets(n_ray: np.ndarray, n_tree: np.ndarray) -> np.ndarray:
     return np.log(n_ray / n_tree)
 
 
-SD_MIN = 1e-3       # columns with less spread than this (ln units) are not scaled
+SD_MIN = 1e-3       # columns with less spread than this (ln units) are ignored
+U_MAX = 8.0         # standardised inputs are clipped to [-U_MAX, U_MAX]
 
 
 def normaliser(x: np.ndarray):
     """Column mean and inverse standard deviation of a training set.  A column
-    whose standard deviation is at most SD_MIN carries no information at the
-    inputs' FP32 resolution (an empty slot is ln of the floor in every row) and
-    gets sinv = 1, so that rounding noise is not amplified."""
+    whose standard deviation is at most SD_MIN carried no information in
+    training (an empty slot is ln of the floor in every row): it gets
+    sinv = 0, so the network ignores it instead of extrapolating when a
+    deeper tree fills that slot."""
     mu = x.mean(axis=0)
     sd = np.sqrt(((x - mu) ** 2).mean(axis=0))
-    sinv = np.where(sd > SD_MIN, 1.0 / np.where(sd > SD_MIN, sd, 1.0), 1.0)
+    sinv = np.where(sd > SD_MIN, 1.0 / np.where(sd > SD_MIN, sd, 1.0), 0.0)
     return mu, sinv
+
+
+def standardise(x, mu, sinv):
+    """u = (x - mu) sinv, clipped to [-U_MAX, U_MAX]."""
+    return np.clip((x - mu) * sinv, -U_MAX, U_MAX)
 
 
 # ---------------------------------------------------------------------------
@@ -135,7 +142,7 @@ def gelu_grad(z):
 
 def forward(p: dict, mu, sinv, x: np.ndarray):
     """delta [n, n_dir] and the intermediates the backward pass needs."""
-    u = (x - mu) * sinv
+    u = standardise(x, mu, sinv)
     z1 = u @ p["W1"].T + p["b1"]
     a1 = gelu(z1)
     z2 = a1 @ p["W2"].T + p["b2"]

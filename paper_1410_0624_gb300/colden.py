@@ -35,7 +35,8 @@ EXPORTS = (
 )
 _VOID = ("cd_opts_default", "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_stats_reset", "cd_batch_free",
          "cd_adam_default", "cd_net_free", "cd_net_num_params")
-K_RESTRICT, K_SHELL, K_LEAF, K_OTHER, K_NET, K_FEATURES, K_RAYMARCH = 0, 1, 2, 3, 4, 5, 6
+K_RESTRICT, K_SHELL, K_LEAF, K_OTHER, K_NET, K_FEATURES, K_RAYMARCH, K_LEARNED = 0, 1, 2, 3, 4, 5, 6, 7
+KERNEL_KINDS = ("restrict", "shell", "leaf", "other", "net", "features", "raymarch", "learned")
 
 
 class ColdenError(RuntimeError):

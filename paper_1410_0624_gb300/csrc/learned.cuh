@@ -10,6 +10,7 @@ namespace cd {
 constexpr int kSlots = CD_NET_SLOTS;
 constexpr float kCFloor = 1e16f;    // cm^-2, floor under a level's contribution
 constexpr float kNFloor = 1e-10f;   // cm^-3, floor under the leaf density
+constexpr float kUMax = 8.f;        // standardised inputs are clipped to [-kUMax, kUMax]
 
 // Offsets of the packed parameters (floats).
 struct NetLayout {

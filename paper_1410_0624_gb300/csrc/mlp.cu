@@ -143,7 +143,7 @@ __global__ void reduce_splits(int64_t n, int Z, const float *__restrict__ part, 
     }
 }
 
-// U[r][i] = (X[row r][i] - mu[i]) sinv[i]
+// U[r][i] = (X[row r][i] - mu[i]) sinv[i], clipped to [-kUMax, kUMax]
 __global__ void gather_normalise(int64_t B, int n_in, const float *__restrict__ X, const int64_t *__restrict__ rows,
                                  const float *__restrict__ mu, const float *__restrict__ sinv, float *__restrict__ U)
 {
@@ -153,7 +153,7 @@ __global__ void gather_normalise(int64_t B, int n_in, const float *__restrict__ 
         const int64_t r = e / n_in;
         const int i = (int)(e - r * n_in);
         const int64_t src = rows ? rows[r] : r;
-        U[e] = (X[src * n_in + i] - mu[i]) * sinv[i];
+        U[e] = fminf(fmaxf((X[src * n_in + i] - mu[i]) * sinv[i], -kUMax), kUMax);
     }
 }
 
@@ -253,8 +253,8 @@ __global__ void __launch_bounds__(256) column_moments(int64_t n, int n_in, const
     }
 }
 
-// pass 0: mu = sum / n; pass 1: sinv = 1 / sqrt(sum / n), or 1 for a column
-// whose spread is at most kSdMin (no information at FP32 resolution)
+// pass 0: mu = sum / n; pass 1: sinv = 1 / sqrt(sum / n), or 0 for a column
+// whose spread is at most kSdMin (it carried no information: ignored)
 constexpr double kSdMin = 1e-3;
 
 __global__ void finish_moments(int n_in, int splits, int64_t n, const double *__restrict__ partial, int pass,
@@ -269,7 +269,7 @@ __global__ void finish_moments(int n_in, int splits, int64_t n, const double *__
         mu[col] = (float)t;
     } else {
         const double sd = sqrt(t);
-        sinv[col] = sd > kSdMin ? (float)(1.0 / sd) : 1.f;
+        sinv[col] = sd > kSdMin ? (float)(1.0 / sd) : 0.f;
     }
 }
 

@@ -212,19 +212,35 @@ struct OctArgs {
 };
 
 constexpr int kOctThreads = 256;
+constexpr int kOctUnits = 128 * kMaxNd / 8 / kOctThreads;   // (row, 8 directions) units per thread: 3
+
+// Far slots of a tile of 128 consecutive octs o0 .. o0+127 (o0 a multiple of
+// 128): Delta_l = 4 reads the 16 parents o0/8 + r/8, Delta_l = 5 the 2
+// grandparents, every coarser level one ancestor; rows 0-15, 16-17, 18 and 19
+// (the tail, Delta_l >= 7 summed) of sT.
+__device__ __forceinline__ float far_slot_entry(const OctArgs &A, int64_t o0, int row, int d, int nd)
+{
+    const int L = A.L;
+    if (row < 16) return L >= 5 ? A.C[L - 2][((o0 >> 3) + row) * nd + d] : 0.f;
+    if (row < 18) return L >= 6 ? A.C[L - 3][((o0 >> 6) + row - 16) * nd + d] : 0.f;
+    if (row == 18) return L >= 7 ? A.C[L - 4][(o0 >> 9) * nd + d] : 0.f;
+    float t = 0.f;
+    for (int dl = 7; dl <= L - 1; ++dl) t += A.C[L - dl + 2][(o0 >> (3 * (dl - 3))) * nd + d];
+    return t;
+}
 
 __global__ void __launch_bounds__(kOctThreads, 1) learned_oct_tc(OctArgs A)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const TcLayout &T = A.T;
     const int nd = T.nd, KE = T.KE;
-    unsigned char *sA = smem;                                    // [128 x KE] BF16
+    unsigned char *sA = smem;                                    // [128 x KE] BF16 operand
     unsigned char *sB = sA + align128((size_t)128 * KE * 2);     // W1e image
-    unsigned char *sO = sB + align128((size_t)128 * KE * 2);     // [128][128] BF16 output rows
-    float *sMu = reinterpret_cast<float *>(sO + 128 * kH * 2);   // [KE]
+    float *sMu = reinterpret_cast<float *>(sB + align128((size_t)128 * KE * 2));   // [KE]
     float *sSi = sMu + KE;                                       // [KE]
     float *sB1 = sSi + KE;                                       // [128]
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sB1 + kH);      // [0] weights, [1] MMA
+    float *sT = sB1 + kH;                                        // [20][nd] far slots of the tile
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sT + 20 * nd);  // [0] weights, [1] MMA
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
     int *sflag = reinterpret_cast<int *>(tslot + 1);
 
@@ -252,43 +268,73 @@ __global__ void __launch_bounds__(kOctThreads, 1) learned_oct_tc(OctArgs A)
     }
     bool weights_ready = false;
     uint32_t phase = 0;
+    const int units = 128 * (nd / 8);
 
     for (int64_t tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
         const int64_t o0 = tile * 128;
         const int rows = (int)std::min<int64_t>(128, A.n_oct - o0);
-        // build u_ext (one warp per oct row, lanes over directions)
-        for (int r = warp; r < 128; r += kOctThreads / 32) {
-            const int64_t oct = o0 + r;
-            const bool valid = r < rows;
-            for (int d = lane; d < nd; d += 32) {
-                float c[7];
+        // 1. the near slots (Delta_l = 1..3) of this thread's units: lanes take
+        //    consecutive octs, each 8 consecutive directions (two 16-byte loads
+        //    per table), all issued before anything waits on them
+        float c[kOctUnits][3][8];
 #pragma unroll
-                for (int s = 0; s < 7; ++s) c[s] = 0.f;
-                if (valid) {
-                    // slot Delta_l (tail summed into slot 7); dl is a constant
-                    // after unrolling, so c stays in registers
+        for (int j = 0; j < kOctUnits; ++j) {
+            const int u = tid + j * kOctThreads;
+            const int r = u & 127, d0 = (u >> 7) * 8;
+            const bool ok = u < units && r < rows;
 #pragma unroll
-                    for (int dl = 1; dl < CD_MAXL; ++dl) {
-                        if (dl > A.L - 1) break;
-                        const float v = dl <= 3 ? A.Et[dl][oct * nd + d]
-                                                : A.C[A.L - dl + 2][(oct >> (3 * (dl - 3))) * nd + d];
-                        c[(dl < kSlots ? dl : kSlots - 1) - 1] += v;
-                    }
-                    float tot = 0.f;
+            for (int t = 0; t < 3; ++t) {
+                if (ok && t + 1 <= A.L - 1) {
+                    const float4 *src = reinterpret_cast<const float4 *>(A.Et[t + 1] + (o0 + r) * nd + d0);
+                    const float4 a = src[0], b = src[1];
+                    c[j][t][0] = a.x; c[j][t][1] = a.y; c[j][t][2] = a.z; c[j][t][3] = a.w;
+                    c[j][t][4] = b.x; c[j][t][5] = b.y; c[j][t][6] = b.z; c[j][t][7] = b.w;
+                } else {
 #pragma unroll
-                    for (int s = 0; s < 7; ++s) tot += c[s];
-                    A.ext[oct * nd + d] = tot;
-                }
-#pragma unroll
-                for (int s = 0; s < 7; ++s) {
-                    const int k = s * nd + d;
-                    const float u = valid ? (__logf(fmaxf(c[s], kCFloor)) - sMu[k]) * sSi[k] : 0.f;
-                    *reinterpret_cast<__nv_bfloat16 *>(sA + op_off(r, k, KE)) = __float2bfloat16_rn(u);
+                    for (int q = 0; q < 8; ++q) c[j][t][q] = 0.f;
                 }
             }
-            for (int k = 7 * nd + lane; k < KE; k += 32)
-                *reinterpret_cast<__nv_bfloat16 *>(sA + op_off(r, k, KE)) = __float2bfloat16_rn(0.f);
         }
+        // 2. the far slots shared by the tile
+        for (int e = tid; e < 20 * nd; e += kOctThreads) sT[e] = far_slot_entry(A, o0, e / nd, e % nd, nd);
+        __syncthreads();
+        // 3. u_ext -> operand rows (16-byte stores, lanes on consecutive rows),
+        //    external column -> HBM
+#pragma unroll
+        for (int j = 0; j < kOctUnits; ++j) {
+            const int u = tid + j * kOctThreads;
+            if (u >= units) continue;
+            const int r = u & 127, d0 = (u >> 7) * 8;
+            const bool ok = r < rows;
+            float tot[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) tot[q] = 0.f;
+#pragma unroll
+            for (int s = 0; s < 7; ++s) {
+                float v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int d = d0 + q;
+                    const float cv = s < 3 ? c[j][s][q]
+                                           : s == 3 ? sT[(r >> 3) * nd + d]
+                                           : s == 4 ? sT[(16 + (r >> 6)) * nd + d]
+                                           : s == 5 ? sT[18 * nd + d] : sT[19 * nd + d];
+                    tot[q] += cv;
+                    const int k = s * nd + d;
+                    v[q] = ok ? fminf(fmaxf((__logf(fmaxf(cv, kCFloor)) - sMu[k]) * sSi[k], -kUMax), kUMax) : 0.f;
+                }
+                *reinterpret_cast<uint4 *>(sA + op_off(r, s * nd + d0, KE)) =
+                    make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                               pack_bf16x2(v[6], v[7]));
+            }
+            if (ok) {
+                float4 *dst = reinterpret_cast<float4 *>(A.ext + (o0 + r) * nd + d0);
+                dst[0] = make_float4(tot[0], tot[1], tot[2], tot[3]);
+                dst[1] = make_float4(tot[4], tot[5], tot[6], tot[7]);
+            }
+        }
+        for (int e = tid; e < 128 * (KE - 7 * nd); e += kOctThreads)   // K padding
+            *reinterpret_cast<__nv_bfloat16 *>(sA + op_off(e & 127, 7 * nd + (e >> 7), KE)) = __float2bfloat16_rn(0.f);
         fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
@@ -302,49 +348,46 @@ __global__ void __launch_bounds__(kOctThreads, 1) learned_oct_tc(OctArgs A)
                 ok = mbar_wait_bounded(&bar[1], phase, kMaxPolls);
             }
             if (!ok) *sflag = 1;
-            // the previous tile's output copy must have read sO
-            bulk_wait_read<0>();
         }
         phase ^= 1;
         __syncthreads();
         if (*sflag) break;
         tc_fence_after();
-        if (warp < 4) {
-            const int r = warp * 32 + lane;
-#pragma unroll 1
-            for (int c = 0; c < kH; c += 32) {
-                uint32_t v[32];
-                tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-                tmem_ld_wait();
-                uint4 *dst = reinterpret_cast<uint4 *>(sO + (size_t)r * kH * 2 + c * 2);
+        // 4. h = D + b1 -> HBM; warps w and w + 4 share TMEM lanes 32 (w % 4) ..,
+        //    taking columns 0-63 and 64-127
+        {
+            const int quarter = warp & 3, half = warp >> 2;
+            const int r = quarter * 32 + lane;
+            __nv_bfloat16 *hrow = A.h + (o0 + r) * kH + half * 64;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint4 w;
-                    w.x = pack_bf16x2(__uint_as_float(v[8 * q + 0]) + sB1[c + 8 * q + 0],
-                                      __uint_as_float(v[8 * q + 1]) + sB1[c + 8 * q + 1]);
-                    w.y = pack_bf16x2(__uint_as_float(v[8 * q + 2]) + sB1[c + 8 * q + 2],
-                                      __uint_as_float(v[8 * q + 3]) + sB1[c + 8 * q + 3]);
-                    w.z = pack_bf16x2(__uint_as_float(v[8 * q + 4]) + sB1[c + 8 * q + 4],
-                                      __uint_as_float(v[8 * q + 5]) + sB1[c + 8 * q + 5]);
-                    w.w = pack_bf16x2(__uint_as_float(v[8 * q + 6]) + sB1[c + 8 * q + 6],
-                                      __uint_as_float(v[8 * q + 7]) + sB1[c + 8 * q + 7]);
-                    dst[q] = w;
+            for (int cc = 0; cc < 64; cc += 32) {
+                const int c0 = half * 64 + cc;
+                uint32_t v[32];
+                tmem_ld32(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+                tmem_ld_wait();
+                if (r < rows) {
+                    uint4 *dst = reinterpret_cast<uint4 *>(hrow + cc);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int p2 = 0; p2 < 4; ++p2) {
+                            const int n = c0 + 8 * q + 2 * p2;
+                            w[p2] = pack_bf16x2(__uint_as_float(v[8 * q + 2 * p2]) + sB1[n],
+                                                __uint_as_float(v[8 * q + 2 * p2 + 1]) + sB1[n + 1]);
+                        }
+                        dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
+                    }
                 }
             }
         }
-        fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
-        if (tid == 0) {
-            bulk_s2g(A.h + o0 * kH, sO, (uint32_t)(rows * kH * 2));
-            bulk_commit();
-        }
     }
     if (*sflag && tid == 0) {
         atomicExch(&g_ltc_fault, 1);
         mbar_wait_bounded(&bar[1], phase ^ 1, kMaxPolls);   // let an issued chain finish
     }
-    if (tid == 0) bulk_wait_all<0>();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -373,8 +416,15 @@ constexpr int kCellThreads = 256;   // two groups of 128
 // writes at one direction fall in 32 different banks.
 __host__ __device__ constexpr int nstride(int nd) { return nd | 1; }
 
+// Shared memory of learned_cell_tc.  Per group: the operand buffer (the leaf
+// inputs [128 x KC] for MMA1, then the activations [128 x 128] for MMA2 and
+// MMA3: MMA1 has finished reading the inputs before the first activation is
+// written), the staged N rows, and two stages of the tile's inputs that bulk
+// copies bring in one tile ahead (densities of the 128 leaves, external
+// columns and layer-1 parts of their 16 octs).
 struct CellSmem {
-    size_t w1c, w2, w3, kloc, muc, sic, b2, b3, grp, grp_stride, x, a2, n, bar, total;
+    size_t w1c, w2, w3, kloc, muc, sic, b2, b3, bar, grp, grp_stride, a, n, stage, stage_bytes, st_rho, st_ext, st_h,
+        total;
     int kstride;                      // floats between kloc[t] rows
 };
 
@@ -392,15 +442,32 @@ __host__ __device__ inline CellSmem cell_smem(const TcLayout &T)
     S.sic = take((size_t)T.KC * 4);
     S.b2 = take(kH * 4);
     S.b3 = take((size_t)T.NP * 4);
-    S.bar = take(64);
+    S.bar = take(128);
     S.grp = o;
-    const size_t x = 0, a2 = align128((size_t)128 * T.KC * 2), n = a2 + align128((size_t)128 * kH * 2);
-    S.x = x;
-    S.a2 = a2;
-    S.n = n;
-    S.grp_stride = align128(n + (size_t)128 * nstride(T.nd) * 4);
+    S.a = 0;
+    S.n = align128((size_t)128 * kH * 2);
+    S.st_rho = 0;
+    S.st_ext = 128 * 4;
+    S.st_h = S.st_ext + (size_t)16 * T.nd * 4;
+    S.stage_bytes = align128(S.st_h + 16 * kH * 2);
+    S.stage = S.n + align128((size_t)128 * nstride(T.nd) * 4);
+    S.grp_stride = S.stage + 2 * S.stage_bytes;
     S.total = S.grp + 2 * S.grp_stride;
     return S;
+}
+
+// a tile's inputs: 128 densities, 16 external columns, 16 layer-1 parts
+__device__ __forceinline__ void prefetch_tile(const CellArgs &A, const CellSmem &S, int64_t tile, unsigned char *st,
+                                              uint64_t *bar)
+{
+    const int64_t c0 = tile * 128;
+    const int rows = (int)(A.n_leaf - c0 < 128 ? A.n_leaf - c0 : 128);   // a multiple of 8
+    const uint32_t b_rho = (uint32_t)rows * 4, b_ext = (uint32_t)(rows / 8) * A.T.nd * 4,
+                   b_h = (uint32_t)(rows / 8) * kH * 2;
+    mbar_expect_tx(bar, b_rho + b_ext + b_h);
+    bulk_g2s(st + S.st_rho, A.rho_leaf + c0, b_rho, bar);
+    bulk_g2s(st + S.st_ext, A.ext + (c0 >> 3) * A.T.nd, b_ext, bar);
+    bulk_g2s(st + S.st_h, A.h + (c0 >> 3) * kH, b_h, bar);
 }
 
 __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
@@ -408,7 +475,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
     extern __shared__ __align__(1024) unsigned char smem[];
     const TcLayout &T = A.T;
     const CellSmem S = cell_smem(T);
-    const int nd = T.nd, KC = T.KC, NP = T.NP;
+    const int nd = T.nd, KC = T.KC, NP = T.NP, ns = nstride(T.nd);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int g = warp >> 2, quarter = warp & 3, i = tid & 127;   // group, TMEM lane quarter, row
     float *sK = reinterpret_cast<float *>(smem + S.kloc);
@@ -416,16 +483,16 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
     const float *sSi = reinterpret_cast<const float *>(smem + S.sic);
     const float *sB2 = reinterpret_cast<const float *>(smem + S.b2);
     const float *sB3 = reinterpret_cast<const float *>(smem + S.b3);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S.bar);     // [0] weights, [1 + g] group MMAs
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 3);
+    // [0] weights, [1 + g] group MMAs, [3 + 2 g + stage] group input stages
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S.bar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 7);
     int *sflag = reinterpret_cast<int *>(tslot + 1);                  // [2] per-group fault flags
     unsigned char *G = smem + S.grp + g * S.grp_stride;
-    unsigned char *sX = G + S.x;
-    unsigned char *sA2 = G + S.a2;
+    unsigned char *sOp = G + S.a;
     float *sN = reinterpret_cast<float *>(G + S.n);
 
     if (tid == 0) {
-        for (int b = 0; b < 3; ++b) mbar_init(&bar[b], 1);
+        for (int b = 0; b < 7; ++b) mbar_init(&bar[b], 1);
         fence_mbar_init();
         sflag[0] = sflag[1] = 0;
     }
@@ -441,7 +508,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         reinterpret_cast<float *>(smem + S.b2)[k] = reinterpret_cast<const float *>(A.tc + T.b2)[k];
     for (int k = tid; k < NP; k += kCellThreads)
         reinterpret_cast<float *>(smem + S.b3)[k] = reinterpret_cast<const float *>(A.tc + T.b3)[k];
-    if (warp == 0) tmem_alloc(tslot, 512);
+    if (warp == 0) tmem_alloc(tslot, 256);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -453,12 +520,20 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         bulk_g2s(smem + S.w2, A.tc + T.w2, b2, &bar[0]);
         bulk_g2s(smem + S.w3, A.tc + T.w3, b3, &bar[0]);
     }
-    const uint32_t tD1 = tbase + (uint32_t)(g * 256), tD2 = tD1 + 128;   // D3 reuses D1's columns
+    // one accumulator of 128 columns per group: D1, D2 and D3 in turn (each
+    // is read out before the next MMA chain is issued)
+    const uint32_t tD = tbase + (uint32_t)(g * 128);
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const int bid = 1 + g;                                               // named barrier of the group
+    const int64_t first = 2 * (int64_t)blockIdx.x + g, stride = 2 * (int64_t)gridDim.x;
     bool weights_ready = false;
-    uint32_t phase = 0;
+    uint32_t phase = 0, sphase[2] = {0, 0};
+    bool pending[2] = {false, false};          // leader: a prefetch into the stage has not been waited for
     bool fault = false;
+    if (i == 0 && first < A.ntiles) {
+        prefetch_tile(A, S, first, G + S.stage, &bar[3 + 2 * g]);
+        pending[0] = true;
+    }
 
     // leader of the group: issue, commit and wait (bounded); everyone learns
     // the outcome after the group barrier
@@ -468,9 +543,9 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
             if (!weights_ready) ok = weights_ready = mbar_wait_bounded(&bar[0], 0, kMaxPolls);
             if (ok) {
                 tc_fence_after();
-                if (layer == 1) mma_chain(tD1, smem_u32(sX), smem_u32(smem + S.w1c), KC, kH);
-                else if (layer == 2) mma_chain(tD2, smem_u32(sA2), smem_u32(smem + S.w2), kH, kH);
-                else mma_chain(tD1, smem_u32(sA2), smem_u32(smem + S.w3), kH, NP);
+                if (layer == 1) mma_chain(tD, smem_u32(sOp), smem_u32(smem + S.w1c), KC, kH);
+                else if (layer == 2) mma_chain(tD, smem_u32(sOp), smem_u32(smem + S.w2), kH, kH);
+                else mma_chain(tD, smem_u32(sOp), smem_u32(smem + S.w3), kH, NP);
                 umma_commit(&bar[1 + g]);
                 ok = mbar_wait_bounded(&bar[1 + g], phase, kMaxPolls);
             }
@@ -482,21 +557,42 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         tc_fence_after();
     };
 
-    for (int64_t tile = 2 * (int64_t)blockIdx.x + g; tile < A.ntiles && !fault; tile += 2 * (int64_t)gridDim.x) {
+    int stg = 0;
+    for (int64_t tile = first; tile < A.ntiles && !fault; tile += stride, stg ^= 1) {
         const int64_t c0 = tile * 128;
         const int rows = (int)std::min<int64_t>(128, A.n_leaf - c0);
         const int64_t m = c0 + i;
         const bool valid = i < rows;
-        const int64_t oct = valid ? m >> 3 : 0;
+        unsigned char *st = G + S.stage + stg * S.stage_bytes;
+        // the next tile's inputs go to the other stage (its last reader was the
+        // previous tile, finished at that tile's final barrier)
+        if (i == 0) {
+            if (tile + stride < A.ntiles) {
+                prefetch_tile(A, S, tile + stride, G + S.stage + (stg ^ 1) * S.stage_bytes,
+                              &bar[3 + 2 * g + (stg ^ 1)]);
+                pending[stg ^ 1] = true;
+            }
+            if (mbar_wait_bounded(&bar[3 + 2 * g + stg], sphase[stg], kMaxPolls)) pending[stg] = false;
+            else sflag[g] = 1;
+        }
+        sphase[stg] ^= 1;
+        named_barrier(bid, 128);
+        if (sflag[g]) {
+            fault = true;
+            break;
+        }
+        const float *sR = reinterpret_cast<const float *>(st + S.st_rho);
+        const float *sE = reinterpret_cast<const float *>(st + S.st_ext) + (i >> 3) * nd;
+        const uint4 *sH = reinterpret_cast<const uint4 *>(st + S.st_h) + (i >> 3) * (kH / 8);
 
         // ---- inputs of the leaf: internal + local term, u_cell, N_tree ----
         {
             float rho8[8];
             const int t = (int)(m & 7);
 #pragma unroll
-            for (int s = 0; s < 8; ++s) rho8[s] = valid ? A.rho_leaf[oct * 8 + s] : 0.f;
+            for (int s2 = 0; s2 < 8; ++s2) rho8[s2] = valid ? sR[(i & ~7) + s2] : 0.f;
             const float *Kt = sK + t * S.kstride;
-            float *nrow = sN + (size_t)i * nstride(nd);
+            float *nrow = sN + (size_t)i * ns;
             for (int d0 = 0; d0 < KC; d0 += 8) {
                 float u[8];
 #pragma unroll
@@ -506,21 +602,18 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
                     if (d < nd) {
                         float loc = 0.f;
 #pragma unroll
-                        for (int s = 0; s < 8; ++s) loc = fmaf(rho8[s], Kt[s * nd + d], loc);
+                        for (int s2 = 0; s2 < 8; ++s2) loc = fmaf(rho8[s2], Kt[s2 * nd + d], loc);
                         loc *= A.dx_leaf;
-                        nrow[d] = valid ? loc + A.ext[oct * nd + d] : 0.f;
+                        nrow[d] = valid ? loc + sE[d] : 0.f;
                         v = (__logf(fmaxf(loc, kCFloor)) - sMu[d]) * sSi[d];
                     } else if (d == nd) {
-                        v = (__logf(fmaxf(valid ? A.rho_leaf[m] : 0.f, kNFloor)) - sMu[d]) * sSi[d];
+                        v = (__logf(fmaxf(valid ? sR[i] : 0.f, kNFloor)) - sMu[d]) * sSi[d];
                     }
-                    u[j] = valid ? v : 0.f;
+                    u[j] = valid ? fminf(fmaxf(v, -kUMax), kUMax) : 0.f;
                 }
-                uint4 w;
-                w.x = pack_bf16x2(u[0], u[1]);
-                w.y = pack_bf16x2(u[2], u[3]);
-                w.z = pack_bf16x2(u[4], u[5]);
-                w.w = pack_bf16x2(u[6], u[7]);
-                *reinterpret_cast<uint4 *>(sX + op_off(i, d0, KC)) = w;
+                *reinterpret_cast<uint4 *>(sOp + op_off(i, d0, KC)) =
+                    make_uint4(pack_bf16x2(u[0], u[1]), pack_bf16x2(u[2], u[3]), pack_bf16x2(u[4], u[5]),
+                               pack_bf16x2(u[6], u[7]));
             }
         }
         fence_proxy_async_smem();
@@ -529,28 +622,25 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         issue_and_wait(1);
         if (fault) break;
 
-        // ---- z1 = D1 + h[oct], a1 = gelu(z1) -> A2 ----
-        {
-            const uint4 *hrow = reinterpret_cast<const uint4 *>(A.h + oct * kH);
+        // ---- z1 = D1 + h[oct], a1 = gelu(z1) -> operand buffer ----
 #pragma unroll 1
-            for (int c = 0; c < kH; c += 32) {
-                uint32_t v[32];
-                tmem_ld32(tD1 + lane_off + (uint32_t)c, v);
-                tmem_ld_wait();
+        for (int c = 0; c < kH; c += 32) {
+            uint32_t v[32];
+            tmem_ld32(tD + lane_off + (uint32_t)c, v);
+            tmem_ld_wait();
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint4 hv = hrow[(c >> 3) + q];
-                    const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
-                    uint32_t o[4];
+            for (int q = 0; q < 4; ++q) {
+                const uint4 hv = sH[(c >> 3) + q];
+                const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+                uint32_t o[4];
 #pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162 *>(&hw[p]);
-                        const float2 hf = __bfloat1622float2(hb);
-                        o[p] = pack_bf16x2(gelu_fast(__uint_as_float(v[8 * q + 2 * p]) + hf.x),
-                                           gelu_fast(__uint_as_float(v[8 * q + 2 * p + 1]) + hf.y));
-                    }
-                    *reinterpret_cast<uint4 *>(sA2 + op_off(i, c + 8 * q, kH)) = make_uint4(o[0], o[1], o[2], o[3]);
+                for (int p2 = 0; p2 < 4; ++p2) {
+                    const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162 *>(&hw[p2]);
+                    const float2 hf = __bfloat1622float2(hb);
+                    o[p2] = pack_bf16x2(gelu_fast(__uint_as_float(v[8 * q + 2 * p2]) + hf.x),
+                                        gelu_fast(__uint_as_float(v[8 * q + 2 * p2 + 1]) + hf.y));
                 }
+                *reinterpret_cast<uint4 *>(sOp + op_off(i, c + 8 * q, kH)) = make_uint4(o[0], o[1], o[2], o[3]);
             }
         }
         fence_proxy_async_smem();
@@ -559,22 +649,22 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         issue_and_wait(2);
         if (fault) break;
 
-        // ---- a2 = gelu(D2 + b2) -> A2 (MMA2 has finished reading it) ----
+        // ---- a2 = gelu(D2 + b2) -> operand buffer (MMA2 has finished reading it) ----
 #pragma unroll 1
         for (int c = 0; c < kH; c += 32) {
             uint32_t v[32];
-            tmem_ld32(tD2 + lane_off + (uint32_t)c, v);
+            tmem_ld32(tD + lane_off + (uint32_t)c, v);
             tmem_ld_wait();
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 uint32_t o[4];
 #pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    const int n = c + 8 * q + 2 * p;
-                    o[p] = pack_bf16x2(gelu_fast(__uint_as_float(v[8 * q + 2 * p]) + sB2[n]),
-                                       gelu_fast(__uint_as_float(v[8 * q + 2 * p + 1]) + sB2[n + 1]));
+                for (int p2 = 0; p2 < 4; ++p2) {
+                    const int n = c + 8 * q + 2 * p2;
+                    o[p2] = pack_bf16x2(gelu_fast(__uint_as_float(v[8 * q + 2 * p2]) + sB2[n]),
+                                        gelu_fast(__uint_as_float(v[8 * q + 2 * p2 + 1]) + sB2[n + 1]));
                 }
-                *reinterpret_cast<uint4 *>(sA2 + op_off(i, c + 8 * q, kH)) = make_uint4(o[0], o[1], o[2], o[3]);
+                *reinterpret_cast<uint4 *>(sOp + op_off(i, c + 8 * q, kH)) = make_uint4(o[0], o[1], o[2], o[3]);
             }
         }
         fence_proxy_async_smem();
@@ -585,12 +675,12 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
 
         // ---- delta = D3 + b3; N = N_tree exp(delta); shield ----
         {
-            float *nrow = sN + (size_t)i * nstride(nd);
+            float *nrow = sN + (size_t)i * ns;
             float acc = 0.f;
 #pragma unroll 1
             for (int c = 0; c < NP; c += 32) {
                 uint32_t v[32];
-                tmem_ld32(tD1 + lane_off + (uint32_t)c, v);
+                tmem_ld32(tD + lane_off + (uint32_t)c, v);
                 tmem_ld_wait();
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
@@ -615,7 +705,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
             float *nh = A.n_h ? A.n_h + c0 * nd : nullptr;
             float *av = A.a_v ? A.a_v + c0 * nd : nullptr;
             for (int e = i; e < total; e += 128) {
-                const float N = sN[r * nstride(nd) + d];
+                const float N = sN[r * ns + d];
                 if (nh) nh[e] = N;
                 if (av) av[e] = N * A.av_per_nh;
                 r += step_r;
@@ -626,17 +716,22 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
                 }
             }
         }
-        named_barrier(bid, 128);     // sN is rewritten by the next tile
+        named_barrier(bid, 128);     // sN and the input stage are rewritten by later tiles
     }
     if (fault && i == 0) {
         atomicExch(&g_ltc_fault, 1);
         mbar_wait_bounded(&bar[1 + g], phase ^ 1, kMaxPolls);   // let an issued chain finish
     }
+    // a prefetch still in flight must land before the CTA exits
+    if (i == 0) {
+        for (int b = 0; b < 2; ++b)
+            if (pending[b]) mbar_wait_bounded(&bar[3 + 2 * g + b], sphase[b], kMaxPolls);
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tbase, 512);
+        tmem_dealloc(tbase, 256);
     }
 }
 
@@ -650,7 +745,7 @@ int num_sms()
 
 size_t oct_smem(const TcLayout &T)
 {
-    return 2 * align128((size_t)128 * T.KE * 2) + 128 * kH * 2 + (size_t)(2 * T.KE + kH) * 4 + 2 * 8 + 16;
+    return 2 * align128((size_t)128 * T.KE * 2) + (size_t)(2 * T.KE + kH + 20 * T.nd) * 4 + 2 * 8 + 16;
 }
 
 // Packs the BF16 operands when the master weights changed since the last pack.
@@ -686,7 +781,7 @@ cd_status ensure_packed(cd_net net, cudaStream_t s)
 
 }  // namespace
 
-bool learned_tc_supported(int nd, int hidden) { return hidden == kH && nd >= 1 && nd <= kMaxNd; }
+bool learned_tc_supported(int nd, int hidden) { return hidden == kH && nd >= 8 && nd <= kMaxNd && nd % 8 == 0; }
 
 cd_status column_density_learned_tc(cd_tree t, cd_geom g, const cd_opts &o, float *n_h, float *a_v, float *shield,
                                     cudaStream_t s)
@@ -694,8 +789,8 @@ cd_status column_density_learned_tc(cd_tree t, cd_geom g, const cd_opts &o, floa
     cd_net net = (cd_net)o.net;
     const int nd = g->n_dir;
     if (!learned_tc_supported(nd, net->lay.H)) {
-        set_error("the BF16 learned form needs hidden = %d and 1 <= n_dir <= %d (got %d, %d); use CD_FP32", kH,
-                  kMaxNd, net->lay.H, nd);
+        set_error("the BF16 learned form needs hidden = %d and n_dir a multiple of 8 up to %d (got %d, %d); "
+                  "use CD_FP32", kH, kMaxNd, net->lay.H, nd);
         return CD_EUNSUPPORTED;
     }
     if (t->L < 2) {
@@ -759,7 +854,7 @@ cd_status column_density_learned_tc(cd_tree t, cd_geom g, const cd_opts &o, floa
         const size_t smem = cell_smem(T).total;
         CD_CUDA(cudaFuncSetAttribute(learned_cell_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int grid = (int)std::min<int64_t>((A.ntiles + 1) / 2, sms);
-        LaunchScope ls(CD_K_FEATURES, s);
+        LaunchScope ls(CD_K_LEARNED, s);
         learned_cell_tc<<<grid, kCellThreads, smem, s>>>(A);
         CD_CHECK_LAUNCH();
     }

@@ -52,7 +52,7 @@ def test_opts_default_and_errors_without_gpu(lib):
                                       ctypes.byref(h)) == colden.CD_EUNSUPPORTED
     assert lib.cd_precompute_geometry(99, 1, 0, None, 0, 0, None, ctypes.byref(h)) == colden.CD_EINVAL
     assert lib.cd_column_density(None, None, None, None, None, None, None) == colden.CD_EINVAL
-    assert lib.cd_stats_get(7, None, None) == colden.CD_EINVAL
+    assert lib.cd_stats_get(len(colden.KERNEL_KINDS), None, None) == colden.CD_EINVAL
 
 
 def test_no_oracle_in_product_path():

@@ -133,7 +133,16 @@ def test_normaliser_moments():
     x = np.array([[1.0, 5.0, 7.0], [2.0, 5.0, 7.0 + 1e-4], [3.0, 5.0, 7.0], [4.0, 5.0, 7.0 + 1e-4]])
     mu, sinv = ol.normaliser(x)
     assert np.allclose(mu, [2.5, 5.0, 7.00005])
-    assert np.allclose(sinv, [1.0 / math.sqrt(1.25), 1.0, 1.0])
+    assert np.allclose(sinv, [1.0 / math.sqrt(1.25), 0.0, 0.0])
+
+
+def test_standardise_clips_and_ignores_constant_columns():
+    x = np.array([[0.0, 5.0], [1.0, 5.0], [100.0, 9.0]])
+    mu, sinv = ol.normaliser(x[:2])
+    u = ol.standardise(x, mu, sinv)
+    assert np.allclose(u[:2, 0], [-1.0, 1.0])
+    assert u[2, 0] == ol.U_MAX            # far outside the training range: clipped
+    assert np.all(u[:, 1] == 0.0)          # no spread in training: ignored
 
 
 # ---------------------------------------------------------------------------
