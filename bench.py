@@ -605,7 +605,7 @@ def run_learned(args):
     torch.cuda.empty_cache()
 
     # ---- evaluation field ----
-    L = 9
+    L = args.eval_level
     rho = synth.lognormal_grf_torch(1 << L, 30.0, 2.0, 200, device="cuda").contiguous()
     box = 10 * synth.PC_CM
     tree = colden.build_tree_uniform(rho, box)
@@ -694,8 +694,8 @@ def run_learned(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": "learned correction (48 dirs x 8 slots + ln n -> 2 x 128 GELU -> 48) trained on "
-                                   "16 seeded 128^3 fields, evaluated on a 512^3 uniform field (10 pc, k^-11/3 "
-                                   "log-normal, mean 30, sigma_ln 2, seed 200), N_H + shield out",
+                                   "16 seeded 128^3 fields, evaluated on a %d^3 uniform field (10 pc, k^-11/3 "
+                                   "log-normal, mean 30, sigma_ln 2, seed 200), N_H + shield out" % (1 << L),
                        "precision": "bf16", "l2": "512 MB buffer written between timed steps; N_H output %.1f GB"
                                                   % (4 * units / 1e9),
                        "training": {"fields": n_fields, "rows_per_field": rows_per, "steps": args.train_steps,
@@ -778,8 +778,8 @@ def _learned_oracle_checks(colden, synth, tree, geom, rho, box, L, cpu_seconds):
         n = int(min(2_000_000, max(2 * n, n * cpu_seconds / max(dt, 1e-3) * 1.1)))
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     cpu = {"value": n * nd / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": "%d seeded random leaves of the 512^3 field x %d dirs: per-level walk, features, FP64 "
-                     "network (%.1f s)" % (n, nd, dt)}
+           "sample": "%d seeded random leaves of the %d^3 field x %d dirs: per-level walk, features, FP64 "
+                     "network (%.1f s)" % (n, 1 << L, nd, dt)}
     return out, cpu
 
 
@@ -806,6 +806,7 @@ def main():
     ap.add_argument("--train-rows", type=int, default=1_000_000, help="learned: training leaves per field")
     ap.add_argument("--train-steps", type=int, default=3000, help="learned: Adam steps")
     ap.add_argument("--ray-leaves", type=int, default=100_000, help="learned: leaves scored against the ray-marcher")
+    ap.add_argument("--eval-level", type=int, default=9, help="learned: leaf level of the evaluation field")
     ap.add_argument("--boxes", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=3)
     args = ap.parse_args()
