@@ -205,6 +205,62 @@ __global__ void __launch_bounds__(256) leaf_list(LeafListArgs P)
 
 }  // namespace
 
+// ---- tensor-core lists -------------------------------------------------------------
+
+// Receivers (sorted Morton keys of one level, output row = position) -> their
+// distinct parents grouped by class (low six Morton bits) with the output row
+// of each child, and the tiles (128 rows, two halves) over each class.
+static cd_status build_tc_list(const std::vector<uint64_t> &recv, int32_t *recv_parent, TcList &L)
+{
+    L = TcList();
+    L.n_recv = (int64_t)recv.size();
+    L.recv_parent = recv_parent;
+    if (recv.empty()) return CD_OK;
+    std::vector<uint64_t> key;
+    std::vector<int32_t> out;
+    for (size_t i = 0; i < recv.size(); ++i) {
+        const uint64_t p = recv[i] >> 3;
+        if (key.empty() || key.back() != p) {
+            key.push_back(p);
+            out.insert(out.end(), 8, -1);
+        }
+        out[8 * (key.size() - 1) + (recv[i] & 7)] = (int32_t)i;
+    }
+    std::vector<size_t> ord(key.size());
+    std::iota(ord.begin(), ord.end(), (size_t)0);
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return (key[a] & 63) < (key[b] & 63); });
+    std::vector<uint64_t> skey(key.size());
+    std::vector<int32_t> sout(out.size());
+    for (size_t r = 0; r < ord.size(); ++r) {
+        skey[r] = key[ord[r]];
+        for (int o = 0; o < 8; ++o) sout[8 * r + o] = out[8 * ord[r] + o];
+    }
+    std::vector<int4> tiles;
+    for (size_t i = 0; i < skey.size();) {
+        const int cls = (int)(skey[i] & 63);
+        size_t j = i;
+        while (j < skey.size() && (int)(skey[j] & 63) == cls) ++j;
+        for (size_t b = i; b < j; b += 128)
+            for (int h = 0; h < 2; ++h) tiles.push_back(make_int4(cls, (int)b, (int)std::min<size_t>(128, j - b), h));
+        i = j;
+    }
+    L.nrows = (int64_t)skey.size();
+    L.ntiles = (int64_t)tiles.size();
+    if (cudaMalloc(&L.key, skey.size() * 8) != cudaSuccess || cudaMalloc(&L.out, sout.size() * 4) != cudaSuccess ||
+        cudaMalloc(&L.tiles, tiles.size() * sizeof(int4)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("tensor-core list allocation failed");
+        return CD_ENOMEM;
+    }
+    if (cudaMemcpy(L.key, skey.data(), skey.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(L.out, sout.data(), sout.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(L.tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess) {
+        set_error("tensor-core list upload failed");
+        return CD_ECUDA;
+    }
+    return CD_OK;
+}
+
 // ---- host build ------------------------------------------------------------------
 
 cd_status build_amr(cd_tree t, int base, int lmax, int64_t n, const int8_t *level, const int32_t *ijk)
@@ -358,11 +414,27 @@ cd_status build_amr(cd_tree t, int base, int lmax, int64_t n, const int8_t *leve
         if (!up((void **)&t->rho_lvl[l], nullptr, cells * 4)) return st;
         if (l >= 1 && !up((void **)&t->rho_brick[l], nullptr, cells * 2)) return st;
     }
+    // tensor-core lists of the levels the BF16 contraction serves (receiving level >= 4)
+    for (int k = 4; k <= lmax - 1; ++k) {
+        if (k <= lmax - 2 && (st = build_tc_list(ref[k], t->ref_parent[k], t->tc_ref[k])) != CD_OK) return st;
+        if ((st = build_tc_list(oct[k], nullptr, t->tc_oct[k])) != CD_OK) return st;
+    }
     t->amr = 1;
     t->L = lmax;
     t->base = base;
     t->n_leaf = n;
     return CD_OK;
+}
+
+void free_tc_lists(cd_tree t)
+{
+    for (int k = 0; k <= CD_MAXL; ++k)
+        for (TcList *L : {&t->tc_ref[k], &t->tc_oct[k]}) {
+            if (L->key) cudaFree(L->key);
+            if (L->out) cudaFree(L->out);
+            if (L->tiles) cudaFree(L->tiles);
+            *L = TcList();
+        }
 }
 
 // rho: leaf densities in the caller's order (device).
@@ -428,6 +500,8 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
         t->ws.ndir = nd;
     }
     const auto dx = [&](int l) { return (float)(t->box_cm / (double)((int64_t)1 << l)); };
+    // BF16: the tensor-core contraction over the level's receiver lists where it serves
+    const bool tc = opts.precision == CD_BF16 && tc_supported(nd) && g->wb != nullptr;
     ShellListArgs A;
     for (int q = 0; q < 4; ++q) {
         A.tab[q] = g->tab[q];
@@ -437,6 +511,19 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
     // far-shell prefixes of the refined cells
     for (int k = 3; k <= L - 2; ++k) {
         if (!t->n_ref[k]) continue;
+        if (tc && k >= 4 && t->tc_ref[k].ntiles) {
+            ExtLaunch e = {};
+            e.k = k;
+            e.nd = nd;
+            e.tmask = 4;
+            e.dx[3] = dx(k - 2);
+            e.prefix_in = (k - 1 >= 3) ? t->ws.S[k - 1] : nullptr;
+            e.out = t->ws.S[k];
+            e.list = &t->tc_ref[k];
+            cd_status st = launch_ext_tc(e, t->rho_brick, g, s);
+            if (st != CD_OK) return st;
+            continue;
+        }
         A.k = k;
         A.tmask = 4;
         for (int q = 0; q < 4; ++q) {
@@ -458,6 +545,18 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
     for (int k = 0; k <= L - 1; ++k) {
         const int64_t no = t->oct_begin[k + 1] - t->oct_begin[k];
         if (!no) continue;
+        if (tc && k >= 4 && t->tc_oct[k].ntiles) {
+            ExtLaunch e = {};
+            e.k = k;
+            e.nd = nd;
+            e.tmask = 7;
+            for (int q = 1; q <= 3; ++q) e.dx[q] = dx(k - q + 1);
+            e.out = t->ws.E + t->oct_begin[k] * nd;
+            e.list = &t->tc_oct[k];
+            cd_status st = launch_ext_tc(e, t->rho_brick, g, s);
+            if (st != CD_OK) return st;
+            continue;
+        }
         A.k = k;
         A.tmask = 0;
         for (int q = 0; q < 4; ++q) {

@@ -430,6 +430,7 @@ void cd_tree_free(cd_tree t)
     cudaDeviceSynchronize();
     free_workspace(t);
     free_level_sums(t);
+    free_tc_lists(t);
     for (int l = 0; l <= CD_MAXL; ++l) {
         if (t->rho_lvl[l]) cudaFree(t->rho_lvl[l]);
         if (t->rho_brick[l]) cudaFree(t->rho_brick[l]);

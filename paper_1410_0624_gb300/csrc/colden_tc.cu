@@ -60,7 +60,13 @@ struct TcArgs {
     float *out;                  // [8^k][nd]: the shell sum of this launch (no far-field prefix)
     float dx_k;
     int64_t nG;                  // 8^(k-3)
-    int64_t ntiles;              // 2 * 64 * ceil(nG / 128)
+    int64_t ntiles;              // 2 * 64 * ceil(nG / 128), or the list's tile count
+    // list mode (tiles != NULL, AMR meshes): tile i = {class, first row, rows,
+    // half} over row_key (parent Morton keys grouped by class); the output row
+    // of child o of row r is row_out[8 r + o] (-1: not a receiver)
+    const int4 *tiles;
+    const uint64_t *row_key;
+    const int32_t *row_out;
 };
 
 // tile -> (row block gb, class cls, half h); the two halves of one row block
@@ -146,6 +152,11 @@ __global__ void __launch_bounds__(kThreads, 2) shell_sum_tc(TcArgs P)
                 int64_t gb;
                 int cls, h;
                 tile_coords(tile, gb, cls, h);
+                if (P.tiles) {
+                    const int4 tt = P.tiles[tile];
+                    cls = tt.x;
+                    h = tt.w;
+                }
                 const unsigned char *Bc = reinterpret_cast<const unsigned char *>(P.B) + (size_t)cls * kChunks * bhalf +
                                           (size_t)h * bstage;
                 for (int j = 0; j < nchunk; ++j, ++q) {
@@ -171,8 +182,13 @@ __global__ void __launch_bounds__(kThreads, 2) shell_sum_tc(TcArgs P)
             int cls, h;
             tile_coords(tile, gb, cls, h);
             const int64_t G = gb * 128 + m;
-            const bool valid = G < P.nG;
-            const uint64_t Pm = ((uint64_t)(valid ? G : 0) << 6) | (uint64_t)cls;
+            bool valid = G < P.nG;
+            uint64_t Pm = ((uint64_t)(valid ? G : 0) << 6) | (uint64_t)cls;
+            if (P.tiles) {
+                const int4 tt = P.tiles[tile];
+                valid = m < tt.z;
+                Pm = P.row_key[tt.y + (valid ? m : 0)];
+            }
             const int px = (int)compact3(Pm), py = (int)compact3(Pm >> 1), pz = (int)compact3(Pm >> 2);
             const __nv_bfloat16 *corner[3];
             uint32_t mask[3];
@@ -228,7 +244,19 @@ __global__ void __launch_bounds__(kThreads, 2) shell_sum_tc(TcArgs P)
             int cls, h;
             tile_coords(tile, gb, cls, h);
             const int64_t G0 = gb * 128 + quarter * 32;               // the warp's first row
-            const int nrows = (int)(P.nG - G0 < 32 ? (P.nG - G0 > 0 ? P.nG - G0 : 0) : 32);
+            int nrows = (int)(P.nG - G0 < 32 ? (P.nG - G0 > 0 ? P.nG - G0 : 0) : 32);
+            int my_out[4] = {-1, -1, -1, -1};   // list mode: output rows of this lane's row, children 4h .. 4h+3
+            if (P.tiles) {
+                const int4 tt = P.tiles[tile];
+                h = tt.w;
+                nrows = tt.z - quarter * 32;
+                nrows = nrows < 0 ? 0 : (nrows > 32 ? 32 : nrows);
+                if (lane < nrows) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        my_out[j] = P.row_out[8 * (int64_t)(tt.y + quarter * 32 + lane) + 4 * h + j];
+                }
+            }
             // row r of the warp is parent P = ((G0 + r) << 6) | cls; its columns of
             // this tile are the contiguous run out[(8P + 4h) nd .. + Nt)
             float *row0 = P.out + (size_t)((((G0 << 6) | cls) * 8) + 4 * h) * P.nd;
@@ -246,10 +274,19 @@ __global__ void __launch_bounds__(kThreads, 2) shell_sum_tc(TcArgs P)
                 for (int i = 0; i < 32; ++i) T[lane * 33 + i] = __uint_as_float(v[i]);
                 __syncwarp();
                 const int col = c + lane;
-                if (col < P.Nt) {
+                if (col < P.Nt && !P.tiles) {
                     float *o = row0 + col;
 #pragma unroll 4
                     for (int r = 0; r < nrows; ++r, o += rstride) *o = P.dx_k * T[r * 33 + lane];
+                } else if (P.tiles) {
+                    // row r's output row for this lane's child, broadcast from lane r
+                    const int j = col < P.Nt ? col / P.nd : 0, d = col - j * P.nd;
+                    for (int r = 0; r < nrows; ++r) {
+                        const int o0 = __shfl_sync(0xffffffffu, my_out[0], r), o1 = __shfl_sync(0xffffffffu, my_out[1], r),
+                                  o2 = __shfl_sync(0xffffffffu, my_out[2], r), o3 = __shfl_sync(0xffffffffu, my_out[3], r);
+                        const int dst = j == 0 ? o0 : j == 1 ? o1 : j == 2 ? o2 : o3;
+                        if (col < P.Nt && dst >= 0) P.out[(int64_t)dst * P.nd + d] = P.dx_k * T[r * 33 + lane];
+                    }
                 }
                 __syncwarp();
             }
@@ -327,6 +364,16 @@ __global__ void add_parent_rows(float *__restrict__ out, const float *__restrict
     }
 }
 
+// out[i][d] += prefix[parent[i]][d] over n = n_recv nd elements
+__global__ void add_parent_list(float *__restrict__ out, const float *__restrict__ prefix,
+                                const int32_t *__restrict__ parent, int nd, int64_t n)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / nd;
+        out[e] += prefix[(int64_t)parent[i] * nd + (e - i * nd)];
+    }
+}
+
 int num_sms()
 {
     int dev = 0, n = 0;
@@ -400,6 +447,16 @@ cd_status launch_ext_tc(const ExtLaunch &a, const __nv_bfloat16 *const *brick, c
     P.dx_k = a.dx[t0] / (float)(1 << (t0 - 1));   // dx of table t's level = 2^(t-1) dx_k
     P.nG = (int64_t)1 << (3 * (a.k - 3));
     P.ntiles = 2 * 64 * ((P.nG + 127) / 128);
+    P.tiles = nullptr;
+    P.row_key = nullptr;
+    P.row_out = nullptr;
+    if (a.list) {
+        P.tiles = a.list->tiles;
+        P.row_key = a.list->key;
+        P.row_out = a.list->out;
+        P.ntiles = a.list->ntiles;
+        if (P.ntiles == 0) return CD_OK;
+    }
     const size_t bstage = (size_t)P.Nt * kChunkBricks * 16;
     const size_t smem = kStages * (kAStageBytes + bstage) + sizeof(float) * 4 * 32 * 33 + (2 * kStages + 2) * 8 + 16;
     CD_CUDA(cudaFuncSetAttribute(shell_sum_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -409,7 +466,14 @@ cd_status launch_ext_tc(const ExtLaunch &a, const __nv_bfloat16 *const *brick, c
         shell_sum_tc<<<(unsigned)grid, kThreads, smem, s>>>(P);
     }
     CD_CHECK_LAUNCH();
-    if (a.prefix_in) {
+    if (a.prefix_in && a.list) {
+        // S_k[i] += S_{k-1}[parent index of receiver i]
+        const int64_t n = a.list->n_recv * a.nd;
+        LaunchScope ls(CD_K_SHELL, s);
+        add_parent_list<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
+            a.out, a.prefix_in, a.list->recv_parent, a.nd, n);
+        CD_CHECK_LAUNCH();
+    } else if (a.prefix_in) {
         // S_k[c] += S_{k-1}[parent c]
         const int64_t n = ((int64_t)1 << (3 * a.k)) * a.nd;
         LaunchScope ls(CD_K_SHELL, s);

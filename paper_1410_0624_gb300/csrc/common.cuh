@@ -93,6 +93,20 @@ struct LevelSums {
     int64_t rows = 0;
 };
 
+// A sparse set of receiving cells of one level (AMR meshes), arranged for the
+// tensor-core shell contraction: the receivers' parents grouped by class
+// (the low six Morton bits), and the tiles over those rows.
+struct TcList {
+    int64_t n_recv = 0;          // receivers (output rows 0 .. n_recv-1)
+    int64_t nrows = 0;           // distinct parents
+    int64_t ntiles = 0;
+    uint64_t *key = nullptr;     // (device) [nrows] parent Morton keys, grouped by class
+    int32_t *out = nullptr;      // (device) [nrows][8] output row of child o, -1 if not a receiver
+    int4 *tiles = nullptr;       // (device) [ntiles] {class, first row, rows, half}
+    int32_t *recv_parent = nullptr;   // (device, borrowed) prefix row of each receiver, or NULL
+};
+
+
 }  // namespace cd
 
 struct cd_tree_s {
@@ -117,6 +131,8 @@ struct cd_tree_s {
     uint64_t *oct_key = nullptr;          // (device) Morton key of every oct at its level
     int32_t *oct_parent = nullptr;        // (device) index of the oct's parent among the refined cells
     int32_t *oct_leaf = nullptr;          // (device) [n_oct][8] output row of child o, -1 if refined
+    cd::TcList tc_ref[CD_MAXL + 1];       // tensor-core lists: refined cells of level k (far-shell prefixes)
+    cd::TcList tc_oct[CD_MAXL + 1];       // tensor-core lists: leaf-bearing octs of level k
     float *oct_rho8 = nullptr;            // (device) [n_oct][8] volume-mean density of child o
     uint64_t *leaf_key = nullptr;         // (device) output order: Morton key at the leaf's level
     int8_t *leaf_lvl = nullptr;           // (device) output order: level
@@ -171,6 +187,7 @@ cd_status restrict_uniform(cd_tree t, const float *rho_dev, cudaStream_t s);
 cd_status restrict_dense(cd_tree t, int top, cudaStream_t s);
 
 // amr.cu
+void free_tc_lists(cd_tree t);
 cd_status build_amr(cd_tree t, int base, int lmax, int64_t n, const int8_t *level, const int32_t *ijk);
 cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s);
 cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n_h, float *a_v, float *shield,
@@ -188,7 +205,8 @@ struct ExtLaunch {
     const float *rho[4];      // dense level arrays of the shell level of each table
     float dx[4];              // dx of that shell level, cm
     const float *prefix_in;   // S_{k-1} (Morton) or NULL
-    float *out;               // Morton [8^k][nd]
+    float *out;               // Morton [8^k][nd], or [n_recv][nd] with a list
+    const TcList *list;       // tensor-core form only: receivers of an AMR level (NULL: every cell of level k)
 };
 cd_status launch_ext_fp32(const ExtLaunch &a, cd_geom g, cudaStream_t s);
 

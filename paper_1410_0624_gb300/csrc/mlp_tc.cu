@@ -13,12 +13,20 @@
 //                    external column sum_s c[s] (FP32).
 //   learned_cell_tc  one GEMM row per leaf, 128 leaves per tile: the internal +
 //                    local term and u_cell on the CUDA cores, then
-//                    MMA1 (W1c) -> + h, GELU -> MMA2 (W2) -> + b2, GELU ->
-//                    MMA3 (W3) -> + b3 = delta -> N = N_tree exp(delta), A_V,
-//                    shield; N is staged in shared memory and written out by
-//                    coalesced stores.
-//                    Two independent groups of four warps share the weights,
-//                    so one group's CUDA-core work overlaps the other's MMAs.
+//                    MMA1 (W1c, + h) -> GELU -> MMA2 (W2, + b2) -> GELU ->
+//                    MMA3 (W3, + b3) = delta log2(e) -> N = N_tree 2^(...),
+//                    A_V and the shield; N is staged in shared memory and
+//                    written out by coalesced stores.  Two independent groups
+//                    of four warps share the weights, so one group's CUDA-core
+//                    work overlaps the other's MMAs.
+//
+// Additions folded into the MMAs.  Every chain ends with one extra K-step of
+// 16 whose A is a constant one-hot block, A1h[m][k] = (k == m / 8): row m
+// (leaf m of the tile) selects column m / 8, its oct.  With B[n][k] = h[oct
+// k][n] this adds h[oct(m)][n] (the tile's 16 layer-1 parts, which
+// learned_oct_tc writes directly in this operand layout); with B[n][k] = b[n]
+// for every k it adds the bias b[n].
+//
 // Every operand is K-major without swizzle: element (row, k) of a [rows x K]
 // tile sits at byte (row/8) (K/8) 128 + (k/8) 128 + (row%8) 16 + (k%8) 2,
 // i.e. LBO = 128 bytes along K and SBO = 16 K bytes between 8-row groups.
@@ -34,10 +42,13 @@ namespace cd {
 namespace {
 
 constexpr int kH = 128;                     // hidden width of the tensor-core form
+constexpr int kKW = kH + 16;                // K of the W2 / W3 images: 128 inputs + the bias block
 constexpr int kMaxNd = 48;
 constexpr uint32_t kMaxPolls = 1u << 26;
 constexpr float kGeluC = 0.7978845608028654f;
 constexpr float kGeluA = 0.044715f;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr int kHBlock = 128 * 16;           // BF16 elements of one tile's layer-1 block (16 octs)
 
 static __device__ int g_ltc_fault;
 
@@ -52,8 +63,8 @@ __host__ __device__ inline uint32_t op_off(int row, int k, int K)
 // Byte offsets of the packed tensor-core weights in one device buffer.
 struct TcLayout {
     int nd, NP, KC, KE, n_in;
-    size_t w1c, w1e, w2, w3;           // BF16 operand images [128 x KC], [128 x KE], [128 x 128], [NP x 128]
-    size_t b1, b2, b3;                 // FP32 [128], [128], [NP]
+    size_t w1c, w1e, w2, w3;           // BF16 operand images [128 x KC], [128 x KE], [128 x kKW], [NP x kKW]
+    size_t b1;                         // FP32 [128]
     size_t muc, sic, mue, sie;         // FP32 standardisation of the cell inputs [KC] and external inputs [KE]
     size_t total;
 };
@@ -70,11 +81,9 @@ TcLayout make_layout(int nd)
     auto take = [&](size_t bytes) { const size_t r = o; o = align128(o + bytes); return r; };
     T.w1c = take((size_t)kH * T.KC * 2);
     T.w1e = take((size_t)kH * T.KE * 2);
-    T.w2 = take((size_t)kH * kH * 2);
-    T.w3 = take((size_t)T.NP * kH * 2);
+    T.w2 = take((size_t)kH * kKW * 2);
+    T.w3 = take((size_t)T.NP * kKW * 2);
     T.b1 = take(kH * 4);
-    T.b2 = take(kH * 4);
-    T.b3 = take((size_t)T.NP * 4);
     T.muc = take((size_t)T.KC * 4);
     T.sic = take((size_t)T.KC * 4);
     T.mue = take((size_t)T.KE * 4);
@@ -86,7 +95,7 @@ TcLayout make_layout(int nd)
 struct TcState {
     TcLayout lay;
     unsigned char *buf = nullptr;
-    __nv_bfloat16 *h = nullptr;        // [n_oct][128] per-oct layer-1 part
+    __nv_bfloat16 *h = nullptr;        // per-leaf-tile blocks [128 n x 16 octs] of the layer-1 parts
     float *ext = nullptr;              // [n_oct][nd] external column
     int64_t cap = 0;                   // octs h / ext hold
 };
@@ -101,14 +110,17 @@ struct PackArgs {
     unsigned char *buf;
 };
 
+// W3 and b3 are scaled by log2(e) so that the last chain gives delta log2(e)
+// and N = N_tree 2^(that).
 __global__ void pack_tc(PackArgs A)
 {
     const TcLayout &T = A.T;
     const NetLayout &N = A.N;
     const int nd = T.nd;
     const float *W1 = A.p + N.W1, *W2 = A.p + N.W2, *W3 = A.p + N.W3;
-    const int64_t n1c = (int64_t)kH * T.KC, n1e = (int64_t)kH * T.KE, n2 = (int64_t)kH * kH, n3 = (int64_t)T.NP * kH;
-    const int64_t total = n1c + n1e + n2 + n3 + 2 * kH + T.NP + 2 * T.KC + 2 * T.KE;
+    const int64_t n1c = (int64_t)kH * T.KC, n1e = (int64_t)kH * T.KE, n2 = (int64_t)kH * kKW,
+                  n3 = (int64_t)T.NP * kKW;
+    const int64_t total = n1c + n1e + n2 + n3 + kH + 2 * T.KC + 2 * T.KE;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = e;
         if (i < n1c) {
@@ -126,30 +138,26 @@ __global__ void pack_tc(PackArgs A)
         }
         i -= n1e;
         if (i < n2) {
-            const int n = (int)(i / kH), k = (int)(i % kH);
-            reinterpret_cast<__nv_bfloat16 *>(A.buf + T.w2 + op_off(n, k, kH))[0] =
-                __float2bfloat16_rn(W2[(int64_t)n * kH + k]);
+            const int n = (int)(i / kKW), k = (int)(i % kKW);
+            const float v = k < kH ? W2[(int64_t)n * kH + k] : A.p[N.b2 + n];
+            reinterpret_cast<__nv_bfloat16 *>(A.buf + T.w2 + op_off(n, k, kKW))[0] = __float2bfloat16_rn(v);
             continue;
         }
         i -= n2;
         if (i < n3) {
-            const int n = (int)(i / kH), k = (int)(i % kH);
-            const float v = n < nd ? W3[(int64_t)n * kH + k] : 0.f;
-            reinterpret_cast<__nv_bfloat16 *>(A.buf + T.w3 + op_off(n, k, kH))[0] = __float2bfloat16_rn(v);
+            const int n = (int)(i / kKW), k = (int)(i % kKW);
+            const float v = n >= nd ? 0.f : kLog2e * (k < kH ? W3[(int64_t)n * kH + k] : A.p[N.b3 + n]);
+            reinterpret_cast<__nv_bfloat16 *>(A.buf + T.w3 + op_off(n, k, kKW))[0] = __float2bfloat16_rn(v);
             continue;
         }
         i -= n3;
         if (i < kH) { reinterpret_cast<float *>(A.buf + T.b1)[i] = A.p[N.b1 + i]; continue; }
         i -= kH;
-        if (i < kH) { reinterpret_cast<float *>(A.buf + T.b2)[i] = A.p[N.b2 + i]; continue; }
-        i -= kH;
-        if (i < T.NP) { reinterpret_cast<float *>(A.buf + T.b3)[i] = i < nd ? A.p[N.b3 + i] : 0.f; continue; }
-        i -= T.NP;
         if (i < 2 * T.KC) {
             const int k = (int)(i % T.KC);
             const int src = k < nd ? k : (k == nd ? kSlots * nd : -1);
             const bool is_mu = i < T.KC;
-            const float v = src < 0 ? (is_mu ? 0.f : 1.f) : (is_mu ? A.mu[src] : A.sinv[src]);
+            const float v = src < 0 ? 0.f : (is_mu ? A.mu[src] : A.sinv[src]);
             reinterpret_cast<float *>(A.buf + (is_mu ? T.muc : T.sic))[k] = v;
             continue;
         }
@@ -157,24 +165,10 @@ __global__ void pack_tc(PackArgs A)
         {
             const int k = (int)(i % T.KE);
             const bool is_mu = i < T.KE;
-            const float v = k < 7 * nd ? (is_mu ? A.mu[nd + k] : A.sinv[nd + k]) : (is_mu ? 0.f : 1.f);
+            const float v = k < 7 * nd ? (is_mu ? A.mu[nd + k] : A.sinv[nd + k]) : 0.f;
             reinterpret_cast<float *>(A.buf + (is_mu ? T.mue : T.sie))[k] = v;
         }
     }
-}
-
-__device__ __forceinline__ float fast_tanh(float x)
-{
-    float y;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float gelu_fast(float z)
-{
-    const float inner = z * fmaf(kGeluC * kGeluA, z * z, kGeluC);
-    const float hz = 0.5f * z;
-    return fmaf(hz, fast_tanh(inner), hz);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
@@ -183,19 +177,48 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
+__device__ __forceinline__ uint32_t bf2(float v)   // a BF16 constant in both halves
+{
+    return pack_bf16x2(v, v);
+}
+
+// GELU (tanh form) of two BF16 values in packed BF16 arithmetic:
+// g = z/2 (1 + tanh(z (c + c a z^2))).  The result is an operand of the next
+// BF16 product either way.
+__device__ __forceinline__ uint32_t gelu_bf16x2(uint32_t z)
+{
+    uint32_t z2, p, inner, t, hz, g;
+    const uint32_t ca = bf2(kGeluC * kGeluA), c = bf2(kGeluC), half = bf2(0.5f);
+    asm("mul.rn.bf16x2 %0, %1, %1;" : "=r"(z2) : "r"(z));
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(p) : "r"(z2), "r"(ca), "r"(c));
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(inner) : "r"(p), "r"(z));
+    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(t) : "r"(inner));
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(hz) : "r"(z), "r"(half));
+    asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(g) : "r"(hz), "r"(t));
+    return g;
+}
+
+__device__ __forceinline__ float fast_exp2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ void named_barrier(int id, int threads)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
-// MMA chain D (+)= A[128 x K] * B[N x K]^T, K in steps of 16.
-__device__ __forceinline__ void mma_chain(uint32_t tmem_d, uint32_t a0, uint32_t b0, int K, int N)
+// D (+)= A[128 x K] * B[N x K]^T over K-steps of 16; A and B are K-major
+// images whose K (hence SBO) may differ.
+__device__ __forceinline__ void mma_steps(uint32_t tmem_d, uint32_t a0, int Ka, uint32_t b0, int Kb, int steps, int N,
+                                          bool accumulate_first)
 {
     const uint32_t idesc = umma_idesc_bf16(128, N);
-    const uint32_t sbo = (uint32_t)K * 16;
-    for (int ks = 0; ks < K / 16; ++ks)
-        umma_bf16(tmem_d, umma_smem_desc(a0 + ks * 256, 128, sbo), umma_smem_desc(b0 + ks * 256, 128, sbo), idesc,
-                  ks > 0 ? 1u : 0u);
+    for (int ks = 0; ks < steps; ++ks)
+        umma_bf16(tmem_d, umma_smem_desc(a0 + ks * 256, 128, (uint32_t)Ka * 16),
+                  umma_smem_desc(b0 + ks * 256, 128, (uint32_t)Kb * 16), idesc, (ks > 0 || accumulate_first) ? 1u : 0u);
 }
 
 // ---- per-oct part ---------------------------------------------------------------
@@ -207,7 +230,7 @@ struct OctArgs {
     int L;
     const float *Et[4];
     const float *C[CD_MAXL + 1];
-    __nv_bfloat16 *h;      // [n_oct][128]
+    __nv_bfloat16 *h;      // layer-1 blocks, kHBlock elements per 16 octs
     float *ext;            // [n_oct][nd]
 };
 
@@ -229,6 +252,12 @@ __device__ __forceinline__ float far_slot_entry(const OctArgs &A, int64_t o0, in
     return t;
 }
 
+size_t oct_smem(const TcLayout &T)
+{
+    return 2 * align128((size_t)128 * T.KE * 2) + (size_t)8 * kHBlock * 2 +
+           (size_t)(2 * T.KE + kH + 20 * T.nd) * 4 + 2 * 8 + 16;
+}
+
 __global__ void __launch_bounds__(kOctThreads, 1) learned_oct_tc(OctArgs A)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -236,7 +265,8 @@ __global__ void __launch_bounds__(kOctThreads, 1) learned_oct_tc(OctArgs A)
     const int nd = T.nd, KE = T.KE;
     unsigned char *sA = smem;                                    // [128 x KE] BF16 operand
     unsigned char *sB = sA + align128((size_t)128 * KE * 2);     // W1e image
-    float *sMu = reinterpret_cast<float *>(sB + align128((size_t)128 * KE * 2));   // [KE]
+    __nv_bfloat16 *sHb = reinterpret_cast<__nv_bfloat16 *>(sB + align128((size_t)128 * KE * 2));  // 8 h blocks
+    float *sMu = reinterpret_cast<float *>(sHb + 8 * kHBlock);  // [KE]
     float *sSi = sMu + KE;                                       // [KE]
     float *sB1 = sSi + KE;                                       // [128]
     float *sT = sB1 + kH;                                        // [20][nd] far slots of the tile
@@ -297,6 +327,8 @@ __global__ void __launch_bounds__(kOctThreads, 1) learned_oct_tc(OctArgs A)
         }
         // 2. the far slots shared by the tile
         for (int e = tid; e < 20 * nd; e += kOctThreads) sT[e] = far_slot_entry(A, o0, e / nd, e % nd, nd);
+        // the previous tile's h blocks must have been read out of sHb
+        if (tid == 0) bulk_wait_read<0>();
         __syncthreads();
         // 3. u_ext -> operand rows (16-byte stores, lanes on consecutive rows),
         //    external column -> HBM
@@ -343,7 +375,7 @@ __global__ void __launch_bounds__(kOctThreads, 1) learned_oct_tc(OctArgs A)
             if (!weights_ready) ok = weights_ready = mbar_wait_bounded(&bar[0], 0, kMaxPolls);
             if (ok) {
                 tc_fence_after();
-                mma_chain(tbase, smem_u32(sA), smem_u32(sB), KE, kH);
+                mma_steps(tbase, smem_u32(sA), KE, smem_u32(sB), KE, KE / 16, kH, false);
                 umma_commit(&bar[1]);
                 ok = mbar_wait_bounded(&bar[1], phase, kMaxPolls);
             }
@@ -353,41 +385,42 @@ __global__ void __launch_bounds__(kOctThreads, 1) learned_oct_tc(OctArgs A)
         __syncthreads();
         if (*sflag) break;
         tc_fence_after();
-        // 4. h = D + b1 -> HBM; warps w and w + 4 share TMEM lanes 32 (w % 4) ..,
-        //    taking columns 0-63 and 64-127
+        // 4. h = D + b1 -> the B-operand blocks of the per-leaf kernel: block
+        //    r / 16, element (n, r % 16); rows past the end are zero (a 0 x NaN
+        //    in the product would poison a real row).  Warps w and w + 4 share
+        //    TMEM lanes 32 (w % 4) .., taking columns 0-63 and 64-127.
         {
             const int quarter = warp & 3, half = warp >> 2;
             const int r = quarter * 32 + lane;
-            __nv_bfloat16 *hrow = A.h + (o0 + r) * kH + half * 64;
-#pragma unroll
+            unsigned char *blk = reinterpret_cast<unsigned char *>(sHb + (r >> 4) * kHBlock);
+#pragma unroll 1
             for (int cc = 0; cc < 64; cc += 32) {
                 const int c0 = half * 64 + cc;
                 uint32_t v[32];
                 tmem_ld32(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
                 tmem_ld_wait();
-                if (r < rows) {
-                    uint4 *dst = reinterpret_cast<uint4 *>(hrow + cc);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint32_t w[4];
-#pragma unroll
-                        for (int p2 = 0; p2 < 4; ++p2) {
-                            const int n = c0 + 8 * q + 2 * p2;
-                            w[p2] = pack_bf16x2(__uint_as_float(v[8 * q + 2 * p2]) + sB1[n],
-                                                __uint_as_float(v[8 * q + 2 * p2 + 1]) + sB1[n + 1]);
-                        }
-                        dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
-                    }
+                for (int q = 0; q < 32; ++q) {
+                    const int n = c0 + q;
+                    const float hv = r < rows ? __uint_as_float(v[q]) + sB1[n] : 0.f;
+                    *reinterpret_cast<__nv_bfloat16 *>(blk + op_off(n, r & 15, 16)) = __float2bfloat16_rn(hv);
                 }
             }
         }
+        fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
+        if (tid == 0) {
+            const int nblk = (rows + 15) / 16;
+            bulk_s2g(A.h + (o0 >> 4) * kHBlock, sHb, (uint32_t)(nblk * kHBlock * 2));
+            bulk_commit();
+        }
     }
     if (*sflag && tid == 0) {
         atomicExch(&g_ltc_fault, 1);
         mbar_wait_bounded(&bar[1], phase ^ 1, kMaxPolls);   // let an issued chain finish
     }
+    if (tid == 0) bulk_wait_all<0>();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -402,11 +435,11 @@ struct CellArgs {
     TcLayout T;
     const unsigned char *tc;
     int64_t n_leaf, ntiles;
-    float dx_leaf, av_per_nh, shield_k;
-    const float *rho_leaf;       // Morton
-    const float *kloc;           // [8][8][nd]
-    const __nv_bfloat16 *h;      // [n_oct][128]
-    const float *ext;            // [n_oct][nd]
+    float dx_leaf, av_per_nh, c2;    // c2 = -shield_k av_per_nh log2(e)
+    const float *rho_leaf;           // Morton
+    const float *kloc;               // [8][8][nd]
+    const __nv_bfloat16 *h;          // layer-1 blocks
+    const float *ext;                // [n_oct][nd]
     float *n_h, *a_v, *shield;
 };
 
@@ -416,14 +449,16 @@ constexpr int kCellThreads = 256;   // two groups of 128
 // writes at one direction fall in 32 different banks.
 __host__ __device__ constexpr int nstride(int nd) { return nd | 1; }
 
-// Shared memory of learned_cell_tc.  Per group: the operand buffer (the leaf
-// inputs [128 x KC] for MMA1, then the activations [128 x 128] for MMA2 and
-// MMA3: MMA1 has finished reading the inputs before the first activation is
-// written), the staged N rows, and two stages of the tile's inputs that bulk
-// copies bring in one tile ahead (densities of the 128 leaves, external
-// columns and layer-1 parts of their 16 octs).
+// Shared memory of learned_cell_tc.  Shared: the weight images, the one-hot
+// block, K_loc, the cell standardisation.  Per group: the operand buffer (the
+// leaf inputs [128 x KC] for MMA1, then the activations [128 x 128] for MMA2
+// and MMA3: MMA1 has finished reading the inputs before the first activation
+// is written), the staged N rows, and two stages of the tile's inputs that
+// bulk copies bring in one tile ahead (the 16 octs' layer-1 block, which MMA1
+// reads in place, densities of the 128 leaves and external columns of their
+// 16 octs).
 struct CellSmem {
-    size_t w1c, w2, w3, kloc, muc, sic, b2, b3, bar, grp, grp_stride, a, n, stage, stage_bytes, st_rho, st_ext, st_h,
+    size_t w1c, w2, w3, onehot, kloc, muc, sic, bar, grp, grp_stride, a, n, stage, stage_bytes, st_rho, st_ext, st_h,
         total;
     int kstride;                      // floats between kloc[t] rows
 };
@@ -435,39 +470,37 @@ __host__ __device__ inline CellSmem cell_smem(const TcLayout &T)
     auto take = [&](size_t bytes) { const size_t r = o; o = align128(o + bytes); return r; };
     S.kstride = 8 * T.nd + 4;
     S.w1c = take((size_t)kH * T.KC * 2);
-    S.w2 = take((size_t)kH * kH * 2);
-    S.w3 = take((size_t)T.NP * kH * 2);
+    S.w2 = take((size_t)kH * kKW * 2);
+    S.w3 = take((size_t)T.NP * kKW * 2);
+    S.onehot = take((size_t)kHBlock * 2);
     S.kloc = take((size_t)8 * S.kstride * 4);
     S.muc = take((size_t)T.KC * 4);
     S.sic = take((size_t)T.KC * 4);
-    S.b2 = take(kH * 4);
-    S.b3 = take((size_t)T.NP * 4);
     S.bar = take(128);
     S.grp = o;
     S.a = 0;
     S.n = align128((size_t)128 * kH * 2);
-    S.st_rho = 0;
-    S.st_ext = 128 * 4;
-    S.st_h = S.st_ext + (size_t)16 * T.nd * 4;
-    S.stage_bytes = align128(S.st_h + 16 * kH * 2);
+    S.st_h = 0;
+    S.st_rho = (size_t)kHBlock * 2;
+    S.st_ext = S.st_rho + 128 * 4;
+    S.stage_bytes = align128(S.st_ext + (size_t)16 * T.nd * 4);
     S.stage = S.n + align128((size_t)128 * nstride(T.nd) * 4);
     S.grp_stride = S.stage + 2 * S.stage_bytes;
     S.total = S.grp + 2 * S.grp_stride;
     return S;
 }
 
-// a tile's inputs: 128 densities, 16 external columns, 16 layer-1 parts
+// a tile's inputs: the layer-1 block, 128 densities, 16 external columns
 __device__ __forceinline__ void prefetch_tile(const CellArgs &A, const CellSmem &S, int64_t tile, unsigned char *st,
                                               uint64_t *bar)
 {
     const int64_t c0 = tile * 128;
     const int rows = (int)(A.n_leaf - c0 < 128 ? A.n_leaf - c0 : 128);   // a multiple of 8
-    const uint32_t b_rho = (uint32_t)rows * 4, b_ext = (uint32_t)(rows / 8) * A.T.nd * 4,
-                   b_h = (uint32_t)(rows / 8) * kH * 2;
+    const uint32_t b_rho = (uint32_t)rows * 4, b_ext = (uint32_t)(rows / 8) * A.T.nd * 4, b_h = kHBlock * 2;
     mbar_expect_tx(bar, b_rho + b_ext + b_h);
+    bulk_g2s(st + S.st_h, A.h + tile * kHBlock, b_h, bar);
     bulk_g2s(st + S.st_rho, A.rho_leaf + c0, b_rho, bar);
     bulk_g2s(st + S.st_ext, A.ext + (c0 >> 3) * A.T.nd, b_ext, bar);
-    bulk_g2s(st + S.st_h, A.h + (c0 >> 3) * kH, b_h, bar);
 }
 
 __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
@@ -481,8 +514,6 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
     float *sK = reinterpret_cast<float *>(smem + S.kloc);
     const float *sMu = reinterpret_cast<const float *>(smem + S.muc);
     const float *sSi = reinterpret_cast<const float *>(smem + S.sic);
-    const float *sB2 = reinterpret_cast<const float *>(smem + S.b2);
-    const float *sB3 = reinterpret_cast<const float *>(smem + S.b3);
     // [0] weights, [1 + g] group MMAs, [3 + 2 g + stage] group input stages
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S.bar);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 7);
@@ -504,17 +535,19 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         reinterpret_cast<float *>(smem + S.muc)[k] = reinterpret_cast<const float *>(A.tc + T.muc)[k];
         reinterpret_cast<float *>(smem + S.sic)[k] = reinterpret_cast<const float *>(A.tc + T.sic)[k];
     }
-    for (int k = tid; k < kH; k += kCellThreads)
-        reinterpret_cast<float *>(smem + S.b2)[k] = reinterpret_cast<const float *>(A.tc + T.b2)[k];
-    for (int k = tid; k < NP; k += kCellThreads)
-        reinterpret_cast<float *>(smem + S.b3)[k] = reinterpret_cast<const float *>(A.tc + T.b3)[k];
+    for (int e = tid; e < kHBlock; e += kCellThreads) {   // one-hot: row m selects column m / 8
+        const int m = e >> 4, k = e & 15;
+        *reinterpret_cast<__nv_bfloat16 *>(smem + S.onehot + op_off(m, k, 16)) =
+            __float2bfloat16_rn(k == (m >> 3) ? 1.f : 0.f);
+    }
+    fence_proxy_async_smem();
     if (warp == 0) tmem_alloc(tslot, 256);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tslot;
     if (tid == 0) {
-        const uint32_t b1 = (uint32_t)(kH * KC * 2), b2 = (uint32_t)(kH * kH * 2), b3 = (uint32_t)(NP * kH * 2);
+        const uint32_t b1 = (uint32_t)(kH * KC * 2), b2 = (uint32_t)(kH * kKW * 2), b3 = (uint32_t)(NP * kKW * 2);
         mbar_expect_tx(&bar[0], b1 + b2 + b3);
         bulk_g2s(smem + S.w1c, A.tc + T.w1c, b1, &bar[0]);
         bulk_g2s(smem + S.w2, A.tc + T.w2, b2, &bar[0]);
@@ -524,6 +557,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
     // is read out before the next MMA chain is issued)
     const uint32_t tD = tbase + (uint32_t)(g * 128);
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    const uint32_t a_op = smem_u32(sOp), a_1h = smem_u32(smem + S.onehot);
     const int bid = 1 + g;                                               // named barrier of the group
     const int64_t first = 2 * (int64_t)blockIdx.x + g, stride = 2 * (int64_t)gridDim.x;
     bool weights_ready = false;
@@ -537,15 +571,21 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
 
     // leader of the group: issue, commit and wait (bounded); everyone learns
     // the outcome after the group barrier
-    auto issue_and_wait = [&](int layer) {
+    auto issue_and_wait = [&](int layer, uint32_t h_block) {
         if (i == 0) {
             bool ok = true;
             if (!weights_ready) ok = weights_ready = mbar_wait_bounded(&bar[0], 0, kMaxPolls);
             if (ok) {
                 tc_fence_after();
-                if (layer == 1) mma_chain(tD, smem_u32(sOp), smem_u32(smem + S.w1c), KC, kH);
-                else if (layer == 2) mma_chain(tD, smem_u32(sOp), smem_u32(smem + S.w2), kH, kH);
-                else mma_chain(tD, smem_u32(sOp), smem_u32(smem + S.w3), kH, NP);
+                if (layer == 1) {
+                    mma_steps(tD, a_op, KC, smem_u32(smem + S.w1c), KC, KC / 16, kH, false);
+                    mma_steps(tD, a_1h, 16, h_block, 16, 1, kH, true);
+                } else {
+                    const uint32_t w = smem_u32(smem + (layer == 2 ? S.w2 : S.w3));
+                    const int N = layer == 2 ? kH : NP;
+                    mma_steps(tD, a_op, kH, w, kKW, kH / 16, N, false);
+                    mma_steps(tD, a_1h, 16, w + (kH / 16) * 256, kKW, 1, N, true);
+                }
                 umma_commit(&bar[1 + g]);
                 ok = mbar_wait_bounded(&bar[1 + g], phase, kMaxPolls);
             }
@@ -555,6 +595,25 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         named_barrier(bid, 128);
         fault = sflag[g] != 0;
         tc_fence_after();
+    };
+
+    // GELU of a 128-column accumulator row -> the operand buffer
+    auto gelu_row = [&]() {
+#pragma unroll 1
+        for (int c = 0; c < kH; c += 32) {
+            uint32_t v[32];
+            tmem_ld32(tD + lane_off + (uint32_t)c, v);
+            tmem_ld_wait();
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t o[4];
+#pragma unroll
+                for (int p2 = 0; p2 < 4; ++p2)
+                    o[p2] = gelu_bf16x2(pack_bf16x2(__uint_as_float(v[8 * q + 2 * p2]),
+                                                    __uint_as_float(v[8 * q + 2 * p2 + 1])));
+                *reinterpret_cast<uint4 *>(sOp + op_off(i, c + 8 * q, kH)) = make_uint4(o[0], o[1], o[2], o[3]);
+            }
+        }
     };
 
     int stg = 0;
@@ -583,7 +642,6 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         }
         const float *sR = reinterpret_cast<const float *>(st + S.st_rho);
         const float *sE = reinterpret_cast<const float *>(st + S.st_ext) + (i >> 3) * nd;
-        const uint4 *sH = reinterpret_cast<const uint4 *>(st + S.st_h) + (i >> 3) * (kH / 8);
 
         // ---- inputs of the leaf: internal + local term, u_cell, N_tree ----
         {
@@ -596,20 +654,39 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
             for (int d0 = 0; d0 < KC; d0 += 8) {
                 float u[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int d = d0 + j;
-                    float v = 0.f;
-                    if (d < nd) {
-                        float loc = 0.f;
+                for (int h4 = 0; h4 < 2; ++h4) {
+                    const int d = d0 + 4 * h4;
+                    if (d + 3 < nd) {   // four directions at once (nd is a multiple of 8)
+                        float4 loc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                        for (int s2 = 0; s2 < 8; ++s2) loc = fmaf(rho8[s2], Kt[s2 * nd + d], loc);
-                        loc *= A.dx_leaf;
-                        nrow[d] = valid ? loc + sE[d] : 0.f;
-                        v = (__logf(fmaxf(loc, kCFloor)) - sMu[d]) * sSi[d];
-                    } else if (d == nd) {
-                        v = (__logf(fmaxf(valid ? sR[i] : 0.f, kNFloor)) - sMu[d]) * sSi[d];
+                        for (int s2 = 0; s2 < 8; ++s2) {
+                            const float4 k4 = *reinterpret_cast<const float4 *>(Kt + s2 * nd + d);
+                            loc.x = fmaf(rho8[s2], k4.x, loc.x);
+                            loc.y = fmaf(rho8[s2], k4.y, loc.y);
+                            loc.z = fmaf(rho8[s2], k4.z, loc.z);
+                            loc.w = fmaf(rho8[s2], k4.w, loc.w);
+                        }
+                        const float4 e4 = *reinterpret_cast<const float4 *>(sE + d);
+                        const float4 mu4 = *reinterpret_cast<const float4 *>(sMu + d);
+                        const float4 si4 = *reinterpret_cast<const float4 *>(sSi + d);
+                        const float lv[4] = {loc.x * A.dx_leaf, loc.y * A.dx_leaf, loc.z * A.dx_leaf,
+                                             loc.w * A.dx_leaf};
+                        const float ev[4] = {e4.x, e4.y, e4.z, e4.w}, mv[4] = {mu4.x, mu4.y, mu4.z, mu4.w},
+                                    sv[4] = {si4.x, si4.y, si4.z, si4.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            nrow[d + q] = valid ? lv[q] + ev[q] : 0.f;
+                            const float x = (__logf(fmaxf(lv[q], kCFloor)) - mv[q]) * sv[q];
+                            u[4 * h4 + q] = valid ? fminf(fmaxf(x, -kUMax), kUMax) : 0.f;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            float x = 0.f;
+                            if (d + q == nd) x = (__logf(fmaxf(valid ? sR[i] : 0.f, kNFloor)) - sMu[nd]) * sSi[nd];
+                            u[4 * h4 + q] = valid ? fminf(fmaxf(x, -kUMax), kUMax) : 0.f;
+                        }
                     }
-                    u[j] = valid ? fminf(fmaxf(v, -kUMax), kUMax) : 0.f;
                 }
                 *reinterpret_cast<uint4 *>(sOp + op_off(i, d0, KC)) =
                     make_uint4(pack_bf16x2(u[0], u[1]), pack_bf16x2(u[2], u[3]), pack_bf16x2(u[4], u[5]),
@@ -619,61 +696,26 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         fence_proxy_async_smem();
         tc_fence_before();
         named_barrier(bid, 128);
-        issue_and_wait(1);
+        issue_and_wait(1, smem_u32(st + S.st_h));
         if (fault) break;
 
-        // ---- z1 = D1 + h[oct], a1 = gelu(z1) -> operand buffer ----
-#pragma unroll 1
-        for (int c = 0; c < kH; c += 32) {
-            uint32_t v[32];
-            tmem_ld32(tD + lane_off + (uint32_t)c, v);
-            tmem_ld_wait();
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint4 hv = sH[(c >> 3) + q];
-                const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
-                uint32_t o[4];
-#pragma unroll
-                for (int p2 = 0; p2 < 4; ++p2) {
-                    const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162 *>(&hw[p2]);
-                    const float2 hf = __bfloat1622float2(hb);
-                    o[p2] = pack_bf16x2(gelu_fast(__uint_as_float(v[8 * q + 2 * p2]) + hf.x),
-                                        gelu_fast(__uint_as_float(v[8 * q + 2 * p2 + 1]) + hf.y));
-                }
-                *reinterpret_cast<uint4 *>(sOp + op_off(i, c + 8 * q, kH)) = make_uint4(o[0], o[1], o[2], o[3]);
-            }
-        }
+        // ---- a1 = gelu(D1) (D1 includes h[oct] + b1) ----
+        gelu_row();
         fence_proxy_async_smem();
         tc_fence_before();
         named_barrier(bid, 128);
-        issue_and_wait(2);
+        issue_and_wait(2, 0);
         if (fault) break;
 
-        // ---- a2 = gelu(D2 + b2) -> operand buffer (MMA2 has finished reading it) ----
-#pragma unroll 1
-        for (int c = 0; c < kH; c += 32) {
-            uint32_t v[32];
-            tmem_ld32(tD + lane_off + (uint32_t)c, v);
-            tmem_ld_wait();
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                uint32_t o[4];
-#pragma unroll
-                for (int p2 = 0; p2 < 4; ++p2) {
-                    const int n = c + 8 * q + 2 * p2;
-                    o[p2] = pack_bf16x2(gelu_fast(__uint_as_float(v[8 * q + 2 * p2]) + sB2[n]),
-                                        gelu_fast(__uint_as_float(v[8 * q + 2 * p2 + 1]) + sB2[n + 1]));
-                }
-                *reinterpret_cast<uint4 *>(sOp + op_off(i, c + 8 * q, kH)) = make_uint4(o[0], o[1], o[2], o[3]);
-            }
-        }
+        // ---- a2 = gelu(D2) (D2 includes b2; MMA2 has finished reading a1) ----
+        gelu_row();
         fence_proxy_async_smem();
         tc_fence_before();
         named_barrier(bid, 128);
-        issue_and_wait(3);
+        issue_and_wait(3, 0);
         if (fault) break;
 
-        // ---- delta = D3 + b3; N = N_tree exp(delta); shield ----
+        // ---- D3 = delta log2(e); N = N_tree 2^D3; shield ----
         {
             float *nrow = sN + (size_t)i * ns;
             float acc = 0.f;
@@ -686,11 +728,11 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
                 for (int j = 0; j < 32; ++j) {
                     const int d = c + j;
                     if (d < nd) {
-                        const float dl = __uint_as_float(v[j]) + sB3[d];
+                        const float dl = __uint_as_float(v[j]);
                         const float nt = nrow[d];
-                        const float N = isfinite(dl) ? nt * __expf(dl) : nt;
+                        const float N = isfinite(dl) ? nt * fast_exp2(dl) : nt;
                         nrow[d] = N;
-                        acc += __expf(-A.shield_k * (N * A.av_per_nh));
+                        acc += fast_exp2(A.c2 * N);
                     }
                 }
             }
@@ -743,9 +785,12 @@ int num_sms()
     return n > 0 ? n : 152;
 }
 
-size_t oct_smem(const TcLayout &T)
+int max_smem_optin()
 {
-    return 2 * align128((size_t)128 * T.KE * 2) + (size_t)(2 * T.KE + kH + 20 * T.nd) * 4 + 2 * 8 + 16;
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
 }
 
 // Packs the BF16 operands when the master weights changed since the last pack.
@@ -797,18 +842,27 @@ cd_status column_density_learned_tc(cd_tree t, cd_geom g, const cd_opts &o, floa
         set_error("the BF16 learned form needs at least two tree levels");
         return CD_EUNSUPPORTED;
     }
+    const int sms = num_sms(), smax = max_smem_optin();
+    const TcLayout lay = make_layout(nd);
+    const size_t smem_oct = oct_smem(lay), smem_cell = cell_smem(lay).total;
+    if ((int)smem_oct > smax || (int)smem_cell > smax) {
+        set_error("the learned kernels need %zu / %zu bytes of shared memory, the device offers %d", smem_oct,
+                  smem_cell, smax);
+        return CD_EUNSUPPORTED;
+    }
     cd_status st = ensure_level_sums(t, g, CD_BF16, s);
     if (st != CD_OK) return st;
     if ((st = ensure_packed(net, s)) != CD_OK) return st;
     TcState *ts = static_cast<TcState *>(net->tc);
     const TcLayout &T = ts->lay;
+    const int64_t n_blocks = (t->n_oct + 15) / 16;
     if (ts->cap < t->n_oct) {
         if (ts->h) cudaFree(ts->h);
         if (ts->ext) cudaFree(ts->ext);
         ts->h = nullptr;
         ts->ext = nullptr;
         ts->cap = 0;
-        if (cudaMalloc(&ts->h, (size_t)t->n_oct * kH * 2) != cudaSuccess ||
+        if (cudaMalloc(&ts->h, (size_t)n_blocks * kHBlock * 2) != cudaSuccess ||
             cudaMalloc(&ts->ext, (size_t)t->n_oct * nd * 4) != cudaSuccess) {
             cudaGetLastError();
             set_error("cannot allocate the per-oct buffers of the learned form");
@@ -816,7 +870,6 @@ cd_status column_density_learned_tc(cd_tree t, cd_geom g, const cd_opts &o, floa
         }
         ts->cap = t->n_oct;
     }
-    const int sms = num_sms();
     {
         OctArgs A = {};
         A.T = T;
@@ -828,11 +881,10 @@ cd_status column_density_learned_tc(cd_tree t, cd_geom g, const cd_opts &o, floa
         for (int k = 0; k <= CD_MAXL; ++k) A.C[k] = t->lv.C[k];
         A.h = ts->h;
         A.ext = ts->ext;
-        const size_t smem = oct_smem(T);
-        CD_CUDA(cudaFuncSetAttribute(learned_oct_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CD_CUDA(cudaFuncSetAttribute(learned_oct_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_oct));
         const int grid = (int)std::min<int64_t>(A.ntiles, sms);
         LaunchScope ls(CD_K_NET, s);
-        learned_oct_tc<<<grid, kOctThreads, smem, s>>>(A);
+        learned_oct_tc<<<grid, kOctThreads, smem_oct, s>>>(A);
         CD_CHECK_LAUNCH();
     }
     {
@@ -843,7 +895,7 @@ cd_status column_density_learned_tc(cd_tree t, cd_geom g, const cd_opts &o, floa
         A.ntiles = (t->n_leaf + 127) / 128;
         A.dx_leaf = (float)(t->box_cm / (double)((int64_t)1 << t->L));
         A.av_per_nh = (float)o.av_per_nh;
-        A.shield_k = (float)o.shield_k;
+        A.c2 = (float)(-o.shield_k * o.av_per_nh * 1.4426950408889634);
         A.rho_leaf = t->rho_leaf;
         A.kloc = g->kloc;
         A.h = ts->h;
@@ -851,11 +903,10 @@ cd_status column_density_learned_tc(cd_tree t, cd_geom g, const cd_opts &o, floa
         A.n_h = n_h;
         A.a_v = a_v;
         A.shield = shield;
-        const size_t smem = cell_smem(T).total;
-        CD_CUDA(cudaFuncSetAttribute(learned_cell_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CD_CUDA(cudaFuncSetAttribute(learned_cell_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cell));
         const int grid = (int)std::min<int64_t>((A.ntiles + 1) / 2, sms);
         LaunchScope ls(CD_K_LEARNED, s);
-        learned_cell_tc<<<grid, kCellThreads, smem, s>>>(A);
+        learned_cell_tc<<<grid, kCellThreads, smem_cell, s>>>(A);
         CD_CHECK_LAUNCH();
     }
     return CD_OK;

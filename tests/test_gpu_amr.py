@@ -145,3 +145,52 @@ def test_amr_1024_effective_sampled():
     got = n_h.reshape(-1, nd)[torch.from_numpy(sel).cuda()].double().cpu().numpy()
     assert np.max(np.abs(got - ref) / ref) <= RTOL
     assert np.max(np.abs(sh[torch.from_numpy(sel).cuda()].double().cpu().numpy() - oracle.shield(ref))) <= SHIELD_ATOL
+
+
+# BF16 tensor-core contraction over the AMR receiver lists (levels >= 4); the
+# tolerance of the uniform BF16 path: 1e-2 relative on N_H (BF16 densities and
+# weights, FP32 accumulation of positive terms), 5e-3 on the screening factor.
+BF16_RTOL = 1e-2
+BF16_SHIELD_ATOL = 5e-3
+
+
+@pytest.mark.parametrize("dset", [("healpix", 1, 0), ("healpix", 2, 0), ("mxn", 4, 4)])
+def test_amr_bf16_parity_all_leaves(dset):
+    fine = synth.lognormal_grf(64, 30.0, 2.0, seed=17)
+    lv = synth.amr_leaves(fine, 4, [40.0, 60.0])
+    box = 10 * PC
+    assert len(np.unique(lv["level"])) == 3
+    tree = colden.build_tree_amr(lv["base"], lv["lmax"], box, lv["level"], lv["ijk"], lv["rho"])
+    geom = colden.precompute_geometry(dset[0], dset[1], dset[2])
+    nd = geom.n_dir
+    n_h, a_v, sh = _run(tree, geom, precision=colden.BF16)
+    n32, _, _ = _run(tree, geom, precision=colden.FP32)
+    olv, oijk = tree.leaves()
+    T = oracle.Tree.amr(lv["base"], lv["lmax"], box, lv["level"], lv["ijk"], lv["rho"])
+    ref = T.column_density(geom.dirs, olv, oijk)
+    rel = np.abs(n_h.reshape(-1, nd) - ref) / ref
+    assert rel.max() <= BF16_RTOL, rel.max()
+    assert np.max(np.abs(sh - oracle.shield(ref))) <= BF16_SHIELD_ATOL
+    # the tensor cores did run (BF16 rounding differs from the FP32 path)
+    assert np.max(np.abs(n_h - n32) / n32) > 1e-5
+
+
+def test_amr_bf16_1024_effective_sampled():
+    lv = synth.amr_leaves_grf_torch(10, 7, [1e2, 1e3, 1e4], 30.0, 2.0, seed=2)
+    torch.cuda.empty_cache()
+    box = 20 * PC
+    tree = colden.build_tree_amr(7, 10, box, lv["level"], lv["ijk"], lv["rho"])
+    geom = colden.precompute_geometry("healpix", 2)
+    nd = geom.n_dir
+    n_h = torch.empty(tree.n_leaf * nd, device="cuda")
+    sh = torch.empty(tree.n_leaf, device="cuda")
+    colden.column_density(tree, geom, n_h=n_h, shield=sh, precision=colden.BF16)
+    colden.device_status()
+    olv, oijk = tree.leaves()
+    rng = np.random.default_rng(4)
+    sel = np.concatenate([rng.choice(np.nonzero(olv == l)[0], 40) for l in range(7, 11)])
+    T = oracle.Tree.amr(7, 10, box, lv["level"], lv["ijk"], lv["rho"])
+    ref = T.column_density(geom.dirs, olv[sel], oijk[sel])
+    got = n_h.reshape(-1, nd)[torch.from_numpy(sel).cuda()].double().cpu().numpy()
+    assert np.max(np.abs(got - ref) / ref) <= BF16_RTOL
+    assert np.max(np.abs(sh[torch.from_numpy(sel).cuda()].double().cpu().numpy() - oracle.shield(ref))) <= BF16_SHIELD_ATOL
