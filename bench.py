@@ -452,17 +452,42 @@ def run_amr(args):
         rows = torch.from_numpy(sel).cuda()
         err = _errors(n_h.reshape(-1, nd)[rows].double().cpu().numpy(), sh[rows].double().cpu().numpy(), ref)
     dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
+    dom_ms = kern[dom]["ms_per_step"]
+    # the other form (FP32 list kernels vs BF16 tensor-core lists), same mesh
+    other = None
+    if not args.no_compare:
+        oprec = colden.FP32 if prec == colden.BF16 else colden.BF16
+
+        def ostep():
+            colden.tree_update(tree, rho, stream=stream)
+            colden.column_density(tree, geom, n_h=n_h, shield=sh, precision=oprec, stream=stream)
+
+        for _ in range(args.warmup):
+            flush.zero_()
+            ostep()
+        torch.cuda.synchronize()
+        oms = _time_steps(ostep, flush, stream, args.steps)
+        other = {"precision": "fp32" if oprec == colden.FP32 else "bf16", "ms_per_step": oms,
+                 "value": units / (oms / 1e3), "kernels": _kernel_breakdown(colden, ostep, flush, args.steps)}
     line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "bf16" if prec == colden.BF16 else "f32", "data": "synthetic",
             "config": {"workload": "AMR: base 128^3 + 3 levels (1024^3 effective), 20 pc, k^-11/3 log-normal "
                                    "(mean 30, sigma_ln 2, seed 2), 48 HEALPix dirs, N_H + shield out",
                        "leaves": int(tree.n_leaf), "leaves_per_level": np.bincount(lv["level"])[7:].tolist(),
-                       "refined_octs": int(tree.n_oct), "precision_requested": args.precision,
-                       "note": "AMR meshes run the FP32 list kernels", "build_s": build_s},
+                       "refined_octs": int(tree.n_oct), "precision": args.precision, "build_s": build_s,
+                       "l2": "512 MB buffer written between timed steps"},
             "gpu_launches": int(launches), "kernels": kern,
+            "roofline": {"bound": "hbm", "achieved": bpu * units / (dom_ms / 1e3) / 1e9, "peak": peak,
+                         "unit": "GB/s", "frac": bpu * units / (dom_ms / 1e3) / 1e9 / peak, "traffic": None,
+                         "kernel": dom, "kernel_ms": dom_ms, "peak_kind": peak_kind,
+                         "algo_bytes_per_cell_dir": bpu, "note": "algorithmic bytes of the whole path over the "
+                                                                  "dominant kernel kind's time"},
             "step_roofline_frac": bpu * units / (ms / 1e3) / 1e9 / peak, "dominant_kernel": dom,
             "clocks": clk, "error_vs_oracle": err}
+    if other is not None:
+        line["compare"] = other
+        line["speedup_vs_" + other["precision"]] = other["ms_per_step"] / ms
     print(json.dumps(line), flush=True)
     return 0
 
