@@ -12,11 +12,12 @@
 //                    against the resident W1e, writes h (BF16) and the oct's
 //                    external column sum_s c[s] (FP32).
 //   learned_cell_tc  one GEMM row per leaf, 128 leaves per tile: the internal +
-//                    local term and u_cell on the CUDA cores, then
+//                    local term as a small MMA (the oct's 8 densities against
+//                    dx K_loc), u_cell on the CUDA cores, then
 //                    MMA1 (W1c, + h) -> GELU -> MMA2 (W2, + b2) -> GELU ->
 //                    MMA3 (W3, + b3) = delta log2(e) -> N = N_tree 2^(...),
-//                    A_V and the shield; N is staged in shared memory and
-//                    written out by coalesced stores.  Two independent groups
+//                    A_V and the shield; the tile's N rows leave as one bulk
+//                    copy.  Two independent groups
 //                    of four warps share the weights, so one group's CUDA-core
 //                    work overlaps the other's MMAs.
 //
@@ -441,26 +442,24 @@ struct CellArgs {
     const __nv_bfloat16 *h;          // layer-1 blocks
     const float *ext;                // [n_oct][nd]
     float *n_h, *a_v, *shield;
+    int vec;                         // n_h is 16-byte aligned: a tile's rows leave as one bulk copy
 };
 
 constexpr int kCellThreads = 256;   // two groups of 128
 
-// Row stride (floats) of the staged N rows: odd, so that the 32 rows a warp
-// writes at one direction fall in 32 different banks.
-__host__ __device__ constexpr int nstride(int nd) { return nd | 1; }
-
 // Shared memory of learned_cell_tc.  Shared: the weight images, the one-hot
-// block, K_loc, the cell standardisation.  Per group: the operand buffer (the
+// block, the local-term operand B_loc [NP x 64] = dx K_loc[t][s][d] at
+// k = 8 t + s, the cell standardisation.  Per group: the operand buffer (the
 // leaf inputs [128 x KC] for MMA1, then the activations [128 x 128] for MMA2
-// and MMA3: MMA1 has finished reading the inputs before the first activation
-// is written), the staged N rows, and two stages of the tile's inputs that
+// and MMA3, then the tile's N rows [128 x nd] FP32 on their way out), the
+// local-term operand A_loc [128 x 64] (row m holds its oct's 8 densities in
+// block t = m % 8, zero elsewhere), and two stages of the tile's inputs that
 // bulk copies bring in one tile ahead (the 16 octs' layer-1 block, which MMA1
 // reads in place, densities of the 128 leaves and external columns of their
 // 16 octs).
 struct CellSmem {
-    size_t w1c, w2, w3, onehot, kloc, muc, sic, bar, grp, grp_stride, a, n, stage, stage_bytes, st_rho, st_ext, st_h,
-        total;
-    int kstride;                      // floats between kloc[t] rows
+    size_t w1c, w2, w3, onehot, bloc, muc, sic, bar, grp, grp_stride, a, aloc, stage, stage_bytes, st_rho, st_ext,
+        st_h, total;
 };
 
 __host__ __device__ inline CellSmem cell_smem(const TcLayout &T)
@@ -468,23 +467,22 @@ __host__ __device__ inline CellSmem cell_smem(const TcLayout &T)
     CellSmem S;
     size_t o = 0;
     auto take = [&](size_t bytes) { const size_t r = o; o = align128(o + bytes); return r; };
-    S.kstride = 8 * T.nd + 4;
     S.w1c = take((size_t)kH * T.KC * 2);
     S.w2 = take((size_t)kH * kKW * 2);
     S.w3 = take((size_t)T.NP * kKW * 2);
     S.onehot = take((size_t)kHBlock * 2);
-    S.kloc = take((size_t)8 * S.kstride * 4);
+    S.bloc = take((size_t)T.NP * 64 * 2);
     S.muc = take((size_t)T.KC * 4);
     S.sic = take((size_t)T.KC * 4);
     S.bar = take(128);
     S.grp = o;
     S.a = 0;
-    S.n = align128((size_t)128 * kH * 2);
+    S.aloc = align128((size_t)128 * kH * 2);
     S.st_h = 0;
     S.st_rho = (size_t)kHBlock * 2;
     S.st_ext = S.st_rho + 128 * 4;
     S.stage_bytes = align128(S.st_ext + (size_t)16 * T.nd * 4);
-    S.stage = S.n + align128((size_t)128 * nstride(T.nd) * 4);
+    S.stage = S.aloc + (size_t)128 * 64 * 2;
     S.grp_stride = S.stage + 2 * S.stage_bytes;
     S.total = S.grp + 2 * S.grp_stride;
     return S;
@@ -508,10 +506,9 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
     extern __shared__ __align__(1024) unsigned char smem[];
     const TcLayout &T = A.T;
     const CellSmem S = cell_smem(T);
-    const int nd = T.nd, KC = T.KC, NP = T.NP, ns = nstride(T.nd);
+    const int nd = T.nd, KC = T.KC, NP = T.NP;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int g = warp >> 2, quarter = warp & 3, i = tid & 127;   // group, TMEM lane quarter, row
-    float *sK = reinterpret_cast<float *>(smem + S.kloc);
     const float *sMu = reinterpret_cast<const float *>(smem + S.muc);
     const float *sSi = reinterpret_cast<const float *>(smem + S.sic);
     // [0] weights, [1 + g] group MMAs, [3 + 2 g + stage] group input stages
@@ -520,16 +517,23 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
     int *sflag = reinterpret_cast<int *>(tslot + 1);                  // [2] per-group fault flags
     unsigned char *G = smem + S.grp + g * S.grp_stride;
     unsigned char *sOp = G + S.a;
-    float *sN = reinterpret_cast<float *>(G + S.n);
+    unsigned char *sAloc = G + S.aloc;
 
     if (tid == 0) {
         for (int b = 0; b < 7; ++b) mbar_init(&bar[b], 1);
         fence_mbar_init();
         sflag[0] = sflag[1] = 0;
     }
-    for (int e = tid; e < 64 * nd; e += kCellThreads) {
-        const int ts = e / nd, d = e - ts * nd;      // ts = t * 8 + s
-        sK[(ts >> 3) * S.kstride + (ts & 7) * nd + d] = A.kloc[e];
+    // B_loc[d][8 t + s] = dx K_loc[t][s][d] (directions past nd are zero)
+    for (int e = tid; e < NP * 64; e += kCellThreads) {
+        const int n = e >> 6, k = e & 63;
+        const float v = n < nd ? A.dx_leaf * A.kloc[(k >> 3) * 8 * nd + (k & 7) * nd + n] : 0.f;
+        *reinterpret_cast<__nv_bfloat16 *>(smem + S.bloc + op_off(n, k, 64)) = __float2bfloat16_rn(v);
+    }
+    // A_loc starts all zero; each tile rewrites only its rows' own blocks
+    for (int e = tid; e < 2 * 128 * 64 / 8; e += kCellThreads) {
+        const int gg = e / (128 * 8), r = e % (128 * 8);
+        reinterpret_cast<uint4 *>(smem + S.grp + gg * S.grp_stride + S.aloc)[r] = make_uint4(0, 0, 0, 0);
     }
     for (int k = tid; k < KC; k += kCellThreads) {
         reinterpret_cast<float *>(smem + S.muc)[k] = reinterpret_cast<const float *>(A.tc + T.muc)[k];
@@ -541,7 +545,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
             __float2bfloat16_rn(k == (m >> 3) ? 1.f : 0.f);
     }
     fence_proxy_async_smem();
-    if (warp == 0) tmem_alloc(tslot, 256);
+    if (warp == 0) tmem_alloc(tslot, 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -553,9 +557,9 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         bulk_g2s(smem + S.w2, A.tc + T.w2, b2, &bar[0]);
         bulk_g2s(smem + S.w3, A.tc + T.w3, b3, &bar[0]);
     }
-    // one accumulator of 128 columns per group: D1, D2 and D3 in turn (each
-    // is read out before the next MMA chain is issued)
-    const uint32_t tD = tbase + (uint32_t)(g * 128);
+    // per group 256 TMEM columns: D (128: D1, D2, D3 in turn, each read out
+    // before the next chain) and the local term (NP columns, alive through the tile)
+    const uint32_t tD = tbase + (uint32_t)(g * 256), tL = tD + 128;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const uint32_t a_op = smem_u32(sOp), a_1h = smem_u32(smem + S.onehot);
     const int bid = 1 + g;                                               // named barrier of the group
@@ -570,14 +574,16 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
     }
 
     // leader of the group: issue, commit and wait (bounded); everyone learns
-    // the outcome after the group barrier
+    // the outcome after the group barrier.  layer 0 = the local term.
     auto issue_and_wait = [&](int layer, uint32_t h_block) {
         if (i == 0) {
             bool ok = true;
             if (!weights_ready) ok = weights_ready = mbar_wait_bounded(&bar[0], 0, kMaxPolls);
             if (ok) {
                 tc_fence_after();
-                if (layer == 1) {
+                if (layer == 0) {
+                    mma_steps(tL, smem_u32(sAloc), 64, smem_u32(smem + S.bloc), 64, 4, NP, false);
+                } else if (layer == 1) {
                     mma_steps(tD, a_op, KC, smem_u32(smem + S.w1c), KC, KC / 16, kH, false);
                     mma_steps(tD, a_1h, 16, h_block, 16, 1, kH, true);
                 } else {
@@ -597,25 +603,31 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         tc_fence_after();
     };
 
-    // GELU of a 128-column accumulator row -> the operand buffer
+    // GELU of a 128-column accumulator row -> the operand buffer; two 32-column
+    // loads in flight per wait
     auto gelu_row = [&]() {
 #pragma unroll 1
-        for (int c = 0; c < kH; c += 32) {
-            uint32_t v[32];
-            tmem_ld32(tD + lane_off + (uint32_t)c, v);
+        for (int c = 0; c < kH; c += 64) {
+            uint32_t v[2][32];
+            tmem_ld32(tD + lane_off + (uint32_t)c, v[0]);
+            tmem_ld32(tD + lane_off + (uint32_t)(c + 32), v[1]);
             tmem_ld_wait();
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                uint32_t o[4];
+            for (int hh = 0; hh < 2; ++hh)
 #pragma unroll
-                for (int p2 = 0; p2 < 4; ++p2)
-                    o[p2] = gelu_bf16x2(pack_bf16x2(__uint_as_float(v[8 * q + 2 * p2]),
-                                                    __uint_as_float(v[8 * q + 2 * p2 + 1])));
-                *reinterpret_cast<uint4 *>(sOp + op_off(i, c + 8 * q, kH)) = make_uint4(o[0], o[1], o[2], o[3]);
-            }
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t o[4];
+#pragma unroll
+                    for (int p2 = 0; p2 < 4; ++p2)
+                        o[p2] = gelu_bf16x2(pack_bf16x2(__uint_as_float(v[hh][8 * q + 2 * p2]),
+                                                        __uint_as_float(v[hh][8 * q + 2 * p2 + 1])));
+                    *reinterpret_cast<uint4 *>(sOp + op_off(i, c + 32 * hh + 8 * q, kH)) =
+                        make_uint4(o[0], o[1], o[2], o[3]);
+                }
         }
     };
 
+    const bool bulk_out = A.n_h && A.vec;
     int stg = 0;
     for (int64_t tile = first; tile < A.ntiles && !fault; tile += stride, stg ^= 1) {
         const int64_t c0 = tile * 128;
@@ -624,7 +636,8 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         const bool valid = i < rows;
         unsigned char *st = G + S.stage + stg * S.stage_bytes;
         // the next tile's inputs go to the other stage (its last reader was the
-        // previous tile, finished at that tile's final barrier)
+        // previous tile, finished at that tile's final barrier); the previous
+        // tile's N rows must have left the operand buffer
         if (i == 0) {
             if (tile + stride < A.ntiles) {
                 prefetch_tile(A, S, tile + stride, G + S.stage + (stg ^ 1) * S.stage_bytes,
@@ -633,6 +646,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
             }
             if (mbar_wait_bounded(&bar[3 + 2 * g + stg], sphase[stg], kMaxPolls)) pending[stg] = false;
             else sflag[g] = 1;
+            if (bulk_out) bulk_wait_read<0>();
         }
         sphase[stg] ^= 1;
         named_barrier(bid, 128);
@@ -643,54 +657,44 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         const float *sR = reinterpret_cast<const float *>(st + S.st_rho);
         const float *sE = reinterpret_cast<const float *>(st + S.st_ext) + (i >> 3) * nd;
 
-        // ---- inputs of the leaf: internal + local term, u_cell, N_tree ----
+        // ---- local term on the tensor cores: A_loc row = the oct's 8 densities ----
         {
-            float rho8[8];
-            const int t = (int)(m & 7);
+            const float4 r0 = *reinterpret_cast<const float4 *>(sR + (i & ~7));
+            const float4 r1 = *reinterpret_cast<const float4 *>(sR + (i & ~7) + 4);
+            const uint4 w = valid ? make_uint4(pack_bf16x2(r0.x, r0.y), pack_bf16x2(r0.z, r0.w),
+                                               pack_bf16x2(r1.x, r1.y), pack_bf16x2(r1.z, r1.w))
+                                  : make_uint4(0, 0, 0, 0);
+            *reinterpret_cast<uint4 *>(sAloc + op_off(i, 8 * (i & 7), 64)) = w;
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        named_barrier(bid, 128);
+        issue_and_wait(0, 0);
+        if (fault) break;
+
+        // ---- u_cell = standardised ln(local term), ln n -> operand buffer ----
+#pragma unroll 1
+        for (int c = 0; c < KC; c += 32) {
+            uint32_t v[32];
+            if (c < NP) {
+                tmem_ld32(tL + lane_off + (uint32_t)c, v);
+                tmem_ld_wait();
+            }
 #pragma unroll
-            for (int s2 = 0; s2 < 8; ++s2) rho8[s2] = valid ? sR[(i & ~7) + s2] : 0.f;
-            const float *Kt = sK + t * S.kstride;
-            float *nrow = sN + (size_t)i * ns;
-            for (int d0 = 0; d0 < KC; d0 += 8) {
+            for (int q = 0; q < 4; ++q) {
                 float u[8];
 #pragma unroll
-                for (int h4 = 0; h4 < 2; ++h4) {
-                    const int d = d0 + 4 * h4;
-                    if (d + 3 < nd) {   // four directions at once (nd is a multiple of 8)
-                        float4 loc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                        for (int s2 = 0; s2 < 8; ++s2) {
-                            const float4 k4 = *reinterpret_cast<const float4 *>(Kt + s2 * nd + d);
-                            loc.x = fmaf(rho8[s2], k4.x, loc.x);
-                            loc.y = fmaf(rho8[s2], k4.y, loc.y);
-                            loc.z = fmaf(rho8[s2], k4.z, loc.z);
-                            loc.w = fmaf(rho8[s2], k4.w, loc.w);
-                        }
-                        const float4 e4 = *reinterpret_cast<const float4 *>(sE + d);
-                        const float4 mu4 = *reinterpret_cast<const float4 *>(sMu + d);
-                        const float4 si4 = *reinterpret_cast<const float4 *>(sSi + d);
-                        const float lv[4] = {loc.x * A.dx_leaf, loc.y * A.dx_leaf, loc.z * A.dx_leaf,
-                                             loc.w * A.dx_leaf};
-                        const float ev[4] = {e4.x, e4.y, e4.z, e4.w}, mv[4] = {mu4.x, mu4.y, mu4.z, mu4.w},
-                                    sv[4] = {si4.x, si4.y, si4.z, si4.w};
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            nrow[d + q] = valid ? lv[q] + ev[q] : 0.f;
-                            const float x = (__logf(fmaxf(lv[q], kCFloor)) - mv[q]) * sv[q];
-                            u[4 * h4 + q] = valid ? fminf(fmaxf(x, -kUMax), kUMax) : 0.f;
-                        }
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            float x = 0.f;
-                            if (d + q == nd) x = (__logf(fmaxf(valid ? sR[i] : 0.f, kNFloor)) - sMu[nd]) * sSi[nd];
-                            u[4 * h4 + q] = valid ? fminf(fmaxf(x, -kUMax), kUMax) : 0.f;
-                        }
-                    }
+                for (int j = 0; j < 8; ++j) {
+                    const int d = c + 8 * q + j;
+                    float x = 0.f;
+                    if (d < nd) x = (__logf(fmaxf(__uint_as_float(v[8 * q + j]), kCFloor)) - sMu[d]) * sSi[d];
+                    else if (d == nd) x = (__logf(fmaxf(sR[i], kNFloor)) - sMu[d]) * sSi[d];
+                    u[j] = valid ? fminf(fmaxf(x, -kUMax), kUMax) : 0.f;
                 }
-                *reinterpret_cast<uint4 *>(sOp + op_off(i, d0, KC)) =
-                    make_uint4(pack_bf16x2(u[0], u[1]), pack_bf16x2(u[2], u[3]), pack_bf16x2(u[4], u[5]),
-                               pack_bf16x2(u[6], u[7]));
+                if (c + 8 * q < KC)
+                    *reinterpret_cast<uint4 *>(sOp + op_off(i, c + 8 * q, KC)) =
+                        make_uint4(pack_bf16x2(u[0], u[1]), pack_bf16x2(u[2], u[3]), pack_bf16x2(u[4], u[5]),
+                                   pack_bf16x2(u[6], u[7]));
             }
         }
         fence_proxy_async_smem();
@@ -715,65 +719,66 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         issue_and_wait(3, 0);
         if (fault) break;
 
-        // ---- D3 = delta log2(e); N = N_tree 2^D3; shield ----
+        // ---- N = (local + external) 2^D3 -> the operand buffer as FP32 rows; shield ----
         {
-            float *nrow = sN + (size_t)i * ns;
+            float *nrow = reinterpret_cast<float *>(sOp) + (size_t)i * nd;
+            float *av = A.a_v && valid ? A.a_v + m * nd : nullptr;
+            float *nh = A.n_h && valid && !bulk_out ? A.n_h + m * nd : nullptr;
             float acc = 0.f;
 #pragma unroll 1
             for (int c = 0; c < NP; c += 32) {
-                uint32_t v[32];
+                uint32_t v[32], w[32];
                 tmem_ld32(tD + lane_off + (uint32_t)c, v);
+                tmem_ld32(tL + lane_off + (uint32_t)c, w);
                 tmem_ld_wait();
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int d = c + j;
-                    if (d < nd) {
-                        const float dl = __uint_as_float(v[j]);
-                        const float nt = nrow[d];
-                        const float N = isfinite(dl) ? nt * fast_exp2(dl) : nt;
-                        nrow[d] = N;
-                        acc += fast_exp2(A.c2 * N);
+                for (int j4 = 0; j4 < 32; j4 += 4) {
+                    if (c + j4 >= nd) break;       // nd is a multiple of 8
+                    const float4 e4 = *reinterpret_cast<const float4 *>(sE + c + j4);
+                    const float ev[4] = {e4.x, e4.y, e4.z, e4.w};
+                    float N[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float dl = __uint_as_float(v[j4 + q]);
+                        const float nt = __uint_as_float(w[j4 + q]) + ev[q];
+                        N[q] = isfinite(dl) ? nt * fast_exp2(dl) : nt;
+                        acc += fast_exp2(A.c2 * N[q]);
                     }
+                    *reinterpret_cast<float4 *>(nrow + c + j4) = make_float4(N[0], N[1], N[2], N[3]);
+                    if (nh)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) nh[c + j4 + q] = N[q];
+                    if (av)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) av[c + j4 + q] = N[q] * A.av_per_nh;
                 }
             }
             if (A.shield && valid) A.shield[m] = acc / (float)nd;
         }
+        fence_proxy_async_smem();
         tc_fence_before();
-        named_barrier(bid, 128);
-        // ---- the tile's rows of N and A_V, element e = r nd + d, coalesced ----
-        if (A.n_h || A.a_v) {
-            const int total = rows * nd, step_r = 128 / nd, step_d = 128 - (128 / nd) * nd;
-            int r = i / nd, d = i - (i / nd) * nd;
-            float *nh = A.n_h ? A.n_h + c0 * nd : nullptr;
-            float *av = A.a_v ? A.a_v + c0 * nd : nullptr;
-            for (int e = i; e < total; e += 128) {
-                const float N = sN[r * ns + d];
-                if (nh) nh[e] = N;
-                if (av) av[e] = N * A.av_per_nh;
-                r += step_r;
-                d += step_d;
-                if (d >= nd) {
-                    d -= nd;
-                    ++r;
-                }
-            }
+        named_barrier(bid, 128);     // the stage is rewritten by later tiles
+        if (bulk_out && i == 0) {
+            bulk_s2g(A.n_h + c0 * nd, sOp, (uint32_t)(rows * nd * 4));
+            bulk_commit();
         }
-        named_barrier(bid, 128);     // sN and the input stage are rewritten by later tiles
     }
     if (fault && i == 0) {
         atomicExch(&g_ltc_fault, 1);
         mbar_wait_bounded(&bar[1 + g], phase ^ 1, kMaxPolls);   // let an issued chain finish
     }
-    // a prefetch still in flight must land before the CTA exits
+    // a prefetch still in flight must land, and the output copies must have
+    // read the operand buffer, before the CTA exits
     if (i == 0) {
         for (int b = 0; b < 2; ++b)
             if (pending[b]) mbar_wait_bounded(&bar[3 + 2 * g + b], sphase[b], kMaxPolls);
+        bulk_wait_all<0>();
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tbase, 256);
+        tmem_dealloc(tbase, 512);
     }
 }
 
@@ -903,6 +908,7 @@ cd_status column_density_learned_tc(cd_tree t, cd_geom g, const cd_opts &o, floa
         A.n_h = n_h;
         A.a_v = a_v;
         A.shield = shield;
+        A.vec = (uintptr_t)n_h % 16 == 0;
         CD_CUDA(cudaFuncSetAttribute(learned_cell_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cell));
         const int grid = (int)std::min<int64_t>((A.ntiles + 1) / 2, sms);
         LaunchScope ls(CD_K_LEARNED, s);

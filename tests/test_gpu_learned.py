@@ -332,6 +332,21 @@ def test_learned_bf16_column_density_matches_oracle(L, k, dset):
     assert np.max(np.abs(gsh - wsh)) < 2e-3
 
 
+def test_learned_bf16_unaligned_outputs_match_aligned():
+    rho, tree, geom, T = _setup(5, 95)
+    nd = geom.n_dir
+    net, _ = _net(nd, 128, seed=3, scale=0.3)
+    a = torch.zeros(tree.n_leaf * nd, device="cuda")
+    colden.column_density(tree, geom, n_h=a, net=net, precision=colden.BF16)
+    big = torch.zeros(tree.n_leaf * nd + 1, device="cuda")
+    b = big[1:]                                   # 4-byte aligned only
+    av = torch.zeros(tree.n_leaf * nd + 1, device="cuda")[1:]
+    colden.column_density(tree, geom, n_h=b, a_v=av, net=net, precision=colden.BF16)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert torch.allclose(av, a / 1.87e21, rtol=1e-6, atol=0)
+
+
 def test_learned_bf16_rejects_unsupported_sizes():
     rho, tree, geom, T = _setup(5, 93)
     n_h = torch.zeros(tree.n_leaf * geom.n_dir, device="cuda")
@@ -372,7 +387,8 @@ def test_learned_falls_back_to_tree_where_delta_is_not_finite():
     assert np.all(np.isfinite(g))
     assert np.allclose(g[:, [3, 5]], q[:, [3, 5]], rtol=2e-5)
     assert not np.allclose(g[:, 0], q[:, 0], rtol=1e-3)
-    # the BF16 form falls back the same way (to its BF16 tree column)
+    # the BF16 form falls back the same way, to its own BF16 tree column (local
+    # term on the tensor cores): within the BF16 tolerance of the plain column
     p128 = synth.mlp_init(nd, 128, 7)
     off_b3 = sum(int(np.prod(s)) for _, s in ol.shapes(nd, 128)[:-1])
     p128[off_b3 + 3] = np.nan
@@ -383,7 +399,7 @@ def test_learned_falls_back_to_tree_where_delta_is_not_finite():
     g = n_h.reshape(-1, nd).cpu().numpy()
     q = plain.reshape(-1, nd).cpu().numpy()
     assert np.all(np.isfinite(g))
-    assert np.allclose(g[:, [3, 5]], q[:, [3, 5]], rtol=1e-5)
+    assert np.max(np.abs(g[:, [3, 5]] - q[:, [3, 5]]) / q[:, [3, 5]]) < 1e-2
 
 
 def test_learned_rejects_mismatched_directions_and_amr():
