@@ -49,6 +49,7 @@ constexpr uint32_t kMaxPolls = 1u << 26;
 constexpr float kGeluC = 0.7978845608028654f;
 constexpr float kGeluA = 0.044715f;
 constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
 constexpr int kHBlock = 128 * 16;           // BF16 elements of one tile's layer-1 block (16 octs)
 
 static __device__ int g_ltc_fault;
@@ -66,7 +67,8 @@ struct TcLayout {
     int nd, NP, KC, KE, n_in;
     size_t w1c, w1e, w2, w3;           // BF16 operand images [128 x KC], [128 x KE], [128 x kKW], [NP x kKW]
     size_t b1;                         // FP32 [128]
-    size_t muc, sic, mue, sie;         // FP32 standardisation of the cell inputs [KC] and external inputs [KE]
+    size_t muc, sic, mue, sie;         // FP32 standardisation u = a lg2(x) + b: a then b for the cell inputs
+                                       // [KC] and for the external inputs [KE]
     size_t total;
 };
 
@@ -154,20 +156,21 @@ __global__ void pack_tc(PackArgs A)
         i -= n3;
         if (i < kH) { reinterpret_cast<float *>(A.buf + T.b1)[i] = A.p[N.b1 + i]; continue; }
         i -= kH;
+        // standardisation as u = a lg2(x) + b: a = ln(2) sinv, b = -mu sinv
         if (i < 2 * T.KC) {
             const int k = (int)(i % T.KC);
             const int src = k < nd ? k : (k == nd ? kSlots * nd : -1);
-            const bool is_mu = i < T.KC;
-            const float v = src < 0 ? 0.f : (is_mu ? A.mu[src] : A.sinv[src]);
-            reinterpret_cast<float *>(A.buf + (is_mu ? T.muc : T.sic))[k] = v;
+            const bool is_a = i < T.KC;
+            const float v = src < 0 ? 0.f : (is_a ? kLn2 * A.sinv[src] : -A.mu[src] * A.sinv[src]);
+            reinterpret_cast<float *>(A.buf + (is_a ? T.muc : T.sic))[k] = v;
             continue;
         }
         i -= 2 * T.KC;
         {
             const int k = (int)(i % T.KE);
-            const bool is_mu = i < T.KE;
-            const float v = k < 7 * nd ? (is_mu ? A.mu[nd + k] : A.sinv[nd + k]) : 0.f;
-            reinterpret_cast<float *>(A.buf + (is_mu ? T.mue : T.sie))[k] = v;
+            const bool is_a = i < T.KE;
+            const float v = k < 7 * nd ? (is_a ? kLn2 * A.sinv[nd + k] : -A.mu[nd + k] * A.sinv[nd + k]) : 0.f;
+            reinterpret_cast<float *>(A.buf + (is_a ? T.mue : T.sie))[k] = v;
         }
     }
 }
@@ -197,6 +200,19 @@ __device__ __forceinline__ uint32_t gelu_bf16x2(uint32_t z)
     asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(hz) : "r"(z), "r"(half));
     asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(g) : "r"(hz), "r"(t));
     return g;
+}
+
+__device__ __forceinline__ float fast_log2(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// standardised, clipped input from a positive quantity: a lg2(max(x, floor)) + b
+__device__ __forceinline__ float std_input(float x, float floor_, float a, float b)
+{
+    return fminf(fmaxf(fmaf(a, fast_log2(fmaxf(x, floor_)), b), -kUMax), kUMax);
 }
 
 __device__ __forceinline__ float fast_exp2(float x)
@@ -267,8 +283,8 @@ __global__ void __launch_bounds__(kOctThreads, 1) learned_oct_tc(OctArgs A)
     unsigned char *sA = smem;                                    // [128 x KE] BF16 operand
     unsigned char *sB = sA + align128((size_t)128 * KE * 2);     // W1e image
     __nv_bfloat16 *sHb = reinterpret_cast<__nv_bfloat16 *>(sB + align128((size_t)128 * KE * 2));  // 8 h blocks
-    float *sMu = reinterpret_cast<float *>(sHb + 8 * kHBlock);  // [KE]
-    float *sSi = sMu + KE;                                       // [KE]
+    float *sMu = reinterpret_cast<float *>(sHb + 8 * kHBlock);  // [KE] standardisation a
+    float *sSi = sMu + KE;                                       // [KE] standardisation b
     float *sB1 = sSi + KE;                                       // [128]
     float *sT = sB1 + kH;                                        // [20][nd] far slots of the tile
     uint64_t *bar = reinterpret_cast<uint64_t *>(sT + 20 * nd);  // [0] weights, [1] MMA
@@ -301,13 +317,17 @@ __global__ void __launch_bounds__(kOctThreads, 1) learned_oct_tc(OctArgs A)
     uint32_t phase = 0;
     const int units = 128 * (nd / 8);
 
-    for (int64_t tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+    // Software pipeline over tiles: the loads of tile k+1 (near slots into
+    // registers, far slots into registers) are issued right after tile k's
+    // operand is built, so they are in flight during tile k's MMA and epilogue.
+    float c[kOctUnits][3][8];
+    float fs[(20 * kMaxNd + kOctThreads - 1) / kOctThreads];
+    auto issue_loads = [&](int64_t tile) {
         const int64_t o0 = tile * 128;
         const int rows = (int)std::min<int64_t>(128, A.n_oct - o0);
-        // 1. the near slots (Delta_l = 1..3) of this thread's units: lanes take
-        //    consecutive octs, each 8 consecutive directions (two 16-byte loads
-        //    per table), all issued before anything waits on them
-        float c[kOctUnits][3][8];
+        // near slots (Delta_l = 1..3) of this thread's units: lanes take
+        // consecutive octs, each 8 consecutive directions (two 16-byte loads
+        // per table)
 #pragma unroll
         for (int j = 0; j < kOctUnits; ++j) {
             const int u = tid + j * kOctThreads;
@@ -326,8 +346,23 @@ __global__ void __launch_bounds__(kOctThreads, 1) learned_oct_tc(OctArgs A)
                 }
             }
         }
-        // 2. the far slots shared by the tile
-        for (int e = tid; e < 20 * nd; e += kOctThreads) sT[e] = far_slot_entry(A, o0, e / nd, e % nd, nd);
+        // far slots shared by the tile
+#pragma unroll
+        for (int q = 0; q < (20 * kMaxNd + kOctThreads - 1) / kOctThreads; ++q) {
+            const int e = tid + q * kOctThreads;
+            fs[q] = e < 20 * nd ? far_slot_entry(A, o0, e / nd, e % nd, nd) : 0.f;
+        }
+    };
+    if (blockIdx.x < A.ntiles) issue_loads(blockIdx.x);
+
+    for (int64_t tile = blockIdx.x; tile < A.ntiles; tile += gridDim.x) {
+        const int64_t o0 = tile * 128;
+        const int rows = (int)std::min<int64_t>(128, A.n_oct - o0);
+#pragma unroll
+        for (int q = 0; q < (20 * kMaxNd + kOctThreads - 1) / kOctThreads; ++q) {
+            const int e = tid + q * kOctThreads;
+            if (e < 20 * nd) sT[e] = fs[q];
+        }
         // the previous tile's h blocks must have been read out of sHb
         if (tid == 0) bulk_wait_read<0>();
         __syncthreads();
@@ -344,17 +379,28 @@ __global__ void __launch_bounds__(kOctThreads, 1) learned_oct_tc(OctArgs A)
             for (int q = 0; q < 8; ++q) tot[q] = 0.f;
 #pragma unroll
             for (int s = 0; s < 7; ++s) {
-                float v[8];
+                float cv[8], a[8], b[8], v[8];
+                if (s < 3) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) cv[q] = c[j][s][q];
+                } else {
+                    const int row = s == 3 ? (r >> 3) : s == 4 ? 16 + (r >> 6) : s == 5 ? 18 : 19;
+                    const float4 x0 = *reinterpret_cast<const float4 *>(sT + row * nd + d0);
+                    const float4 x1 = *reinterpret_cast<const float4 *>(sT + row * nd + d0 + 4);
+                    cv[0] = x0.x; cv[1] = x0.y; cv[2] = x0.z; cv[3] = x0.w;
+                    cv[4] = x1.x; cv[5] = x1.y; cv[6] = x1.z; cv[7] = x1.w;
+                }
+                {
+                    const int k = s * nd + d0;
+                    const float4 a0 = *reinterpret_cast<const float4 *>(sMu + k), a1 = *reinterpret_cast<const float4 *>(sMu + k + 4);
+                    const float4 b0 = *reinterpret_cast<const float4 *>(sSi + k), b1 = *reinterpret_cast<const float4 *>(sSi + k + 4);
+                    a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w; a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+                    b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w; b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+                }
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    const int d = d0 + q;
-                    const float cv = s < 3 ? c[j][s][q]
-                                           : s == 3 ? sT[(r >> 3) * nd + d]
-                                           : s == 4 ? sT[(16 + (r >> 6)) * nd + d]
-                                           : s == 5 ? sT[18 * nd + d] : sT[19 * nd + d];
-                    tot[q] += cv;
-                    const int k = s * nd + d;
-                    v[q] = ok ? fminf(fmaxf((__logf(fmaxf(cv, kCFloor)) - sMu[k]) * sSi[k], -kUMax), kUMax) : 0.f;
+                    tot[q] += cv[q];
+                    v[q] = ok ? std_input(cv[q], kCFloor, a[q], b[q]) : 0.f;
                 }
                 *reinterpret_cast<uint4 *>(sA + op_off(r, s * nd + d0, KE)) =
                     make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
@@ -371,6 +417,7 @@ __global__ void __launch_bounds__(kOctThreads, 1) learned_oct_tc(OctArgs A)
         fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
+        if (tile + gridDim.x < A.ntiles) issue_loads(tile + gridDim.x);   // in flight during MMA + epilogue
         if (tid == 0) {
             bool ok = true;
             if (!weights_ready) ok = weights_ready = mbar_wait_bounded(&bar[0], 0, kMaxPolls);
@@ -573,10 +620,14 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         pending[0] = true;
     }
 
+    const bool bulk_out = A.n_h && A.vec;
     // leader of the group: issue, commit and wait (bounded); everyone learns
     // the outcome after the group barrier.  layer 0 = the local term.
     auto issue_and_wait = [&](int layer, uint32_t h_block) {
         if (i == 0) {
+            // the previous tile's N rows must have left the operand buffer
+            // before anyone writes it again (right after the local term)
+            if (layer == 0 && bulk_out) bulk_wait_read<0>();
             bool ok = true;
             if (!weights_ready) ok = weights_ready = mbar_wait_bounded(&bar[0], 0, kMaxPolls);
             if (ok) {
@@ -627,7 +678,6 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         }
     };
 
-    const bool bulk_out = A.n_h && A.vec;
     int stg = 0;
     for (int64_t tile = first; tile < A.ntiles && !fault; tile += stride, stg ^= 1) {
         const int64_t c0 = tile * 128;
@@ -646,7 +696,6 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
             }
             if (mbar_wait_bounded(&bar[3 + 2 * g + stg], sphase[stg], kMaxPolls)) pending[stg] = false;
             else sflag[g] = 1;
-            if (bulk_out) bulk_wait_read<0>();
         }
         sphase[stg] ^= 1;
         named_barrier(bid, 128);
@@ -672,30 +721,33 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         issue_and_wait(0, 0);
         if (fault) break;
 
-        // ---- u_cell = standardised ln(local term), ln n -> operand buffer ----
+        // ---- u_cell = standardised ln(local term) (8 directions per 16-byte
+        //      store), then ln n and the K padding ----
 #pragma unroll 1
-        for (int c = 0; c < KC; c += 32) {
+        for (int c = 0; c < nd; c += 32) {
             uint32_t v[32];
-            if (c < NP) {
-                tmem_ld32(tL + lane_off + (uint32_t)c, v);
-                tmem_ld_wait();
-            }
+            tmem_ld32(tL + lane_off + (uint32_t)c, v);
+            tmem_ld_wait();
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
+                const int d0 = c + 8 * q;
+                if (d0 >= nd) break;       // nd is a multiple of 8
+                const float4 a0 = *reinterpret_cast<const float4 *>(sMu + d0), a1 = *reinterpret_cast<const float4 *>(sMu + d0 + 4);
+                const float4 b0 = *reinterpret_cast<const float4 *>(sSi + d0), b1 = *reinterpret_cast<const float4 *>(sSi + d0 + 4);
+                const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
                 float u[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int d = c + 8 * q + j;
-                    float x = 0.f;
-                    if (d < nd) x = (__logf(fmaxf(__uint_as_float(v[8 * q + j]), kCFloor)) - sMu[d]) * sSi[d];
-                    else if (d == nd) x = (__logf(fmaxf(sR[i], kNFloor)) - sMu[d]) * sSi[d];
-                    u[j] = valid ? fminf(fmaxf(x, -kUMax), kUMax) : 0.f;
-                }
-                if (c + 8 * q < KC)
-                    *reinterpret_cast<uint4 *>(sOp + op_off(i, c + 8 * q, KC)) =
-                        make_uint4(pack_bf16x2(u[0], u[1]), pack_bf16x2(u[2], u[3]), pack_bf16x2(u[4], u[5]),
-                                   pack_bf16x2(u[6], u[7]));
+                for (int j = 0; j < 8; ++j)
+                    u[j] = valid ? std_input(__uint_as_float(v[8 * q + j]), kCFloor, a[j], b[j]) : 0.f;
+                *reinterpret_cast<uint4 *>(sOp + op_off(i, d0, KC)) =
+                    make_uint4(pack_bf16x2(u[0], u[1]), pack_bf16x2(u[2], u[3]), pack_bf16x2(u[4], u[5]),
+                               pack_bf16x2(u[6], u[7]));
             }
+        }
+        for (int d0 = nd; d0 < KC; d0 += 8) {      // ln n at column nd, zeros after it
+            const float un = valid && d0 == nd ? std_input(sR[i], kNFloor, sMu[nd], sSi[nd]) : 0.f;
+            *reinterpret_cast<uint4 *>(sOp + op_off(i, d0, KC)) = make_uint4(pack_bf16x2(un, 0.f), 0, 0, 0);
         }
         fence_proxy_async_smem();
         tc_fence_before();
