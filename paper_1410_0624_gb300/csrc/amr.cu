@@ -12,8 +12,9 @@
 // Update (device, every step): the leaf densities are permuted into output
 // order, the dense volume-mean arrays of levels 0 .. lmax-1 are rebuilt (a
 // cell inside a coarser leaf takes that leaf's value, a refined cell the mean
-// of its children: the coarse density "corresponds to a mean", §3.2), and the
-// per-oct sibling densities are gathered.
+// of its children: the coarse density "corresponds to a mean", §3.2) --
+// top-down from the base level to the finest dense level, then the
+// restriction below it -- and the per-oct sibling densities are gathered.
 //
 // Shells and leaves run over these lists with the same tables as the uniform
 // tree; the stencil densities come from the dense level arrays.
@@ -41,21 +42,46 @@ __global__ void gather_leaves(const float *__restrict__ in, const int64_t *__res
         out[i] = in[src[i]];
 }
 
-// Leaves of level <= lf paint their cells of level lf (= lmax - 1).
-__global__ void paint_level(const float *__restrict__ rho, const int8_t *__restrict__ lvl,
-                            const uint64_t *__restrict__ key, int64_t n, int lf, float *__restrict__ out)
+// The dense level arrays above the base are built top-down: a cell inside a
+// leaf of a coarser level takes the value its parent already holds (a
+// coalesced pass per level), the leaves of the level are scattered in, and a
+// cell refined at that level is marked NaN until its mean arrives (from
+// mean_finest at the finest dense level, from the restriction below it).
+// Leaf densities are finite (checked on the host path), so NaN is free as a
+// marker.
+
+// NaN at the refined cells of level l (a sorted Morton key list).
+__global__ void mark_refined(const uint64_t *__restrict__ keys, int64_t n, int l, float *__restrict__ dense)
 {
-    const int64_t side = (int64_t)1 << lf;
+    const int64_t side = (int64_t)1 << l;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int l = lvl[i];
-        if (l > lf) continue;
+        const uint64_t m = keys[i];
+        dense[((int64_t)compact3(m >> 2) * side + compact3(m >> 1)) * side + compact3(m)] = __int_as_float(0x7fc00000);
+    }
+}
+
+// The leaves of level l write their value into their cell.
+__global__ void scatter_leaves(const float *__restrict__ rho, const int8_t *__restrict__ lvl,
+                               const uint64_t *__restrict__ key, int64_t n, int l, float *__restrict__ dense)
+{
+    const int64_t side = (int64_t)1 << l;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (lvl[i] != l) continue;
         const uint64_t m = key[i];
-        const int s = 1 << (lf - l);
-        const int64_t x0 = (int64_t)compact3(m) * s, y0 = (int64_t)compact3(m >> 1) * s, z0 = (int64_t)compact3(m >> 2) * s;
-        const float v = rho[i];
-        for (int dz = 0; dz < s; ++dz)
-            for (int dy = 0; dy < s; ++dy)
-                for (int dx = 0; dx < s; ++dx) out[((z0 + dz) * side + (y0 + dy)) * side + x0 + dx] = v;
+        dense[((int64_t)compact3(m >> 2) * side + compact3(m >> 1)) * side + compact3(m)] = rho[i];
+    }
+}
+
+// fine[c] = coarse[parent c] over the row-major level l (NaN propagates: the
+// children of a refined cell are leaves or refined cells of level l).
+__global__ void prolong(const float *__restrict__ coarse, int l, float *__restrict__ fine)
+{
+    const int64_t side = (int64_t)1 << l, n = side * side * side;
+    const int sh = l;                     // log2 side
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = c & (side - 1), y = (c >> sh) & (side - 1), z = c >> (2 * sh);
+        const int64_t hs = side >> 1;
+        fine[c] = coarse[((z >> 1) * hs + (y >> 1)) * hs + (x >> 1)];
     }
 }
 
@@ -160,8 +186,81 @@ struct LeafListArgs {
 };
 
 // Internal + local terms and the epilogue for the leaf children of a list of
-// octs (one warp per oct); the screening sum is taken in a fixed order.
+// octs: half a warp per oct, lane q taking directions 4q .. 4q+3 (and
+// 64 + 4q .. when n_dir > 64), so the external and prefix rows arrive as
+// 16-byte loads and every child row leaves as contiguous 16-byte stores.  The
+// screening sum of a child is a fixed-order butterfly over the 16 lanes.
+// Directions are a multiple of 4 here (leaf_list_scalar serves the rest).
 __global__ void __launch_bounds__(256) leaf_list(LeafListArgs P)
+{
+    extern __shared__ float sm[];
+    const int nd = P.nd;
+    float *s_k = sm;                          // [8 t][8 s][nd], times dx
+    for (int i = threadIdx.x; i < 64 * nd; i += blockDim.x) s_k[i] = P.dx_leaf * P.kloc[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, half = lane >> 4, q = lane & 15;
+    const unsigned hmask = half ? 0xffff0000u : 0x0000ffffu;
+    const int64_t per_block = blockDim.x / 16;
+    // the two halves of a warp are independent (their shuffles name only their own lanes)
+    for (int64_t ii = (int64_t)blockIdx.x * per_block + (threadIdx.x >> 4); ii < P.n;
+         ii += (int64_t)gridDim.x * per_block) {
+        float rho[8];
+        const float4 r0 = *reinterpret_cast<const float4 *>(P.rho8 + 8 * ii);
+        const float4 r1 = *reinterpret_cast<const float4 *>(P.rho8 + 8 * ii + 4);
+        rho[0] = r0.x; rho[1] = r0.y; rho[2] = r0.z; rho[3] = r0.w;
+        rho[4] = r1.x; rho[5] = r1.y; rho[6] = r1.z; rho[7] = r1.w;
+        const float *E = P.E + ii * nd;
+        const float *Sp = P.Sp ? P.Sp + (int64_t)P.oparent[ii] * nd : nullptr;
+        int rows[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) rows[t] = P.oleaf[8 * ii + t];
+        float acc[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) acc[t] = 0.f;
+        for (int d = 4 * q; d < nd; d += 64) {
+            float4 base = *reinterpret_cast<const float4 *>(E + d);
+            if (Sp) {
+                const float4 p = *reinterpret_cast<const float4 *>(Sp + d);
+                base.x += p.x;
+                base.y += p.y;
+                base.z += p.z;
+                base.w += p.w;
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                if (rows[t] < 0) continue;
+                float4 nv = base;
+                const float *kt = s_k + t * 8 * nd + d;
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    const float4 k4 = *reinterpret_cast<const float4 *>(kt + s * nd);
+                    nv.x = fmaf(rho[s], k4.x, nv.x);
+                    nv.y = fmaf(rho[s], k4.y, nv.y);
+                    nv.z = fmaf(rho[s], k4.z, nv.z);
+                    nv.w = fmaf(rho[s], k4.w, nv.w);
+                }
+                const int64_t o = (int64_t)rows[t] * nd + d;
+                if (P.n_h) *reinterpret_cast<float4 *>(P.n_h + o) = nv;
+                if (P.a_v)
+                    *reinterpret_cast<float4 *>(P.a_v + o) =
+                        make_float4(nv.x * P.av_per_nh, nv.y * P.av_per_nh, nv.z * P.av_per_nh, nv.w * P.av_per_nh);
+                acc[t] += (exp2f(P.c_exp2 * nv.x) + exp2f(P.c_exp2 * nv.y)) +
+                          (exp2f(P.c_exp2 * nv.z) + exp2f(P.c_exp2 * nv.w));
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            float a = acc[t];
+#pragma unroll
+            for (int w = 8; w > 0; w >>= 1) a += __shfl_xor_sync(hmask, a, w, 16);
+            if (P.shield && q == 0 && rows[t] >= 0) P.shield[rows[t]] = a * P.inv_nd;
+        }
+    }
+}
+
+// Same work for direction counts that are not a multiple of 4 (one warp per
+// oct, lanes over (child, direction)); the screening sum in a fixed order.
+__global__ void __launch_bounds__(256) leaf_list_scalar(LeafListArgs P)
 {
     extern __shared__ float sm[];
     const int nd = P.nd;
@@ -446,12 +545,23 @@ cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s)
         gather_leaves<<<grid_for(t->n_leaf, 256), 256, 0, s>>>(rho_dev, t->leaf_src, t->n_leaf, t->rho_leaf);
     }
     CD_CHECK_LAUNCH();
-    {
+    // dense levels base .. lf, top-down (the base level's refined cells as NaN)
+    for (int l = t->base; l <= lf; ++l) {
+        if (l == t->base) {
+            if (t->n_ref[l]) {
+                LaunchScope ls(CD_K_RESTRICT, s);
+                mark_refined<<<grid_for(t->n_ref[l], 256), 256, 0, s>>>(t->ref_key[l], t->n_ref[l], l, t->rho_lvl[l]);
+            }
+        } else {
+            LaunchScope ls(CD_K_RESTRICT, s);
+            prolong<<<grid_for((int64_t)1 << (3 * l), 256, 152 * 64), 256, 0, s>>>(t->rho_lvl[l - 1], l, t->rho_lvl[l]);
+        }
+        CD_CHECK_LAUNCH();
         LaunchScope ls(CD_K_RESTRICT, s);
-        paint_level<<<grid_for(t->n_leaf, 256), 256, 0, s>>>(t->rho_leaf, t->leaf_lvl, t->leaf_key, t->n_leaf, lf,
-                                                             t->rho_lvl[lf]);
+        scatter_leaves<<<grid_for(t->n_leaf, 256), 256, 0, s>>>(t->rho_leaf, t->leaf_lvl, t->leaf_key, t->n_leaf, l,
+                                                                 t->rho_lvl[l]);
+        CD_CHECK_LAUNCH();
     }
-    CD_CHECK_LAUNCH();
     const int64_t nfin = t->oct_begin[lf + 1] - t->oct_begin[lf];
     if (nfin > 0) {
         LaunchScope ls(CD_K_RESTRICT, s);
@@ -577,9 +687,12 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
         shell_list_fp32<<<grid_for(no * nd, 256), 256, 0, s>>>(A);
         CD_CHECK_LAUNCH();
     }
-    // leaves
-    const size_t smem = sizeof(float) * (64 * nd + 64 * nd);
-    if (smem > 48 * 1024) CD_CUDA(cudaFuncSetAttribute(leaf_list, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // leaves: the 16-lanes-per-oct kernel when 16-byte rows are possible
+    const bool vec = nd % 4 == 0 && (uintptr_t)n_h % 16 == 0 && (uintptr_t)a_v % 16 == 0;
+    const size_t smem = sizeof(float) * (vec ? 64 * nd : 64 * nd + 64 * nd);
+    if (smem > 48 * 1024)
+        CD_CUDA(cudaFuncSetAttribute(vec ? leaf_list : leaf_list_scalar, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
     for (int k = 0; k <= L - 1; ++k) {
         const int64_t no = t->oct_begin[k + 1] - t->oct_begin[k];
         if (!no) continue;
@@ -600,7 +713,8 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
         B.a_v = a_v;
         B.shield = shield;
         LaunchScope ls(CD_K_LEAF, s);
-        leaf_list<<<grid_for(no, 8, 152 * 16), 256, smem, s>>>(B);
+        if (vec) leaf_list<<<grid_for(no, 16, 152 * 16), 256, smem, s>>>(B);
+        else leaf_list_scalar<<<grid_for(no, 8, 152 * 16), 256, smem, s>>>(B);
         CD_CHECK_LAUNCH();
     }
     return CD_OK;
