@@ -366,6 +366,10 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
     b.n_h = n_h;
     b.a_v = a_v;
     b.shield = shield;
+    if (bf16) {
+        st = launch_leaf_tc(b, s);
+        if (st != CD_EUNSUPPORTED) return st;
+    }
     return launch_leaf(b, s);
 }
 
@@ -375,7 +379,8 @@ cd_status cd_device_status(void *stream)
     cd_status a = leaf_fault_check();
     cd_status b = tc_fault_check();
     cd_status c = learned_tc_fault_check();
-    return a != CD_OK ? a : b != CD_OK ? b : c;
+    cd_status d = leaf_tc_fault_check();
+    return a != CD_OK ? a : b != CD_OK ? b : c != CD_OK ? c : d;
 }
 
 cd_status cd_tree_info(cd_tree t, int64_t *n_leaf, int *max_level, int *base_level, int64_t *n_oct)

@@ -226,6 +226,11 @@ cd_status launch_leaf(const LeafLaunch &a, cudaStream_t s);
 // leaf.cu: CD_ETIMEOUT if a leaf kernel gave up a bounded wait (clears it)
 cd_status leaf_fault_check();
 
+// leaf_tc.cu: the BF16 form's leaf kernel with the local term on the tensor
+// cores; CD_EUNSUPPORTED (no error text) when the sizes do not fit it
+cd_status launch_leaf_tc(const LeafLaunch &a, cudaStream_t s);
+cd_status leaf_tc_fault_check();
+
 // colden_tc.cu: BF16 tensor-core shell contraction for receiving levels >= 4
 bool tc_supported(int nd);
 cd_status build_tc_tables(cd_geom g, cudaStream_t s);

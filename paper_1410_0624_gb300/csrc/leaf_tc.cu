@@ -1,0 +1,337 @@
+// Per-leaf combine and epilogue of the BF16 form, with the internal + local
+// term (§3.2) on the tensor cores:
+//   loc[t][d] = dx_L sum_s rho[oct][s] Kloc[t][s][d]
+// is one small product per tile of 128 leaves (16 octs).  Row m of the A
+// operand holds the oct's eight densities in the block of its own octant
+// t = m % 8 (K = 8 blocks x 16; zeros elsewhere, written once), as a BF16 high
+// part and a BF16 low part (rho - high), so the densities enter with ~16 bits;
+// B[d][16 t + j] = dx_L Kloc[t][j % 8][d] in BF16.  The product lands in TMEM
+// (FP32), and the epilogue adds the oct's external column E and the parent's
+// far-shell prefix Sp (§3.3), forms the screening factor (Eqs. eq_chi,
+// chi_discret) and stages the tile's N_H rows for one bulk store.
+//
+// Tiles are 128 consecutive leaves in Morton order, so E, Sp, the densities and
+// the N_H rows of a tile are contiguous spans; bulk copies bring the next
+// tile's inputs in while the current one is computed.  Groups of four warps
+// (three per CTA when shared memory allows) work on independent tiles so that
+// one group's epilogue overlaps another's MMA.  Every wait is bounded; a
+// timeout sets a device flag (cd_device_status).
+#include <algorithm>
+
+#include "common.cuh"
+#include "umma.cuh"
+
+namespace cd {
+namespace {
+
+constexpr uint32_t kMaxPolls = 1u << 26;
+constexpr int kK = 128;                  // 8 octant blocks x (8 high + 8 low)
+
+static __device__ int g_leaftc_fault;
+
+__host__ __device__ constexpr size_t align128(size_t v) { return (v + 127) & ~(size_t)127; }
+__host__ __device__ constexpr int round16(int v) { return (v + 15) & ~15; }
+
+__host__ __device__ inline uint32_t op_off(int row, int k, int K)
+{
+    return (uint32_t)((row >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+struct LeafTcArgs {
+    LeafLaunch a;
+    int NP, G;                 // padded directions (MMA N), groups of 128 threads
+    int64_t n_leaf, ntiles;
+    float c2;                  // -shield_k av_per_nh log2(e)
+    int out_bulk;              // n_h is 16-byte aligned: tile rows leave as one bulk copy
+};
+
+struct LeafTcSmem {
+    size_t bloc, bar, grp, grp_stride, aloc, out, stage, stage_bytes, st_e, st_p, st_r, total;
+};
+
+__host__ __device__ inline LeafTcSmem leaf_tc_smem(int nd, int NP, int G)
+{
+    LeafTcSmem S;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t r = o; o = align128(o + bytes); return r; };
+    S.bloc = take((size_t)NP * kK * 2);
+    S.bar = take(128);
+    S.grp = o;
+    S.aloc = 0;
+    S.out = align128((size_t)128 * kK * 2);
+    S.st_e = 0;
+    S.st_p = align128((size_t)16 * nd * 4);
+    S.st_r = S.st_p + align128((size_t)2 * nd * 4);
+    S.stage_bytes = align128(S.st_r + 128 * 4);
+    S.stage = S.out + align128((size_t)128 * nd * 4);
+    S.grp_stride = S.stage + 2 * S.stage_bytes;
+    S.total = S.grp + (size_t)G * S.grp_stride;
+    return S;
+}
+
+__device__ __forceinline__ float fast_exp2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void named_barrier(int id, int threads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// a tile's inputs: E rows of its 16 octs, Sp rows of their 2 parents, 128 densities
+__device__ __forceinline__ void prefetch(const LeafTcArgs &P, const LeafTcSmem &S, int64_t tile, unsigned char *st,
+                                         uint64_t *bar)
+{
+    const int nd = P.a.nd;
+    const uint32_t be = 16u * nd * 4, bp = P.a.Sp ? 2u * nd * 4 : 0u, br = 128 * 4;
+    mbar_expect_tx(bar, be + bp + br);
+    bulk_g2s(st + S.st_e, P.a.E + tile * 16 * nd, be, bar);
+    if (P.a.Sp) bulk_g2s(st + S.st_p, P.a.Sp + tile * 2 * nd, bp, bar);
+    bulk_g2s(st + S.st_r, P.a.rho_leaf + tile * 128, br, bar);
+}
+
+__global__ void __launch_bounds__(384, 1) leaf_tc(LeafTcArgs P)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int nd = P.a.nd, NP = P.NP, G = P.G;
+    const LeafTcSmem S = leaf_tc_smem(nd, NP, G);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int g = warp >> 2, quarter = warp & 3, i = tid & 127;   // group, TMEM lane quarter, row
+    // [0 .. G) group MMAs, [G + 2 g + stage] input stages
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S.bar);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 3 * G);
+    int *sflag = reinterpret_cast<int *>(tslot + 1);
+    unsigned char *Gb = smem + S.grp + (size_t)g * S.grp_stride;
+    unsigned char *sA = Gb + S.aloc;
+    float *sO = reinterpret_cast<float *>(Gb + S.out);
+
+    if (tid == 0) {
+        for (int b = 0; b < 3 * G; ++b) mbar_init(&bar[b], 1);
+        fence_mbar_init();
+        for (int q = 0; q < G; ++q) sflag[q] = 0;
+    }
+    // B[d][16 t + j] = dx Kloc[t][j % 8][d] (BF16), directions past nd zero
+    for (int e = tid; e < NP * kK; e += blockDim.x) {
+        const int n = e / kK, k = e % kK;
+        const int t = k >> 4, s = k & 7;
+        const float v = n < nd ? P.a.dx_leaf * P.a.kloc[(t * 8 + s) * nd + n] : 0.f;
+        *reinterpret_cast<__nv_bfloat16 *>(smem + S.bloc + op_off(n, k, kK)) = __float2bfloat16_rn(v);
+    }
+    // every group's A starts all zero; a tile rewrites only each row's own block
+    for (int e = tid; e < G * 128 * kK / 8; e += blockDim.x) {
+        const int gg = e / (128 * kK / 8), r = e % (128 * kK / 8);
+        reinterpret_cast<uint4 *>(smem + S.grp + (size_t)gg * S.grp_stride + S.aloc)[r] = make_uint4(0, 0, 0, 0);
+    }
+    fence_proxy_async_smem();
+    if (warp == 0) tmem_alloc(tslot, 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tD = *tslot + (uint32_t)(g * 64);
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    const int bid = 1 + g;
+    const int64_t first = (int64_t)blockIdx.x * G + g, stride = (int64_t)gridDim.x * G;
+    const uint32_t idesc = umma_idesc_bf16(128, NP);
+    uint32_t phase = 0, sphase[2] = {0, 0};
+    bool pending[2] = {false, false};
+    bool fault = false;
+    if (i == 0 && first < P.ntiles) {
+        prefetch(P, S, first, Gb + S.stage, &bar[G + 2 * g]);
+        pending[0] = true;
+    }
+
+    int stg = 0;
+    for (int64_t tile = first; tile < P.ntiles && !fault; tile += stride, stg ^= 1) {
+        unsigned char *st = Gb + S.stage + stg * S.stage_bytes;
+        if (i == 0) {
+            if (tile + stride < P.ntiles) {
+                prefetch(P, S, tile + stride, Gb + S.stage + (stg ^ 1) * S.stage_bytes, &bar[G + 2 * g + (stg ^ 1)]);
+                pending[stg ^ 1] = true;
+            }
+            if (mbar_wait_bounded(&bar[G + 2 * g + stg], sphase[stg], kMaxPolls)) pending[stg] = false;
+            else sflag[g] = 1;
+        }
+        sphase[stg] ^= 1;
+        named_barrier(bid, 128);
+        if (sflag[g]) {
+            fault = true;
+            break;
+        }
+        const float *sR = reinterpret_cast<const float *>(st + S.st_r);
+        // ---- A row: the oct's densities, high and low BF16 parts, in block t ----
+        {
+            const float4 r0 = *reinterpret_cast<const float4 *>(sR + (i & ~7));
+            const float4 r1 = *reinterpret_cast<const float4 *>(sR + (i & ~7) + 4);
+            const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+            float hi[8], lo[8];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                hi[s] = __bfloat162float(__float2bfloat16_rn(rv[s]));
+                lo[s] = rv[s] - hi[s];
+            }
+            const int k0 = 16 * (i & 7);
+            *reinterpret_cast<uint4 *>(sA + op_off(i, k0, kK)) =
+                make_uint4(pack_bf16x2(hi[0], hi[1]), pack_bf16x2(hi[2], hi[3]), pack_bf16x2(hi[4], hi[5]),
+                           pack_bf16x2(hi[6], hi[7]));
+            *reinterpret_cast<uint4 *>(sA + op_off(i, k0 + 8, kK)) =
+                make_uint4(pack_bf16x2(lo[0], lo[1]), pack_bf16x2(lo[2], lo[3]), pack_bf16x2(lo[4], lo[5]),
+                           pack_bf16x2(lo[6], lo[7]));
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        named_barrier(bid, 128);
+        if (i == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(smem + S.bloc);
+            for (int ks = 0; ks < kK / 16; ++ks)
+                umma_bf16(tD, umma_smem_desc(a0 + ks * 256, 128, kK * 16), umma_smem_desc(b0 + ks * 256, 128, kK * 16),
+                          idesc, ks > 0 ? 1u : 0u);
+            umma_commit(&bar[g]);
+            if (!mbar_wait_bounded(&bar[g], phase, kMaxPolls)) sflag[g] = 1;
+            // the previous tile's rows must have left the output buffer
+            if (P.out_bulk) bulk_wait_read<0>();
+        }
+        phase ^= 1;
+        named_barrier(bid, 128);
+        if (sflag[g]) {
+            fault = true;
+            break;
+        }
+        tc_fence_after();
+        // ---- N_H = loc + E[oct] + Sp[parent]; screening factor ----
+        {
+            const int64_t m = tile * 128 + i;
+            const float *Ei = reinterpret_cast<const float *>(st + S.st_e) + (i >> 3) * nd;
+            const float *Pi = P.a.Sp ? reinterpret_cast<const float *>(st + S.st_p) + (i >> 6) * nd : nullptr;
+            float *orow = sO + (size_t)i * nd;
+            float *av = P.a.a_v ? P.a.a_v + m * nd : nullptr;
+            float *nh = P.a.n_h && !P.out_bulk ? P.a.n_h + m * nd : nullptr;
+            float acc = 0.f;
+#pragma unroll 1
+            for (int c = 0; c < nd; c += 32) {
+                uint32_t v[32];
+                tmem_ld32(tD + lane_off + (uint32_t)c, v);
+                tmem_ld_wait();
+#pragma unroll
+                for (int j4 = 0; j4 < 32; j4 += 4) {
+                    if (c + j4 >= nd) break;       // nd is a multiple of 4
+                    float4 e = *reinterpret_cast<const float4 *>(Ei + c + j4);
+                    if (Pi) {
+                        const float4 p = *reinterpret_cast<const float4 *>(Pi + c + j4);
+                        e.x += p.x;
+                        e.y += p.y;
+                        e.z += p.z;
+                        e.w += p.w;
+                    }
+                    const float4 N = make_float4(__uint_as_float(v[j4]) + e.x, __uint_as_float(v[j4 + 1]) + e.y,
+                                                 __uint_as_float(v[j4 + 2]) + e.z, __uint_as_float(v[j4 + 3]) + e.w);
+                    acc += (fast_exp2(P.c2 * N.x) + fast_exp2(P.c2 * N.y)) + (fast_exp2(P.c2 * N.z) + fast_exp2(P.c2 * N.w));
+                    if (P.out_bulk) {
+                        *reinterpret_cast<float4 *>(orow + c + j4) = N;
+                    } else if (nh) {
+                        nh[c + j4] = N.x;
+                        nh[c + j4 + 1] = N.y;
+                        nh[c + j4 + 2] = N.z;
+                        nh[c + j4 + 3] = N.w;
+                    }
+                    if (av) {
+                        av[c + j4] = N.x * P.a.av_per_nh;
+                        av[c + j4 + 1] = N.y * P.a.av_per_nh;
+                        av[c + j4 + 2] = N.z * P.a.av_per_nh;
+                        av[c + j4 + 3] = N.w * P.a.av_per_nh;
+                    }
+                }
+            }
+            if (P.a.shield) P.a.shield[m] = acc / (float)nd;
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        named_barrier(bid, 128);
+        if (P.out_bulk && i == 0) {
+            bulk_s2g(P.a.n_h + tile * 128 * nd, sO, (uint32_t)(128 * nd * 4));
+            bulk_commit();
+        }
+    }
+    if (fault && i == 0) {
+        atomicExch(&g_leaftc_fault, 1);
+        mbar_wait_bounded(&bar[g], phase ^ 1, kMaxPolls);   // let an issued product finish
+    }
+    if (i == 0) {
+        for (int b = 0; b < 2; ++b)
+            if (pending[b]) mbar_wait_bounded(&bar[G + 2 * g + b], sphase[b], kMaxPolls);
+        bulk_wait_all<0>();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(*tslot, 256);
+    }
+}
+
+int sms()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 152;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
+}  // namespace
+
+// The tensor-core leaf kernel serves uniform trees with at least one full tile
+// (128 leaves), n_dir a multiple of 4 up to 64, 16-byte aligned inputs.
+cd_status launch_leaf_tc(const LeafLaunch &a, cudaStream_t s)
+{
+    const int nd = a.nd;
+    const int64_t n_leaf = a.n_oct * 8;
+    if (nd % 4 != 0 || nd > 64 || n_leaf < 128 || n_leaf % 128 != 0 || !aligned16(a.E) || !aligned16(a.Sp) ||
+        !aligned16(a.rho_leaf) || !a.E)
+        return CD_EUNSUPPORTED;
+    LeafTcArgs P;
+    P.a = a;
+    P.NP = round16(nd);
+    P.n_leaf = n_leaf;
+    P.ntiles = n_leaf / 128;
+    P.c2 = (float)(-(double)a.shield_k * (double)a.av_per_nh * 1.4426950408889634);
+    P.out_bulk = a.n_h && aligned16(a.n_h);
+    int dev = 0, smax = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    P.G = 3;
+    while (P.G > 1 && (int)leaf_tc_smem(nd, P.NP, P.G).total > smax) --P.G;
+    const size_t smem = leaf_tc_smem(nd, P.NP, P.G).total;
+    if ((int)smem > smax) return CD_EUNSUPPORTED;
+    CD_CUDA(cudaFuncSetAttribute(leaf_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t grid = std::min<int64_t>((P.ntiles + P.G - 1) / P.G, sms());
+    LaunchScope ls(CD_K_LEAF, s);
+    leaf_tc<<<(unsigned)grid, 128 * P.G, smem, s>>>(P);
+    CD_CHECK_LAUNCH();
+    return CD_OK;
+}
+
+cd_status leaf_tc_fault_check()
+{
+    int v = 0;
+    CD_CUDA(cudaMemcpyFromSymbol(&v, g_leaftc_fault, sizeof(int)));
+    if (v) {
+        const int zero = 0;
+        CD_CUDA(cudaMemcpyToSymbol(g_leaftc_fault, &zero, sizeof(int)));
+        set_error("a tensor-core leaf kernel gave up a bounded wait");
+        return CD_ETIMEOUT;
+    }
+    return CD_OK;
+}
+
+}  // namespace cd
