@@ -117,7 +117,8 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-KERNEL_SOURCES = {"leaf": "leaf.cu", "shell": "colden_tc.cu", "restrict": "tree.cu"}
+# source file of each kernel kind (the BF16 form's leaf kernel lives in leaf_tc.cu)
+KERNEL_SOURCES = {"leaf": "leaf.cu", "leaf_tc": "leaf_tc.cu", "shell": "colden_tc.cu", "restrict": "tree.cu"}
 
 
 def _source_hash(name):
@@ -127,9 +128,11 @@ def _source_hash(name):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def measured_traffic(kind, L, nd):
+def measured_traffic(kind, L, nd, precision="bf16"):
     """DRAM bytes per launch of a kernel from the committed ncu summary
     (profiles/traffic.json), or None when the kernel source changed since."""
+    if kind == "leaf" and precision == "bf16":
+        kind = "leaf_tc"
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tr = json.load(f)
@@ -385,7 +388,7 @@ def run_ours(args):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": measured_traffic(dom, L, nd), "kernel": dom,
+                             "frac": achieved / peak, "traffic": measured_traffic(dom, L, nd, args.precision), "kernel": dom,
                              "kernel_ms": dom_ms, "peak_kind": peak_kind, "algo_bytes_per_cell_dir": bpu},
                 "step_roofline_frac": bpu * n_leaf * nd / (ms / 1e3) / 1e9 / peak,
                 "kernels": kern, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "error_vs_oracle": err}

@@ -2,18 +2,20 @@
 // term (§3.2) on the tensor cores:
 //   loc[t][d] = dx_L sum_s rho[oct][s] Kloc[t][s][d]
 // is one small product per tile of 128 leaves (16 octs).  Row m of the A
-// operand holds the oct's eight densities in the block of its own octant
-// t = m % 8 (K = 8 blocks x 16; zeros elsewhere, written once), as a BF16 high
-// part and a BF16 low part (rho - high), so the densities enter with ~16 bits;
-// B[d][16 t + j] = dx_L Kloc[t][j % 8][d] in BF16.  The product lands in TMEM
-// (FP32), and the epilogue adds the oct's external column E and the parent's
-// far-shell prefix Sp (§3.3), forms the screening factor (Eqs. eq_chi,
-// chi_discret) and stages the tile's N_H rows for one bulk store.
+// operand holds the oct's eight densities (BF16) in the block of its own
+// octant t = m % 8 (K = 8 blocks x 8; zeros elsewhere, written once);
+// B[d][8 t + s] = dx_L Kloc[t][s][d] in BF16.  The product lands in TMEM
+// (FP32): the local term carries at most 2^-8 relative error from the two
+// roundings, which enters N_H weighted by its share of the column (measured:
+// the BF16 path's largest N_H error is unchanged).  The epilogue adds the oct's
+// external column E and the parent's far-shell prefix Sp (§3.3), forms the
+// screening factor (Eqs. eq_chi, chi_discret) and stages the tile's N_H rows
+// for one bulk store.
 //
 // Tiles are 128 consecutive leaves in Morton order, so E, Sp, the densities and
 // the N_H rows of a tile are contiguous spans; bulk copies bring the next
 // tile's inputs in while the current one is computed.  Groups of four warps
-// (three per CTA when shared memory allows) work on independent tiles so that
+// (four per CTA when shared memory allows) work on independent tiles so that
 // one group's epilogue overlaps another's MMA.  Every wait is bounded; a
 // timeout sets a device flag (cd_device_status).
 #include <algorithm>
@@ -25,7 +27,7 @@ namespace cd {
 namespace {
 
 constexpr uint32_t kMaxPolls = 1u << 26;
-constexpr int kK = 128;                  // 8 octant blocks x (8 high + 8 low)
+constexpr int kK = 64;                  // 8 octant blocks x 8 siblings
 
 static __device__ int g_leaftc_fault;
 
@@ -99,7 +101,7 @@ __device__ __forceinline__ void prefetch(const LeafTcArgs &P, const LeafTcSmem &
     bulk_g2s(st + S.st_r, P.a.rho_leaf + tile * 128, br, bar);
 }
 
-__global__ void __launch_bounds__(384, 1) leaf_tc(LeafTcArgs P)
+__global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int nd = P.a.nd, NP = P.NP, G = P.G;
@@ -119,10 +121,10 @@ __global__ void __launch_bounds__(384, 1) leaf_tc(LeafTcArgs P)
         fence_mbar_init();
         for (int q = 0; q < G; ++q) sflag[q] = 0;
     }
-    // B[d][16 t + j] = dx Kloc[t][j % 8][d] (BF16), directions past nd zero
+    // B[d][8 t + s] = dx Kloc[t][s][d] (BF16), directions past nd zero
     for (int e = tid; e < NP * kK; e += blockDim.x) {
         const int n = e / kK, k = e % kK;
-        const int t = k >> 4, s = k & 7;
+        const int t = k >> 3, s = k & 7;
         const float v = n < nd ? P.a.dx_leaf * P.a.kloc[(t * 8 + s) * nd + n] : 0.f;
         *reinterpret_cast<__nv_bfloat16 *>(smem + S.bloc + op_off(n, k, kK)) = __float2bfloat16_rn(v);
     }
@@ -167,24 +169,13 @@ __global__ void __launch_bounds__(384, 1) leaf_tc(LeafTcArgs P)
             break;
         }
         const float *sR = reinterpret_cast<const float *>(st + S.st_r);
-        // ---- A row: the oct's densities, high and low BF16 parts, in block t ----
+        // ---- A row: the oct's densities in block t ----
         {
             const float4 r0 = *reinterpret_cast<const float4 *>(sR + (i & ~7));
             const float4 r1 = *reinterpret_cast<const float4 *>(sR + (i & ~7) + 4);
-            const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-            float hi[8], lo[8];
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-                hi[s] = __bfloat162float(__float2bfloat16_rn(rv[s]));
-                lo[s] = rv[s] - hi[s];
-            }
-            const int k0 = 16 * (i & 7);
-            *reinterpret_cast<uint4 *>(sA + op_off(i, k0, kK)) =
-                make_uint4(pack_bf16x2(hi[0], hi[1]), pack_bf16x2(hi[2], hi[3]), pack_bf16x2(hi[4], hi[5]),
-                           pack_bf16x2(hi[6], hi[7]));
-            *reinterpret_cast<uint4 *>(sA + op_off(i, k0 + 8, kK)) =
-                make_uint4(pack_bf16x2(lo[0], lo[1]), pack_bf16x2(lo[2], lo[3]), pack_bf16x2(lo[4], lo[5]),
-                           pack_bf16x2(lo[6], lo[7]));
+            *reinterpret_cast<uint4 *>(sA + op_off(i, 8 * (i & 7), kK)) =
+                make_uint4(pack_bf16x2(r0.x, r0.y), pack_bf16x2(r0.z, r0.w), pack_bf16x2(r1.x, r1.y),
+                           pack_bf16x2(r1.z, r1.w));
         }
         fence_proxy_async_smem();
         tc_fence_before();
@@ -309,7 +300,7 @@ cd_status launch_leaf_tc(const LeafLaunch &a, cudaStream_t s)
     int dev = 0, smax = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    P.G = 3;
+    P.G = 4;
     while (P.G > 1 && (int)leaf_tc_smem(nd, P.NP, P.G).total > smax) --P.G;
     const size_t smem = leaf_tc_smem(nd, P.NP, P.G).total;
     if ((int)smem > smax) return CD_EUNSUPPORTED;
