@@ -70,7 +70,9 @@ enum {
 enum {
     CD_MODE_PREC = 0,      /* precalculation module, two-level approximation: the shell at level l is seen from
                               the centre of the target's ancestor at level min(l+2, l0-1) */
-    CD_MODE_INSITU = 1     /* every shell seen from the oct centre (not provided by this build) */
+    CD_MODE_INSITU = 1     /* every shell seen from the oct centre: an exact walk over each shell's cells per
+                              (oct, direction) on the CUDA cores, FP32 whatever cd_opts.precision says; no far-shell
+                              sharing, so it costs more (§4.3, Table 1) */
 };
 
 /* Arithmetic of the shell contraction. */
@@ -140,7 +142,8 @@ cd_status cd_tree_update(cd_tree tree, const float *rho, int rho_on_device, void
  * level-(l-1) ancestor; cells of the inner region get 0.
  *   scheme         CD_DIRS_*; p0, p1 as documented there
  *   dirs           CD_DIRS_CUSTOM only: n_custom x 3 doubles (host)
- *   mode           CD_MODE_PREC (CD_MODE_INSITU returns CD_EUNSUPPORTED)
+ *   mode           CD_MODE_PREC or CD_MODE_INSITU (the tables are built either way; in-situ
+ *                  evaluations use only the local ones)
  * 1 <= number of directions <= 768.  Components below 1e-14 in magnitude are
  * set to zero and each vector renormalised. */
 cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs, int n_custom, int mode,

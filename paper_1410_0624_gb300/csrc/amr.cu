@@ -610,8 +610,10 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
         t->ws.ndir = nd;
     }
     const auto dx = [&](int l) { return (float)(t->box_cm / (double)((int64_t)1 << l)); };
+    // in-situ variant: every oct's shells from its centre (insitu.cu), no prefixes
+    const bool insitu = g->mode == CD_MODE_INSITU;
     // BF16: the tensor-core contraction over the level's receiver lists where it serves
-    const bool tc = opts.precision == CD_BF16 && tc_supported(nd) && g->wb != nullptr;
+    const bool tc = !insitu && opts.precision == CD_BF16 && tc_supported(nd) && g->wb != nullptr;
     ShellListArgs A;
     for (int q = 0; q < 4; ++q) {
         A.tab[q] = g->tab[q];
@@ -619,7 +621,7 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
     }
     A.nd = nd;
     // far-shell prefixes of the refined cells
-    for (int k = 3; k <= L - 2; ++k) {
+    for (int k = 3; k <= L - 2 && !insitu; ++k) {
         if (!t->n_ref[k]) continue;
         if (tc && k >= 4 && t->tc_ref[k].ntiles) {
             ExtLaunch e = {};
@@ -655,6 +657,11 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
     for (int k = 0; k <= L - 1; ++k) {
         const int64_t no = t->oct_begin[k + 1] - t->oct_begin[k];
         if (!no) continue;
+        if (insitu) {
+            cd_status st = launch_insitu(t, g, k, no, t->oct_key + t->oct_begin[k], t->ws.E + t->oct_begin[k] * nd, s);
+            if (st != CD_OK) return st;
+            continue;
+        }
         if (tc && k >= 4 && t->tc_oct[k].ntiles) {
             ExtLaunch e = {};
             e.k = k;
@@ -706,7 +713,7 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
         B.rho8 = t->oct_rho8 + 8 * t->oct_begin[k];
         B.oleaf = t->oct_leaf + 8 * t->oct_begin[k];
         B.E = t->ws.E + t->oct_begin[k] * nd;
-        B.Sp = (k - 1 >= 3) ? t->ws.S[k - 1] : nullptr;
+        B.Sp = (!insitu && k - 1 >= 3) ? t->ws.S[k - 1] : nullptr;
         B.oparent = t->oct_parent + t->oct_begin[k];
         B.kloc = g->kloc;
         B.n_h = n_h;

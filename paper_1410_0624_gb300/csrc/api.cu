@@ -250,11 +250,7 @@ cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs,
         return CD_EINVAL;
     }
     *out = nullptr;
-    if (mode == CD_MODE_INSITU) {
-        set_error("the in-situ variant is not provided by this build");
-        return CD_EUNSUPPORTED;
-    }
-    if (mode != CD_MODE_PREC) {
+    if (mode != CD_MODE_PREC && mode != CD_MODE_INSITU) {
         set_error("unknown mode %d", mode);
         return CD_EINVAL;
     }
@@ -316,11 +312,36 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
     }
     if (!n_h && !a_v && !shield) return CD_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    if (opts.net) return column_density_learned(tree, geom, opts, n_h, a_v, shield, s);
+    const bool insitu = geom->mode == CD_MODE_INSITU;
+    if (opts.net) {
+        if (insitu) {
+            set_error("the learned correction is defined on the precalculated form");
+            return CD_EUNSUPPORTED;
+        }
+        return column_density_learned(tree, geom, opts, n_h, a_v, shield, s);
+    }
     if (tree->amr) return column_density_amr(tree, geom, opts, n_h, a_v, shield, s);
     const int nd = geom->n_dir, L = tree->L;
     cd_status st = ensure_workspace(tree, nd);
     if (st != CD_OK) return st;
+    if (insitu) {
+        // every shell from the oct centre (an exact walk per level), then the leaves
+        if (L >= 2 && (st = launch_insitu(tree, geom, L - 1, tree->n_oct, nullptr, tree->ws.E, s)) != CD_OK) return st;
+        LeafLaunch b = {};
+        b.n_oct = tree->n_oct;
+        b.nd = nd;
+        b.dx_leaf = dx_of(tree, L);
+        b.av_per_nh = (float)opts.av_per_nh;
+        b.shield_k = (float)opts.shield_k;
+        b.rho_leaf = tree->rho_leaf;
+        b.E = L >= 2 ? tree->ws.E : nullptr;
+        b.Sp = nullptr;
+        b.kloc = geom->kloc;
+        b.n_h = n_h;
+        b.a_v = a_v;
+        b.shield = shield;
+        return launch_leaf(b, s);
+    }
     // BF16 tensor cores for receiving levels >= 4 when the direction count
     // fits the accumulator; the few cells of coarser levels stay FP32
     const bool bf16 = opts.precision == CD_BF16 && tc_supported(nd) && geom->wb != nullptr;

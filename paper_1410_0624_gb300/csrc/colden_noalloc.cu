@@ -70,8 +70,8 @@ extern "C" cd_status cd_column_density_noalloc(cd_tree tree, cd_geom geom, const
         set_error("cd_column_density_noalloc computes in FP32 only");
         return CD_EUNSUPPORTED;
     }
-    if (opts.net || tree->amr) {
-        set_error("cd_column_density_noalloc serves uniform trees without a learned correction");
+    if (opts.net || tree->amr || geom->mode == CD_MODE_INSITU) {
+        set_error("cd_column_density_noalloc serves uniform trees in the precalculated form without a learned correction");
         return CD_EUNSUPPORTED;
     }
     if (!n_h && !a_v && !shield) return CD_OK;

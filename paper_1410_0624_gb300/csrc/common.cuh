@@ -193,6 +193,10 @@ cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s);
 cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n_h, float *a_v, float *shield,
                              cudaStream_t s);
 
+// insitu.cu: the external column of n octs of level k (keys NULL: every oct of
+// a uniform tree), every shell seen from the oct centre (§4.3)
+cd_status launch_insitu(cd_tree t, cd_geom g, int k, int64_t n, const uint64_t *keys, float *out, cudaStream_t s);
+
 // geometry.cu
 int make_directions(int scheme, int p0, int p1, const double *custom, int n_custom, double *out);
 cd_status build_geometry_tables(cd_geom g, cudaStream_t s);

@@ -48,8 +48,8 @@ def test_opts_default_and_errors_without_gpu(lib):
     assert lib.cd_build_tree_uniform(0, 1.0, None, 1, None, ctypes.byref(h)) == colden.CD_EINVAL
     assert b"leaf_level" in lib.cd_last_error()
     assert lib.cd_build_tree_uniform(3, -1.0, None, 1, None, ctypes.byref(h)) == colden.CD_EINVAL
-    assert lib.cd_precompute_geometry(0, 1, 0, None, 0, colden.MODE_INSITU, None,
-                                      ctypes.byref(h)) == colden.CD_EUNSUPPORTED
+    assert lib.cd_precompute_geometry(0, 1, 0, None, 0, 7, None, ctypes.byref(h)) == colden.CD_EINVAL
+    assert b"mode" in lib.cd_last_error()
     assert lib.cd_precompute_geometry(99, 1, 0, None, 0, 0, None, ctypes.byref(h)) == colden.CD_EINVAL
     assert lib.cd_column_density(None, None, None, None, None, None, None) == colden.CD_EINVAL
     assert lib.cd_stats_get(len(colden.KERNEL_KINDS), None, None) == colden.CD_EINVAL
