@@ -117,6 +117,49 @@ def dirs_custom(d) -> np.ndarray:
     return out
 
 
+CONE_RINGS, CONE_AZIMUTHS = 4, 8
+
+
+def cone_rays(dirs, n_bins: int = None, rings: int = CONE_RINGS, azimuths: int = CONE_AZIMUTHS,
+              cos_alpha: float = None) -> np.ndarray:
+    """Sub-rays of the cone of each direction, shape [nd, rings * azimuths, 3].
+
+    A direction stands for a bin of solid angle 4 pi / n_bins (§3.2: the
+    directions split the sphere into equal solid angles).  Its cone is the
+    circular cap of that solid angle around u, cos(alpha) = 1 - 2 / n_bins
+    (n_bins defaults to the number of directions).  The cap is cut into
+    `rings` bands of equal solid angle (equal steps in cos theta) and every band
+    into `azimuths` equal sectors; one sub-ray passes through the middle of
+    each piece:
+        cos theta_r = 1 - (r + 1/2) (1 - cos alpha) / rings
+        phi_rj      = 2 pi (j + [r odd] / 2) / azimuths
+        v = cos theta_r u + sin theta_r (cos phi_rj e1 + sin phi_rj e2)
+    with e1 = unit(e_a x u), a the axis of the smallest |u_a| (the first on
+    ties), and e2 = u x e1.  Sub-ray index r * azimuths + j.  Components
+    below 1e-14 in magnitude are zeroed and the vector renormalised, as for
+    the directions.  The pieces have equal solid angle, so the cone average of
+    a quantity is the plain mean over the sub-rays (a midpoint rule for the
+    integral over the cap)."""
+    u = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    nd = u.shape[0]
+    if cos_alpha is None:
+        cos_alpha = 1.0 - 2.0 / float(n_bins if n_bins is not None else nd)
+    axis = np.argmin(np.abs(u), axis=1)
+    e1 = np.cross(np.eye(3)[axis], u)
+    e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
+    e2 = np.cross(u, e1)
+    out = np.zeros((nd, rings * azimuths, 3))
+    for r in range(rings):
+        c = 1.0 - (r + 0.5) * (1.0 - cos_alpha) / rings
+        sn = np.sqrt(max(0.0, 1.0 - c * c))
+        for j in range(azimuths):
+            phi = 2.0 * np.pi * (j + 0.5 * (r & 1)) / azimuths
+            v = c * u + sn * (np.cos(phi) * e1 + np.sin(phi) * e2)
+            v[np.abs(v) < 1e-14] = 0.0
+            out[:, r * azimuths + j] = v / np.linalg.norm(v, axis=1, keepdims=True)
+    return out
+
+
 def ray_cube(p, d, lo, h) -> float:
     """Length of the ray {p + s d, s >= 0} inside the cube [lo, lo+h]^3."""
     p = np.ascontiguousarray(p, dtype=np.float64)
@@ -200,6 +243,17 @@ class Tree:
         if rc != 0:
             raise ValueError("bad target level")
         return (out, pl) if per_level else out
+
+    def column_density_cone(self, dirs, lvl, ijk, n_bins: int = None, rings: int = CONE_RINGS,
+                            azimuths: int = CONE_AZIMUTHS, mode: int = MODE_PREC) -> np.ndarray:
+        """Cone-averaged tree-method N_H, shape [n, ndir]: the mean of the
+        single-ray column (Eqs. N_discret1 and N_discret) over the sub-rays of
+        cone_rays.  The geometric factors K enter the column linearly, so this
+        equals the column computed with K averaged over each cone."""
+        rays = cone_rays(dirs, n_bins, rings, azimuths)
+        nd, ns = rays.shape[0], rays.shape[1]
+        N = self.column_density(rays.reshape(-1, 3), lvl, ijk, mode=mode)
+        return N.reshape(N.shape[0], nd, ns).mean(axis=2)
 
     def raymarch(self, dirs, lvl, ijk) -> np.ndarray:
         """Exact column from each target centre to the box edge (§4 reference)."""
