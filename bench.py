@@ -165,9 +165,10 @@ def _morton(ijk):
     return m
 
 
-def oracle_sample(rho, box, L, nside, target_s, min_leaves=16, max_leaves=400000):
+def oracle_sample(rho, box, L, nside, target_s, min_leaves=16, max_leaves=400000, cone=False):
     """Times the FP64 oracle on a seeded leaf sample sized for ~target_s seconds.
-    Returns (cell-dirs/s, n_leaves, seconds, ijk, N_ref)."""
+    Returns (cell-dirs/s, n_leaves, seconds, ijk, N_ref); cone: the
+    cone-averaged column (the mean over each direction's sub-rays)."""
     import oracle
     T = oracle.Tree.uniform(rho, box)
     dirs = oracle.dirs_healpix(nside)
@@ -175,7 +176,10 @@ def oracle_sample(rho, box, L, nside, target_s, min_leaves=16, max_leaves=400000
     while True:
         ijk = _sample_ijk(L, n)
         t0 = time.perf_counter()
-        ref = T.column_density(dirs, np.full(n, L), ijk)
+        if cone:
+            ref = T.column_density_cone(dirs, np.full(n, L), ijk)
+        else:
+            ref = T.column_density(dirs, np.full(n, L), ijk)
         dt = time.perf_counter() - t0
         if dt >= target_s or n >= max_leaves:
             return n * len(dirs) / dt, n, dt, ijk, ref
@@ -271,7 +275,12 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     rho = torch.from_numpy(rho_np).to(dev).reshape(-1).contiguous()
     tree = colden.build_tree_uniform(rho.reshape(1 << L, 1 << L, 1 << L), box)
-    geom = colden.precompute_geometry("healpix", args.nside)
+    cone = args.geometry == "cone"
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    geom = colden.precompute_geometry("healpix", args.nside, mode=colden.MODE_CONE if cone else colden.MODE_PREC)
+    torch.cuda.synchronize()
+    geom_ms = 1e3 * (time.perf_counter() - t0)
     nd = geom.n_dir
     n_leaf = tree.n_leaf
     n_h = torch.empty(n_leaf * nd, device=dev)
@@ -295,10 +304,11 @@ def run_ours(args):
     # ---- the FP64 oracle on a seeded leaf sample: CPU baseline and reference values ----
     cpu = sample = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
-        rate, n, dt, ijk, ref = oracle_sample(rho_np, box, L, args.nside, args.cpu_seconds)
+        rate, n, dt, ijk, ref = oracle_sample(rho_np, box, L, args.nside, args.cpu_seconds, cone=cone)
         cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "%d seeded random leaves x %d dirs (%.1f s)" % (n, nd, dt)}
+               "sample": "%d seeded random leaves x %d dirs%s (%.1f s)"
+                         % (n, nd, " x 32 cone sub-rays" if cone else "", dt)}
         sample = (torch.from_numpy(_morton(ijk)).to(dev), ref)
 
     def score():
@@ -381,8 +391,10 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16",
                 "data": "synthetic",
                 "config": {"workload": "uniform %d^3 leaves (levels 0..%d), 10 pc box, k^-11/3 log-normal "
-                                       "(mean 30, sigma_ln 2, seed 2), %d HEALPix dirs, N_H + shield out"
-                                       % (1 << L, L, nd), "precision": args.precision,
+                                       "(mean 30, sigma_ln 2, seed 2), %d HEALPix dirs, N_H + shield out%s"
+                                       % (1 << L, L, nd, ", cone-averaged factors" if cone else ""),
+                           "precision": args.precision, "geometry": args.geometry,
+                           "geometry_build_ms": geom_ms,
                            "l2": "512 MB buffer written between timed steps; N_H output (%.2f GB) > L2"
                                  % (4 * n_leaf * nd / 1e9),
                            "parallelism": "replicas" if world > 1 else "single"},
@@ -829,6 +841,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32-plain comparison run")
     ap.add_argument("--level", type=int, default=8)
     ap.add_argument("--nside", type=int, default=2)
+    ap.add_argument("--geometry", default="ray", choices=["ray", "cone"],
+                    help="uniform workload: one ray per direction, or factors averaged over each direction's cone")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--workload", default="uniform", choices=["uniform", "amr", "batch", "learned"])
     ap.add_argument("--train-rows", type=int, default=1_000_000, help="learned: training leaves per field")

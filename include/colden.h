@@ -70,10 +70,30 @@ enum {
 enum {
     CD_MODE_PREC = 0,      /* precalculation module, two-level approximation: the shell at level l is seen from
                               the centre of the target's ancestor at level min(l+2, l0-1) */
-    CD_MODE_INSITU = 1     /* every shell seen from the oct centre: an exact walk over each shell's cells per
+    CD_MODE_INSITU = 1,    /* every shell seen from the oct centre: an exact walk over each shell's cells per
                               (oct, direction) on the CUDA cores, FP32 whatever cd_opts.precision says; no far-shell
                               sharing, so it costs more (§4.3, Table 1) */
+    CD_MODE_CONE = 2       /* as CD_MODE_PREC, but every geometric factor (shell tables, Kloc, BF16 operands) is
+                              the mean over the 32 sub-rays of the direction's cone (below) instead of the value
+                              of one ray; the evaluation costs the same, only wider rows of the FP32 tables */
 };
+
+/* Cone of a direction (CD_MODE_CONE).  Each of the n_dir directions stands
+ * for a bin of 4 pi / n_dir steradians (§3.2: the directions split the sphere
+ * into equal solid angles).  Its cone is the circular cap of that solid angle
+ * around the direction u, cos(alpha) = 1 - 2 / n_dir, cut into 4 rings of equal
+ * solid angle (equal steps in cos theta) and each ring into 8 equal sectors;
+ * sub-ray (r, j), index 8 r + j, passes through the middle of its piece:
+ *   cos theta_r = 1 - (r + 1/2) (1 - cos alpha) / 4,
+ *   phi_rj      = 2 pi (j + 1/2 if r is odd) / 8,
+ *   v = cos theta_r u + sin theta_r (cos phi_rj e1 + sin phi_rj e2),
+ * with e1 = unit(e_a x u), a the first axis whose |u_a| is within 1e-9 of the
+ * smallest, e2 = u x e1; components below 1e-14 are zeroed and v renormalised.
+ * The pieces have equal solid angle, so the averaged factor is the midpoint
+ * rule for the mean of K over the cap.  The column is linear in K, so N_H is
+ * the mean over the sub-rays of the single-ray column.  The in-situ walk and
+ * the learned correction are defined for single rays only (CD_EUNSUPPORTED). */
+#define CD_CONE_SUBRAYS 32
 
 /* Arithmetic of the shell contraction. */
 enum {
@@ -142,8 +162,9 @@ cd_status cd_tree_update(cd_tree tree, const float *rho, int rho_on_device, void
  * level-(l-1) ancestor; cells of the inner region get 0.
  *   scheme         CD_DIRS_*; p0, p1 as documented there
  *   dirs           CD_DIRS_CUSTOM only: n_custom x 3 doubles (host)
- *   mode           CD_MODE_PREC or CD_MODE_INSITU (the tables are built either way; in-situ
- *                  evaluations use only the local ones)
+ *   mode           CD_MODE_PREC, CD_MODE_INSITU (the tables are built either way; in-situ
+ *                  evaluations use only the local ones) or CD_MODE_CONE (tables averaged
+ *                  over each direction's cone)
  * 1 <= number of directions <= 768.  Components below 1e-14 in magnitude are
  * set to zero and each vector renormalised. */
 cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs, int n_custom, int mode,
@@ -218,6 +239,11 @@ cd_status cd_tree_leaves(cd_tree tree, int8_t *level, int32_t *ijk);
 
 /* Number of directions and, if dirs != NULL, the n_dir x 3 unit vectors (host). */
 cd_status cd_geom_info(cd_geom geom, int *n_dir, double *dirs);
+
+/* Rays the geometric factors average over: *n_sub per direction (1 unless the
+ * geometry's mode is CD_MODE_CONE, then CD_CONE_SUBRAYS) and, if rays != NULL,
+ * the n_dir x n_sub x 3 unit vectors (host), direction-major. */
+cd_status cd_geom_rays(cd_geom geom, int *n_sub, double *rays);
 
 /* Synchronises `stream` and reports whether any library kernel on the current
  * device gave up a bounded wait since the last call: CD_ETIMEOUT (flag

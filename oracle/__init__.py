@@ -134,17 +134,19 @@ def cone_rays(dirs, n_bins: int = None, rings: int = CONE_RINGS, azimuths: int =
         cos theta_r = 1 - (r + 1/2) (1 - cos alpha) / rings
         phi_rj      = 2 pi (j + [r odd] / 2) / azimuths
         v = cos theta_r u + sin theta_r (cos phi_rj e1 + sin phi_rj e2)
-    with e1 = unit(e_a x u), a the axis of the smallest |u_a| (the first on
-    ties), and e2 = u x e1.  Sub-ray index r * azimuths + j.  Components
-    below 1e-14 in magnitude are zeroed and the vector renormalised, as for
-    the directions.  The pieces have equal solid angle, so the cone average of
+    with e1 = unit(e_a x u), a the first axis whose |u_a| is within 1e-9 of
+    the smallest (so that exact ties, e.g. |u_x| = |u_y| at 45 degrees, pick
+    the same axis whatever the last bit of the vector), and e2 = u x e1.
+    Sub-ray index r * azimuths + j.  Components below 1e-14 in magnitude are
+    zeroed and the vector renormalised, as for the directions.  The pieces have equal solid angle, so the cone average of
     a quantity is the plain mean over the sub-rays (a midpoint rule for the
     integral over the cap)."""
     u = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
     nd = u.shape[0]
     if cos_alpha is None:
         cos_alpha = 1.0 - 2.0 / float(n_bins if n_bins is not None else nd)
-    axis = np.argmin(np.abs(u), axis=1)
+    au = np.abs(u)
+    axis = np.argmax(au <= au.min(axis=1, keepdims=True) + 1e-9, axis=1)
     e1 = np.cross(np.eye(3)[axis], u)
     e1 /= np.linalg.norm(e1, axis=1, keepdims=True)
     e2 = np.cross(u, e1)

@@ -16,7 +16,7 @@ from . import _build
 
 CD_OK, CD_EINVAL, CD_ENOMEM, CD_ECUDA, CD_ETIMEOUT, CD_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 DIRS_HEALPIX, DIRS_MXN, DIRS_AXES, DIRS_CUSTOM = 0, 1, 2, 3
-MODE_PREC, MODE_INSITU = 0, 1
+MODE_PREC, MODE_INSITU, MODE_CONE = 0, 1, 2
 FP32, BF16 = 0, 1
 
 _STATUS = {CD_EINVAL: "EINVAL", CD_ENOMEM: "ENOMEM", CD_ECUDA: "ECUDA", CD_ETIMEOUT: "ETIMEOUT",
@@ -25,7 +25,8 @@ _STATUS = {CD_EINVAL: "EINVAL", CD_ENOMEM: "ENOMEM", CD_ECUDA: "ECUDA", CD_ETIME
 # every symbol include/colden.h declares (checked by the ABI test)
 EXPORTS = (
     "cd_opts_default", "cd_build_tree_uniform", "cd_build_tree_amr", "cd_tree_update", "cd_precompute_geometry",
-    "cd_column_density", "cd_tree_info", "cd_tree_leaves", "cd_geom_info", "cd_stats_reset", "cd_stats_get",
+    "cd_column_density", "cd_tree_info", "cd_tree_leaves", "cd_geom_info", "cd_geom_rays", "cd_stats_reset",
+    "cd_stats_get",
     "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_column_density_noalloc", "cd_device_status",
     "cd_column_density_batch", "cd_batch_create", "cd_batch_run", "cd_batch_info", "cd_batch_free",
     # include/colden_learned.h
@@ -96,6 +97,7 @@ def load(build_if_missing: bool = False):
     L.cd_tree_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I64)]
     L.cd_tree_leaves.argtypes = [P, P, P]
     L.cd_geom_info.argtypes = [P, ctypes.POINTER(I), P]
+    L.cd_geom_rays.argtypes = [P, ctypes.POINTER(I), P]
     L.cd_tree_free.argtypes = [P]
     L.cd_tree_free.restype = None
     L.cd_geom_free.argtypes = [P]
@@ -200,6 +202,12 @@ class Geometry:
         d = np.zeros((self.n_dir, 3))
         _check(load().cd_geom_info(self._h, ctypes.byref(nd), d.ctypes.data_as(ctypes.c_void_p)))
         self.dirs = d
+        ns = ctypes.c_int()
+        _check(load().cd_geom_rays(self._h, ctypes.byref(ns), None))
+        self.n_sub = ns.value
+        r = np.zeros((self.n_dir, self.n_sub, 3))
+        _check(load().cd_geom_rays(self._h, ctypes.byref(ns), r.ctypes.data_as(ctypes.c_void_p)))
+        self.rays = r
 
     @property
     def handle(self):
@@ -291,7 +299,8 @@ def stats_get(kind: int):
 def precompute_geometry(scheme="healpix", p0: int = 1, p1: int = 0, dirs=None, mode: int = MODE_PREC,
                         stream=None) -> Geometry:
     """cd_precompute_geometry.  scheme: 'healpix' (p0 = Nside), 'mxn' (p0 = M,
-    p1 = N), 'axes', 'custom' (dirs: [n, 3])."""
+    p1 = N), 'axes', 'custom' (dirs: [n, 3]); mode: MODE_PREC, MODE_INSITU or
+    MODE_CONE (weights averaged over each direction's cone)."""
     code = {"healpix": DIRS_HEALPIX, "mxn": DIRS_MXN, "axes": DIRS_AXES, "custom": DIRS_CUSTOM}[scheme] \
         if isinstance(scheme, str) else int(scheme)
     arr, n = None, 0

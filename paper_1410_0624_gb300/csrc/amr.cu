@@ -136,6 +136,7 @@ struct ShellListArgs {
     float *out;                  // [n][nd]
     const int2 *tab[4];
     const int *cmax[4];
+    int maxe;                    // entries per table row
 };
 
 // Eq. N_discret for a list of receiving cells: thread per (cell, direction),
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(256) shell_list_fp32(ShellListArgs P)
             const int R = region_side(t);
             const int64_t ox = 2 * ((cx >> t) - 1), oy = 2 * ((cy >> t) - 1), oz = 2 * ((cz >> t) - 1);
             const int cfg = (int)(m & ((1u << (3 * t)) - 1));
-            const int2 *row = P.tab[t] + (size_t)cfg * CD_MAXE * nd + d;
+            const int2 *row = P.tab[t] + (size_t)cfg * P.maxe * nd + d;
             const int cnt = P.cmax[t][cfg];
             const float *rho = P.lvl[t];
             float part = 0.f;
@@ -619,6 +620,7 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
         A.tab[q] = g->tab[q];
         A.cmax[q] = g->cmax[q];
     }
+    A.maxe = g->maxe;
     A.nd = nd;
     // far-shell prefixes of the refined cells
     for (int k = 3; k <= L - 2 && !insitu; ++k) {

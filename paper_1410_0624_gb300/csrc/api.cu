@@ -250,7 +250,7 @@ cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs,
         return CD_EINVAL;
     }
     *out = nullptr;
-    if (mode != CD_MODE_PREC && mode != CD_MODE_INSITU) {
+    if (mode != CD_MODE_PREC && mode != CD_MODE_INSITU && mode != CD_MODE_CONE) {
         set_error("unknown mode %d", mode);
         return CD_EINVAL;
     }
@@ -269,16 +269,21 @@ cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs,
     g->mode = mode;
     g->dirs_host = new double[3 * nd];
     memcpy(g->dirs_host, buf, sizeof(double) * 3 * nd);
+    static_assert(CD_CONE_RINGS * CD_CONE_AZ == CD_CONE_SUBRAYS, "sub-ray count of colden.h");
+    g->n_sub = mode == CD_MODE_CONE ? CD_CONE_SUBRAYS : 1;
+    if (g->n_sub > 1) {
+        g->rays_host = new double[(size_t)3 * nd * g->n_sub];
+        make_cone_rays(g->dirs_host, nd, g->rays_host);
+    } else {
+        g->rays_host = g->dirs_host;
+    }
     auto fail = [&](cd_status code) {
         cd_geom_free(g);
         return code;
     };
     bool ok = cudaMalloc(&g->dirs_dev, sizeof(double) * 3 * nd) == cudaSuccess;
-    for (int t = 1; t <= 3 && ok; ++t) {
-        const size_t ncfg = (size_t)1 << (3 * t);
-        ok = cudaMalloc(&g->tab[t], ncfg * CD_MAXE * nd * sizeof(int2)) == cudaSuccess &&
-             cudaMalloc(&g->cmax[t], ncfg * sizeof(int)) == cudaSuccess;
-    }
+    if (ok && g->n_sub > 1) ok = cudaMalloc(&g->rays_dev, sizeof(double) * 3 * nd * g->n_sub) == cudaSuccess;
+    else g->rays_dev = g->dirs_dev;
     ok = ok && cudaMalloc(&g->kloc, sizeof(float) * 64 * nd) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -286,7 +291,9 @@ cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs,
         return fail(CD_ENOMEM);
     }
     if (cudaMemcpyAsync(g->dirs_dev, g->dirs_host, sizeof(double) * 3 * nd, cudaMemcpyHostToDevice, s) !=
-        cudaSuccess) {
+            cudaSuccess ||
+        (g->n_sub > 1 && cudaMemcpyAsync(g->rays_dev, g->rays_host, sizeof(double) * 3 * nd * g->n_sub,
+                                         cudaMemcpyHostToDevice, s) != cudaSuccess)) {
         set_error("direction upload failed");
         return fail(CD_ECUDA);
     }
@@ -314,8 +321,8 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
     cudaStream_t s = (cudaStream_t)stream;
     const bool insitu = geom->mode == CD_MODE_INSITU;
     if (opts.net) {
-        if (insitu) {
-            set_error("the learned correction is defined on the precalculated form");
+        if (geom->mode != CD_MODE_PREC) {
+            set_error("the learned correction is defined on the single-ray precalculated form");
             return CD_EUNSUPPORTED;
         }
         return column_density_learned(tree, geom, opts, n_h, a_v, shield, s);
@@ -450,6 +457,17 @@ cd_status cd_geom_info(cd_geom g, int *n_dir, double *dirs)
     return CD_OK;
 }
 
+cd_status cd_geom_rays(cd_geom g, int *n_sub, double *rays)
+{
+    if (!g) {
+        set_error("geometry is NULL");
+        return CD_EINVAL;
+    }
+    if (n_sub) *n_sub = g->n_sub;
+    if (rays) memcpy(rays, g->rays_host, sizeof(double) * 3 * g->n_dir * g->n_sub);
+    return CD_OK;
+}
+
 void cd_tree_free(cd_tree t)
 {
     if (!t) return;
@@ -479,6 +497,7 @@ void cd_geom_free(cd_geom g)
 {
     if (!g) return;
     cudaDeviceSynchronize();
+    if (g->rays_dev && g->rays_dev != g->dirs_dev) cudaFree(g->rays_dev);
     if (g->dirs_dev) cudaFree(g->dirs_dev);
     for (int t = 0; t < 4; ++t) {
         if (g->tab[t]) cudaFree(g->tab[t]);
@@ -486,6 +505,7 @@ void cd_geom_free(cd_geom g)
     }
     if (g->kloc) cudaFree(g->kloc);
     if (g->wb) cudaFree(g->wb);
+    if (g->rays_host != g->dirs_host) delete[] g->rays_host;
     delete[] g->dirs_host;
     delete g;
 }

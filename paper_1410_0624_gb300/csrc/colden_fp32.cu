@@ -28,6 +28,7 @@ struct ExtArgs {
     int span;
     const int2 *tab[4];
     const int *cmax[4];
+    int maxe;           // entries per table row
 };
 
 __global__ void __launch_bounds__(kExtThreads) shell_sum_fp32(ExtArgs P)
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(kExtThreads) shell_sum_fp32(ExtArgs P)
                       az = span >= t ? 2 * (cz >> t) : 0;
             const int anchor = region_base(t) + ax + R * (ay + R * az);
             const int cfg = (int)(m & ((1u << (3 * t)) - 1));
-            const int2 *row = P.tab[t] + (size_t)cfg * CD_MAXE * nd + d;
+            const int2 *row = P.tab[t] + (size_t)cfg * P.maxe * nd + d;
             const int n = P.cmax[t][cfg];
             float part = 0.f;
             for (int e = 0; e < n; ++e) {
@@ -104,6 +105,7 @@ cd_status launch_ext_fp32(const ExtLaunch &a, cd_geom g, cudaStream_t s)
         P.tab[t] = g->tab[t];
         P.cmax[t] = g->cmax[t];
     }
+    P.maxe = g->maxe;
     const uint64_t nblk = 1ull << (3 * (a.k - span));
     LaunchScope ls(CD_K_SHELL, s);
     shell_sum_fp32<<<(unsigned)nblk, kExtThreads, 0, s>>>(P);

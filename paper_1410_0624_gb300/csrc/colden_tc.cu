@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 2) shell_sum_tc(TcArgs P)
 
 // ---- B operand construction (FP64 geometry, stored BF16) -----------------------
 
-__global__ void build_b(int nd, const double *__restrict__ dirs, __nv_bfloat16 *__restrict__ B)
+__global__ void build_b(int nd, const double *__restrict__ rays, int ns, __nv_bfloat16 *__restrict__ B)
 {
     const int N = 8 * nd;
     const int64_t total = (int64_t)64 * kChunks * kChunkBricks * 8 * N;
@@ -341,8 +341,7 @@ __global__ void build_b(int nd, const double *__restrict__ dirs, __nv_bfloat16 *
             const int s = a + 6 * bb + 36 * cc;
             const int oP = cls & 7, opP = cls >> 3;
             const int cfg = t == 1 ? o : t == 2 ? (oP << 3) | o : (opP << 6) | (oP << 3) | o;
-            const double u[3] = {dirs[3 * d], dirs[3 * d + 1], dirs[3 * d + 2]};
-            v = (float)(shell_weight(t, cfg, s, u) * (double)(1 << (t - 1)));
+            v = (float)(shell_weight_avg(t, cfg, s, rays + (size_t)3 * ns * d, ns) * (double)(1 << (t - 1)));
         }
         B[e] = __float2bfloat16_rn(v);
     }
@@ -407,7 +406,7 @@ cd_status build_tc_tables(cd_geom g, cudaStream_t s)
         g->wb_bytes = elems * sizeof(__nv_bfloat16);
     }
     LaunchScope ls(CD_K_OTHER, s);
-    build_b<<<num_sms() * 8, 256, 0, s>>>(nd, g->dirs_dev, g->wb);
+    build_b<<<num_sms() * 8, 256, 0, s>>>(nd, g->rays_dev, g->n_sub, g->wb);
     CD_CHECK_LAUNCH();
     return CD_OK;
 }

@@ -11,7 +11,8 @@
 
 #define CD_MAXL 16          // deepest level a tree may have
 #define CD_STENCIL 216      // 6 x 6 x 6 level-l cells around a level-(l-1) ancestor
-#define CD_MAXE 16          // most non-zero weights one ray can have in a 6^3 stencil
+#define CD_CONE_RINGS 4     // sub-ray pattern of CD_MODE_CONE: rings of equal solid angle ...
+#define CD_CONE_AZ 8        // ... times azimuths per ring
 #define CD_MAXDIR 768       // the leaf kernel stages 64 * n_dir floats in shared memory
 
 namespace cd {
@@ -148,16 +149,22 @@ struct cd_geom_s {
     int mode = 0;
     double *dirs_host = nullptr;        // n_dir x 3
     double *dirs_dev = nullptr;
+    // the rays the weights are averaged over: n_sub per direction, [nd][n_sub][3];
+    // one (the direction itself, rays_dev == dirs_dev) unless the mode is CD_MODE_CONE
+    int n_sub = 1;
+    double *rays_host = nullptr;
+    double *rays_dev = nullptr;
     // sparse FP32 shell tables, t = 1..3 (index 0 unused): entry e of (cfg, d)
-    // at tab[t][(cfg * CD_MAXE + e) * nd + d] = {offset in the staged region of
-    // table t, weight bits}; cmax[t][cfg] = largest non-zero count over d
+    // at tab[t][(cfg * maxe + e) * nd + d] = {offset in the staged region of
+    // table t, weight bits}; cmax[t][cfg] = largest non-zero count over d;
+    // maxe = largest count over every table, configuration and direction
+    int maxe = 0;
     int2 *tab[4] = {};
     int *cmax[4] = {};
     float *kloc = nullptr;              // [8 t][8 s][nd], units of dx
     // BF16 B operands for the tensor-core contraction (see colden_tc.cu)
     __nv_bfloat16 *wb = nullptr;
     size_t wb_bytes = 0;
-    int max_entries = 0;
     int dev = 0;
 };
 
@@ -199,6 +206,8 @@ cd_status launch_insitu(cd_tree t, cd_geom g, int k, int64_t n, const uint64_t *
 
 // geometry.cu
 int make_directions(int scheme, int p0, int p1, const double *custom, int n_custom, double *out);
+// the CD_CONE_RINGS * CD_CONE_AZ sub-rays of each of the nd directions, out[nd][n_sub][3]
+void make_cone_rays(const double *dirs, int nd, double *out);
 cd_status build_geometry_tables(cd_geom g, cudaStream_t s);
 
 // colden_fp32.cu

@@ -54,4 +54,13 @@ __device__ __forceinline__ double shell_weight(int t, int cfg, int s, const doub
     return inner ? 0.0 : path_in_cube(p, u, a, b, c);
 }
 
+// shell_weight averaged over the ns rays u[0 .. 3 ns - 1] of one direction
+// (ns = 1: the direction itself, bit for bit)
+__device__ __forceinline__ double shell_weight_avg(int t, int cfg, int s, const double *u, int ns)
+{
+    double acc = 0.0;
+    for (int j = 0; j < ns; ++j) acc += shell_weight(t, cfg, s, u + 3 * j);
+    return acc / ns;
+}
+
 }  // namespace cd

@@ -405,6 +405,10 @@ cd_status cd_learned_features(cd_tree tree, cd_geom geom, int64_t n, const int64
 {
     cd_status st = check_tree_geom(tree, geom);
     if (st != CD_OK) return st;
+    if (geom->mode != CD_MODE_PREC) {
+        set_error("the learned inputs are defined on the single-ray precalculated form");
+        return CD_EUNSUPPORTED;
+    }
     if (n < 0 || !x || (!leaves && n > tree->n_leaf)) {
         set_error("bad feature arguments (n = %lld)", (long long)n);
         return CD_EINVAL;

@@ -54,6 +54,20 @@ def test_cone_ray_pattern(name):
         assert np.allclose(v.reshape(-1, 3).mean(axis=0), 0.5 * (1.0 + cos_a) * u, atol=1e-14)
 
 
+@pytest.mark.parametrize("name", ["healpix2", "mxn4x3", "axes"])
+def test_frame_is_stable_under_last_bit_changes(name):
+    """Sets with exact ties (|u_x| = |u_y| at 45 degrees, zero components) give
+    the same sub-rays when every component moves by a few ulps, as happens
+    between two independent computations of the same direction set."""
+    dirs = _sets()[name]
+    rng = np.random.default_rng(0)
+    base = oracle.cone_rays(dirs)
+    for _ in range(20):
+        d = dirs * (1.0 + rng.integers(-4, 5, size=dirs.shape) * 2.0 ** -52)
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        assert np.max(np.abs(oracle.cone_rays(d, n_bins=len(dirs)) - base)) < 1e-13
+
+
 def test_zero_cone_is_the_ray():
     dirs = oracle.dirs_healpix(1)
     rays = oracle.cone_rays(dirs, cos_alpha=1.0)
