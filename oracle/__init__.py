@@ -293,6 +293,32 @@ def chi(N: np.ndarray, sigma: float = SIGMA_PAPER) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------
+# Heating of the application (§5, Eqs. G0_eff, gamma_uv, gamma_cr)
+# ----------------------------------------------------------------------------
+
+G0_DRAINE = 1.7   # the background UV field of §5, in Habing units
+
+
+def heating_efficiency(g0_eff, T, n_e):
+    """Photoelectric efficiency of Wolfire et al. (1995) as §5 states it, with
+    x = G0_eff sqrt(T) / n_e:
+        eps = 4.9e-2 / (1 + (x / 1925)^0.73) + 3.7e-2 (T / 1e4)^0.7 / (1 + x / 5000)."""
+    g0_eff, T, n_e = (np.asarray(a, dtype=np.float64) for a in (g0_eff, T, n_e))
+    x = g0_eff * np.sqrt(T) / n_e
+    return 4.9e-2 / (1.0 + (x / 1925.0) ** 0.73) + 3.7e-2 * (T / 1e4) ** 0.7 / (1.0 + x / 5000.0)
+
+
+def heating(chi_, n, T, n_e, G0: float = G0_DRAINE):
+    """Per-cell heating of §5: G0_eff = chi G0 (Eq. G0_eff), the photoelectric
+    rate Gamma_UV = 1e-24 eps G0_eff n (Eq. gamma_uv) and the cosmic-ray rate
+    Gamma_CR = 1e-27 n (Eq. gamma_cr), in erg cm^-3 s^-1.  Returns
+    (G0_eff, Gamma_UV, Gamma_CR)."""
+    chi_, n = np.asarray(chi_, dtype=np.float64), np.asarray(n, dtype=np.float64)
+    g0 = chi_ * G0
+    return g0, 1e-24 * heating_efficiency(g0, T, n_e) * g0 * n, 1e-27 * n
+
+
+# ----------------------------------------------------------------------------
 # Leaf order helpers (plain bit interleaving; octant bits x=1, y=2, z=4)
 # ----------------------------------------------------------------------------
 
