@@ -347,6 +347,22 @@ def run_ours(args):
     bpu = algo_bytes_per_cell_dir(nd)
     achieved = bpu * n_leaf * nd / (dom_ms / 1e3) / 1e9
 
+    # ---- the heating epilogue of §5 on the step's screening factor (HBM-bound, timed alone) ----
+    heat = None
+    if args.heating:
+        g = torch.Generator(device=dev).manual_seed(5)
+        T_k = 10.0 ** (1.0 + 3.2 * torch.rand(n_leaf, device=dev, generator=g))
+        n_e = 10.0 ** (-4.0 + 4.5 * torch.rand(n_leaf, device=dev, generator=g))
+        outs = [torch.empty(n_leaf, device=dev) for _ in range(3)]
+        hstep = lambda: colden.heating(tree, sh, T_k, n_e, 1.7, *outs, stream=stream)
+        for _ in range(args.warmup):
+            hstep()
+        hms = _time_steps(hstep, flush, stream, args.steps)
+        hbytes = 28 * n_leaf
+        heat = {"ms": hms, "algo_bytes": hbytes, "GB/s": hbytes / (hms / 1e3) / 1e9,
+                "frac": hbytes / (hms / 1e3) / 1e9 / peak, "peak_kind": peak_kind,
+                "note": "chi, T, n_e, leaf density in (16 B), G0_eff, Gamma_UV, Gamma_CR out (12 B) per leaf"}
+
     # ---- the other form (FP32 plain vs BF16 tensor cores), same workload ----
     other = None
     other_name = "fp32" if args.precision == "bf16" else "bf16"
@@ -404,6 +420,8 @@ def run_ours(args):
                              "kernel_ms": dom_ms, "peak_kind": peak_kind, "algo_bytes_per_cell_dir": bpu},
                 "step_roofline_frac": bpu * n_leaf * nd / (ms / 1e3) / 1e9 / peak,
                 "kernels": kern, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "error_vs_oracle": err}
+        if heat is not None:
+            line["heating"] = heat
         if other is not None:
             line["compare"] = other
             line["speedup_vs_" + other_name] = other["ms_per_step"] / ms
@@ -841,6 +859,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32-plain comparison run")
     ap.add_argument("--level", type=int, default=8)
     ap.add_argument("--nside", type=int, default=2)
+    ap.add_argument("--heating", action="store_true", help="uniform workload: also time the heating epilogue")
     ap.add_argument("--geometry", default="ray", choices=["ray", "cone"],
                     help="uniform workload: one ray per direction, or factors averaged over each direction's cone")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)

@@ -229,6 +229,29 @@ void cd_batch_free(cd_batch batch);
 cd_status cd_column_density_noalloc(cd_tree tree, cd_geom geom, const cd_opts *opts, float *n_h, float *a_v,
                                     float *shield, void *stream);
 
+/* The heating of the application (§5) for every leaf, in the output order
+ * (the order of cd_column_density's shield):
+ *   g0_eff[i]   = chi[i] G0                                      (Eq. G0_eff)
+ *   gamma_uv[i] = 1e-24 eps G0_eff n   erg cm^-3 s^-1            (Eq. gamma_uv)
+ *   gamma_cr[i] = 1e-27 n              erg cm^-3 s^-1            (Eq. gamma_cr)
+ * with n the tree's leaf density (cm^-3, as last built or updated) and the
+ * photoelectric efficiency of Wolfire et al. (1995), x = G0_eff sqrt(T) / n_e:
+ *   eps = 4.9e-2 / (1 + (x / 1925)^0.73) + 3.7e-2 (T / 1e4)^0.7 / (1 + x / 5000).
+ *   chi        n_leaf floats (device): the attenuation factor; the paper's
+ *              chi = <exp(-2e-21 N)> is cd_column_density's shield with
+ *              av_per_nh = 1 and shield_k = 2e-21
+ *   T, n_e     n_leaf floats (device): temperature (K, >= 0) and electron
+ *              density (cm^-3, > 0; §5 takes it from Wolfire et al. 2003, which
+ *              the paper does not restate, so the caller supplies it); needed
+ *              only for gamma_uv, may be NULL otherwise
+ *   G0         the unscreened field in Habing units (§5: 1.7), finite, >= 0
+ *   g0_eff, gamma_uv, gamma_cr   caller-owned device outputs of n_leaf
+ *              floats, each may be NULL
+ * FP32 arithmetic (powf, sqrtf).  Errors: CD_EINVAL (NULL tree or chi,
+ * gamma_uv without T or n_e, bad G0).  Asynchronous on `stream`. */
+cd_status cd_heating(cd_tree tree, const float *chi, const float *T, const float *n_e, double G0, float *g0_eff,
+                     float *gamma_uv, float *gamma_cr, void *stream);
+
 /* Sizes of a tree: number of leaves, finest level, base level, number of
  * leaf-bearing octs.  Any pointer may be NULL. */
 cd_status cd_tree_info(cd_tree tree, int64_t *n_leaf, int *max_level, int *base_level, int64_t *n_oct);
@@ -262,7 +285,8 @@ enum {
     CD_K_FEATURES = 5,     /* per-level inputs of the network and the FP32 learned combine */
     CD_K_RAYMARCH = 6,     /* exact ray-marcher */
     CD_K_LEARNED = 7,      /* fused per-leaf learned kernel (BF16 tensor cores) */
-    CD_K_COUNT = 8
+    CD_K_HEATING = 8,      /* the heating epilogue (cd_heating) */
+    CD_K_COUNT = 9
 };
 /* Resets the counters; with timing != 0 later launches also record CUDA
  * events on their stream (a synchronisation happens in cd_stats_get). */

@@ -26,7 +26,7 @@ _STATUS = {CD_EINVAL: "EINVAL", CD_ENOMEM: "ENOMEM", CD_ECUDA: "ECUDA", CD_ETIME
 EXPORTS = (
     "cd_opts_default", "cd_build_tree_uniform", "cd_build_tree_amr", "cd_tree_update", "cd_precompute_geometry",
     "cd_column_density", "cd_tree_info", "cd_tree_leaves", "cd_geom_info", "cd_geom_rays", "cd_stats_reset",
-    "cd_stats_get",
+    "cd_stats_get", "cd_heating",
     "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_column_density_noalloc", "cd_device_status",
     "cd_column_density_batch", "cd_batch_create", "cd_batch_run", "cd_batch_info", "cd_batch_free",
     # include/colden_learned.h
@@ -36,8 +36,8 @@ EXPORTS = (
 )
 _VOID = ("cd_opts_default", "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_stats_reset", "cd_batch_free",
          "cd_adam_default", "cd_net_free", "cd_net_num_params")
-K_RESTRICT, K_SHELL, K_LEAF, K_OTHER, K_NET, K_FEATURES, K_RAYMARCH, K_LEARNED = 0, 1, 2, 3, 4, 5, 6, 7
-KERNEL_KINDS = ("restrict", "shell", "leaf", "other", "net", "features", "raymarch", "learned")
+K_RESTRICT, K_SHELL, K_LEAF, K_OTHER, K_NET, K_FEATURES, K_RAYMARCH, K_LEARNED, K_HEATING = range(9)
+KERNEL_KINDS = ("restrict", "shell", "leaf", "other", "net", "features", "raymarch", "learned", "heating")
 
 
 class ColdenError(RuntimeError):
@@ -98,6 +98,7 @@ def load(build_if_missing: bool = False):
     L.cd_tree_leaves.argtypes = [P, P, P]
     L.cd_geom_info.argtypes = [P, ctypes.POINTER(I), P]
     L.cd_geom_rays.argtypes = [P, ctypes.POINTER(I), P]
+    L.cd_heating.argtypes = [P, P, P, P, ctypes.c_double, P, P, P, P]
     L.cd_tree_free.argtypes = [P]
     L.cd_tree_free.restype = None
     L.cd_geom_free.argtypes = [P]
@@ -326,6 +327,16 @@ def column_density(tree: Tree, geom: Geometry, n_h=None, a_v=None, shield=None, 
     _check(load().cd_column_density(tree.handle, geom.handle, ctypes.byref(o), _dptr(n_h), _dptr(a_v),
                                     _dptr(shield), ctypes.c_void_p(_stream_ptr(stream))))
     return n_h, a_v, shield
+
+
+def heating(tree: Tree, chi, T=None, n_e=None, G0: float = 1.7, g0_eff=None, gamma_uv=None, gamma_cr=None,
+            stream=None):
+    """cd_heating: G0_eff = chi G0, the photoelectric rate (needs T and n_e)
+    and the cosmic-ray rate per leaf, into caller-owned CUDA float32 tensors
+    (any may be None)."""
+    _check(load().cd_heating(tree.handle, _dptr(chi), _dptr(T), _dptr(n_e), float(G0), _dptr(g0_eff),
+                             _dptr(gamma_uv), _dptr(gamma_cr), ctypes.c_void_p(_stream_ptr(stream))))
+    return g0_eff, gamma_uv, gamma_cr
 
 
 def column_density_noalloc(tree: Tree, geom: Geometry, n_h=None, a_v=None, shield=None,
