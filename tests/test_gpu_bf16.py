@@ -95,6 +95,27 @@ def test_bf16_differs_from_fp32_but_within_tolerance():
     assert rel.max() <= RTOL
 
 
+@pytest.mark.parametrize("dset", ["healpix1", "healpix2", "mxn58", "custom8"])
+def test_bf16_parity_128cube(dset):
+    """128^3 leaves: the oct level (k = 6) and the level above take the
+    TMA-fed tensor-core shell kernel; every leaf against the FP32 path,
+    sampled leaves against the oracle."""
+    L, box = 7, 10 * PC
+    rho = synth.lognormal_grf(128, 30.0, 2.0, seed=300)
+    tree = colden.build_tree_uniform(torch.from_numpy(rho).cuda(), box)
+    geom, dirs = _geom(dset)
+    nd = geom.n_dir
+    n_h, _, sh = _run(tree, geom, colden.BF16)
+    n32, _, sh32 = _run(tree, geom, colden.FP32)
+    rel = np.abs(n_h - n32) / n32
+    assert rel.max() <= RTOL, rel.max()
+    assert np.max(np.abs(sh - sh32)) <= SHIELD_ATOL
+    lv, ijk = tree.leaves()
+    sel = np.random.default_rng(7).choice(len(lv), 400, replace=False)
+    ref = oracle.Tree.uniform(rho, box).column_density(dirs, lv[sel], ijk[sel])
+    assert np.max(np.abs(n_h.reshape(-1, nd)[sel] - ref) / ref) <= RTOL
+
+
 def test_bf16_parity_256cube_sampled():
     """256^3 leaves, 10 pc, k^-11/3 log-normal (mean 30, sigma_ln 2, seed 2),
     48 HEALPix directions: the full-size launch, sampled leaves vs the oracle."""
