@@ -13,109 +13,129 @@
 namespace cd {
 namespace {
 
-// One thread per level-(L-1) cell: reads its 8 leaves from the row-major input,
-// writes them to the Morton leaf array and their mean to level L-1.
-__global__ void restrict_from_leaves(const float *__restrict__ in, int L, float *__restrict__ leaf,
-                                     float *__restrict__ parent)
+// Each block takes a B x B x B patch of one dense level m (B = 2^b <= 8, one
+// thread per cell) and reduces it b times inside shared memory: at every
+// reduction the cells of level m-1 in the patch take the mean of their 8
+// children (summed in octant order, then x 1/8) and the children are written
+// as the BF16 brick of their parent.  So one launch writes b coarser levels and
+// b brick levels, where separate launches per level cost mostly launch time.
+//   top != 0: level m is L - 1 and each thread first reads its 8 leaves from the
+//   row-major input, writes them to the Morton leaf array and their mean to m.
+struct PatchPtrs {
+    float *lvl[CD_MAXL + 1];
+    __nv_bfloat16 *brick[CD_MAXL + 1];
+};
+
+template <bool top>
+__global__ void __launch_bounds__(512) restrict_patch(const float *__restrict__ in, int m, int b,
+                                                      float *__restrict__ leaf, const __grid_constant__ PatchPtrs P)
 {
-    const int64_t np = (int64_t)1 << (L - 1);
-    const int64_t total = np * np * np;
-    const int64_t nl = np * 2;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t x = (uint32_t)(p % np), y = (uint32_t)((p / np) % np), z = (uint32_t)(p / (np * np));
-        float c[8];
+    __shared__ float s_val[2][512];
+    const int B = 1 << b;
+    const int t = threadIdx.x;
+    const int64_t nm = (int64_t)1 << m;                                   // cells per axis at level m
+    const int64_t nb = nm >> b;                                           // patches per axis
+    const int64_t bx = blockIdx.x % nb, by = (blockIdx.x / nb) % nb, bz = blockIdx.x / (nb * nb);
+    if (t < B * B * B) {
+        const int tx = t & (B - 1), ty = (t >> b) & (B - 1), tz = t >> (2 * b);
+        const int64_t x = bx * B + tx, y = by * B + ty, z = bz * B + tz;
+        float v;
+        if (top) {
+            const int64_t nl = nm * 2;
+            float c[8];
 #pragma unroll
-        for (int o = 0; o < 8; ++o) {
-            const int64_t cx = 2 * x + (o & 1), cy = 2 * y + ((o >> 1) & 1), cz = 2 * z + ((o >> 2) & 1);
-            c[o] = in[(cz * nl + cy) * nl + cx];
+            for (int o = 0; o < 8; ++o) {
+                const int64_t cx = 2 * x + (o & 1), cy = 2 * y + ((o >> 1) & 1), cz = 2 * z + ((o >> 2) & 1);
+                c[o] = in[(cz * nl + cy) * nl + cx];
+            }
+            float sum = 0.f;
+#pragma unroll
+            for (int o = 0; o < 8; ++o) sum += c[o];
+            v = sum * 0.125f;
+            float4 *dst = reinterpret_cast<float4 *>(leaf + 8 * morton3((uint32_t)x, (uint32_t)y, (uint32_t)z));
+            dst[0] = make_float4(c[0], c[1], c[2], c[3]);
+            dst[1] = make_float4(c[4], c[5], c[6], c[7]);
+            P.lvl[m][(z * nm + y) * nm + x] = v;
+        } else {
+            v = P.lvl[m][(z * nm + y) * nm + x];
         }
-        float s = 0.f;
+        s_val[0][t] = v;
+    }
+    __syncthreads();
+    int cur = 0;
+    for (int r = 0, n = B; r < b; ++r, n >>= 1) {
+        const int h = n >> 1, lh = b - r - 1;                             // parent patch edge 2^lh
+        const int lc = m - r;                                             // child level
+        if (t < h * h * h) {
+            const int px = t & (h - 1), py = (t >> lh) & (h - 1), pz = t >> (2 * lh);
+            __align__(16) __nv_bfloat16 bv[8];
+            float sum = 0.f;
 #pragma unroll
-        for (int o = 0; o < 8; ++o) s += c[o];
-        parent[p] = s * 0.125f;
-        float4 *dst = reinterpret_cast<float4 *>(leaf + 8 * morton3(x, y, z));
-        dst[0] = make_float4(c[0], c[1], c[2], c[3]);
-        dst[1] = make_float4(c[4], c[5], c[6], c[7]);
+            for (int o = 0; o < 8; ++o) {
+                const int cx = 2 * px + (o & 1), cy = 2 * py + ((o >> 1) & 1), cz = 2 * pz + ((o >> 2) & 1);
+                const float c = s_val[cur][(cz * n + cy) * n + cx];
+                sum += c;
+                bv[o] = __float2bfloat16_rn(c);
+            }
+            const float v = sum * 0.125f;
+            const int64_t np = (int64_t)1 << (lc - 1);
+            const int64_t gx = (bx * B >> (r + 1)) + px, gy = (by * B >> (r + 1)) + py, gz = (bz * B >> (r + 1)) + pz;
+            const int64_t gp = (gz * np + gy) * np + gx;
+            P.lvl[lc - 1][gp] = v;
+            *reinterpret_cast<uint4 *>(P.brick[lc] + 8 * gp) = *reinterpret_cast<const uint4 *>(bv);
+            s_val[cur ^ 1][t] = v;
+        }
+        __syncthreads();
+        cur ^= 1;
     }
 }
 
-// One thread per level-(l-1) cell: mean of its 8 children at level l.
-__global__ void restrict_level(const float *__restrict__ child, int l, float *__restrict__ parent)
+PatchPtrs patch_ptrs(cd_tree t)
 {
-    const int64_t np = (int64_t)1 << (l - 1);
-    const int64_t total = np * np * np;
-    const int64_t nc = np * 2;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t x = p % np, y = (p / np) % np, z = p / (np * np);
-        float s = 0.f;
-#pragma unroll
-        for (int o = 0; o < 8; ++o) {
-            const int64_t cx = 2 * x + (o & 1), cy = 2 * y + ((o >> 1) & 1), cz = 2 * z + ((o >> 2) & 1);
-            s += child[(cz * nc + cy) * nc + cx];
-        }
-        parent[p] = s * 0.125f;
+    PatchPtrs P;
+    for (int l = 0; l <= CD_MAXL; ++l) {
+        P.lvl[l] = t->rho_lvl[l];
+        P.brick[l] = t->rho_brick[l];
     }
+    return P;
 }
 
-// BF16 brick copy of a dense level (l >= 1): brick p = the 8 children of
-// level-(l-1) cell p, 16 bytes, octant order.
-__global__ void to_bricks(const float *__restrict__ lvl, int l, __nv_bfloat16 *__restrict__ brick)
+// Patches of level m down to level 0: each launch reduces min(3, m) levels.
+cd_status restrict_from(cd_tree t, int m, cudaStream_t s)
 {
-    const int64_t np = (int64_t)1 << (l - 1);
-    const int64_t total = np * np * np;
-    const int64_t nc = np * 2;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t x = p % np, y = (p / np) % np, z = p / (np * np);
-        __align__(16) __nv_bfloat16 v[8];
-#pragma unroll
-        for (int o = 0; o < 8; ++o) {
-            const int64_t cx = 2 * x + (o & 1), cy = 2 * y + ((o >> 1) & 1), cz = 2 * z + ((o >> 2) & 1);
-            v[o] = __float2bfloat16_rn(lvl[(cz * nc + cy) * nc + cx]);
-        }
-        *reinterpret_cast<uint4 *>(brick + 8 * p) = *reinterpret_cast<uint4 *>(v);
+    const PatchPtrs P = patch_ptrs(t);
+    while (m >= 1) {
+        const int b = m < 3 ? m : 3;
+        const int64_t nb = (int64_t)1 << (m - b);
+        LaunchScope ls(CD_K_RESTRICT, s);
+        restrict_patch<false><<<(unsigned)(nb * nb * nb), 1 << (3 * b), 0, s>>>(nullptr, m, b, nullptr, P);
+        CD_CHECK_LAUNCH();
+        m -= b;
     }
-}
-
-inline unsigned grid_for(int64_t n, int block)
-{
-    int64_t g = (n + block - 1) / block;
-    if (g > 152 * 32) g = 152 * 32;
-    if (g < 1) g = 1;
-    return (unsigned)g;
+    return CD_OK;
 }
 
 }  // namespace
 
+// Leaves -> level L-1 (and the Morton leaf array) in the same launch as the
+// first reductions, then the coarser levels.
 cd_status restrict_uniform(cd_tree t, const float *rho_dev, cudaStream_t s)
 {
-    const int L = t->L;
-    const int64_t np = (int64_t)1 << (L - 1);
+    const int L = t->L, m = L - 1;
+    const int b = m < 3 ? m : 3;
+    const int64_t nb = (int64_t)1 << (m - b);
     {
         LaunchScope ls(CD_K_RESTRICT, s);
-        restrict_from_leaves<<<grid_for(np * np * np, 256), 256, 0, s>>>(rho_dev, L, t->rho_leaf, t->rho_lvl[L - 1]);
+        restrict_patch<true><<<(unsigned)(nb * nb * nb), 1 << (3 * b), 0, s>>>(rho_dev, m, b, t->rho_leaf,
+                                                                             patch_ptrs(t));
     }
     CD_CHECK_LAUNCH();
-    return restrict_dense(t, L - 1, s);
+    return restrict_from(t, m - b, s);
 }
 
 cd_status restrict_dense(cd_tree t, int top, cudaStream_t s)
 {
-    for (int l = top; l >= 1; --l) {
-        const int64_t n = (int64_t)1 << (l - 1);
-        LaunchScope ls(CD_K_RESTRICT, s);
-        restrict_level<<<grid_for(n * n * n, 256), 256, 0, s>>>(t->rho_lvl[l], l, t->rho_lvl[l - 1]);
-        CD_CHECK_LAUNCH();
-    }
-    for (int l = 1; l <= top; ++l) {
-        const int64_t n = (int64_t)1 << (l - 1);
-        LaunchScope ls(CD_K_RESTRICT, s);
-        to_bricks<<<grid_for(n * n * n, 256), 256, 0, s>>>(t->rho_lvl[l], l, t->rho_brick[l]);
-        CD_CHECK_LAUNCH();
-    }
-    return CD_OK;
+    return restrict_from(t, top, s);
 }
 
 }  // namespace cd
