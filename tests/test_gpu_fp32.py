@@ -160,6 +160,25 @@ def test_tree_update_matches_rebuild():
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("offset", [1, 2])
+def test_unaligned_density_input_matches_aligned(offset):
+    """A device density array that starts 4 or 8 bytes past an allocation
+    (the restriction reads pairs of leaves when the array is 8-byte aligned)."""
+    L, box = 5, 3 * PC
+    rho = synth.lognormal_grf(32, 30.0, 2.0, seed=13)
+    geom, _ = _geom("healpix1")
+    want = _run(colden.build_tree_uniform(torch.from_numpy(rho).cuda(), box), geom)
+    buf = torch.zeros(rho.size + offset, device="cuda")
+    buf[offset:] = torch.from_numpy(rho).cuda().reshape(-1)
+    t = colden.build_tree_uniform(buf[offset:].reshape(rho.shape), box)
+    got = _run(t, geom)
+    for x, y in zip(got, want):
+        assert np.array_equal(x, y)
+    colden.tree_update(t, buf[offset:])
+    for x, y in zip(_run(t, geom), want):
+        assert np.array_equal(x, y)
+
+
 def test_only_requested_outputs_written_and_launches_counted():
     L = 4
     rho = synth.lognormal_iid(16, 10.0, 1.5, seed=9)
