@@ -187,50 +187,49 @@ struct LeafListArgs {
 };
 
 // Internal + local terms and the epilogue for the leaf children of a list of
-// octs: half a warp per oct, lane q taking directions 4q .. 4q+3 (and
-// 64 + 4q .. when n_dir > 64), so the external and prefix rows arrive as
-// 16-byte loads and every child row leaves as contiguous 16-byte stores.  The
-// screening sum of a child is a fixed-order butterfly over the 16 lanes.
+// octs: one warp per oct, its lanes over (child t, 4 directions) units in
+// child-major order, so that consecutive lanes write consecutive 16-byte
+// pieces of the children's rows (an oct's leaf rows are consecutive unless a
+// refined sibling's subtree lies between them).  The oct's 8 densities and leaf
+// rows are read once per warp and broadcast by shuffles; the external and
+// prefix rows are shared by the 8 children (L1 hits); the local weights come
+// from shared memory.  The screening sum of a child adds its units' partial
+// sums in a fixed order through shared memory.
 // Directions are a multiple of 4 here (leaf_list_scalar serves the rest).
 __global__ void __launch_bounds__(256) leaf_list(LeafListArgs P)
 {
     extern __shared__ float sm[];
-    const int nd = P.nd;
+    const int nd = P.nd, nq = nd >> 2, nu = 8 * nq;
     float *s_k = sm;                          // [8 t][8 s][nd], times dx
     for (int i = threadIdx.x; i < 64 * nd; i += blockDim.x) s_k[i] = P.dx_leaf * P.kloc[i];
     __syncthreads();
-    const int lane = threadIdx.x & 31, half = lane >> 4, q = lane & 15;
-    const unsigned hmask = half ? 0xffff0000u : 0x0000ffffu;
-    const int64_t per_block = blockDim.x / 16;
-    // the two halves of a warp are independent (their shuffles name only their own lanes)
-    for (int64_t ii = (int64_t)blockIdx.x * per_block + (threadIdx.x >> 4); ii < P.n;
-         ii += (int64_t)gridDim.x * per_block) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *s_e = sm + 64 * nd + w * nu;       // this warp's per-unit screening partial sums
+    const int iters = (nu + 31) >> 5;
+    for (int64_t ii = (int64_t)blockIdx.x * 8 + w; ii < P.n; ii += (int64_t)gridDim.x * 8) {
+        const float r = P.rho8[8 * ii + (lane & 7)];
+        const int row_l = P.oleaf[8 * ii + (lane & 7)];
         float rho[8];
-        const float4 r0 = *reinterpret_cast<const float4 *>(P.rho8 + 8 * ii);
-        const float4 r1 = *reinterpret_cast<const float4 *>(P.rho8 + 8 * ii + 4);
-        rho[0] = r0.x; rho[1] = r0.y; rho[2] = r0.z; rho[3] = r0.w;
-        rho[4] = r1.x; rho[5] = r1.y; rho[6] = r1.z; rho[7] = r1.w;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) rho[s] = __shfl_sync(0xffffffffu, r, s);
         const float *E = P.E + ii * nd;
         const float *Sp = P.Sp ? P.Sp + (int64_t)P.oparent[ii] * nd : nullptr;
-        int rows[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) rows[t] = P.oleaf[8 * ii + t];
-        float acc[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) acc[t] = 0.f;
-        for (int d = 4 * q; d < nd; d += 64) {
-            float4 base = *reinterpret_cast<const float4 *>(E + d);
-            if (Sp) {
-                const float4 p = *reinterpret_cast<const float4 *>(Sp + d);
-                base.x += p.x;
-                base.y += p.y;
-                base.z += p.z;
-                base.w += p.w;
-            }
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                if (rows[t] < 0) continue;
-                float4 nv = base;
+        for (int j = 0; j < iters; ++j) {
+            const int u = lane + 32 * j;
+            const bool valid = u < nu;
+            const int t = valid ? u / nq : 0, d = 4 * (u - t * nq);
+            const int row = __shfl_sync(0xffffffffu, row_l, t);
+            if (!valid) continue;
+            float e = 0.f;
+            if (row >= 0) {
+                float4 nv = *reinterpret_cast<const float4 *>(E + d);
+                if (Sp) {
+                    const float4 p = *reinterpret_cast<const float4 *>(Sp + d);
+                    nv.x += p.x;
+                    nv.y += p.y;
+                    nv.z += p.z;
+                    nv.w += p.w;
+                }
                 const float *kt = s_k + t * 8 * nd + d;
 #pragma unroll
                 for (int s = 0; s < 8; ++s) {
@@ -240,22 +239,22 @@ __global__ void __launch_bounds__(256) leaf_list(LeafListArgs P)
                     nv.z = fmaf(rho[s], k4.z, nv.z);
                     nv.w = fmaf(rho[s], k4.w, nv.w);
                 }
-                const int64_t o = (int64_t)rows[t] * nd + d;
+                const int64_t o = (int64_t)row * nd + d;
                 if (P.n_h) *reinterpret_cast<float4 *>(P.n_h + o) = nv;
                 if (P.a_v)
                     *reinterpret_cast<float4 *>(P.a_v + o) =
                         make_float4(nv.x * P.av_per_nh, nv.y * P.av_per_nh, nv.z * P.av_per_nh, nv.w * P.av_per_nh);
-                acc[t] += (exp2f(P.c_exp2 * nv.x) + exp2f(P.c_exp2 * nv.y)) +
-                          (exp2f(P.c_exp2 * nv.z) + exp2f(P.c_exp2 * nv.w));
+                e = (exp2f(P.c_exp2 * nv.x) + exp2f(P.c_exp2 * nv.y)) + (exp2f(P.c_exp2 * nv.z) + exp2f(P.c_exp2 * nv.w));
             }
+            s_e[u] = e;
         }
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            float a = acc[t];
-#pragma unroll
-            for (int w = 8; w > 0; w >>= 1) a += __shfl_xor_sync(hmask, a, w, 16);
-            if (P.shield && q == 0 && rows[t] >= 0) P.shield[rows[t]] = a * P.inv_nd;
+        __syncwarp();
+        if (lane < 8 && P.shield && row_l >= 0) {
+            float a = 0.f;
+            for (int q = 0; q < nq; ++q) a += s_e[lane * nq + q];
+            P.shield[row_l] = a * P.inv_nd;
         }
+        __syncwarp();
     }
 }
 
@@ -698,7 +697,7 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
     }
     // leaves: the 16-lanes-per-oct kernel when 16-byte rows are possible
     const bool vec = nd % 4 == 0 && (uintptr_t)n_h % 16 == 0 && (uintptr_t)a_v % 16 == 0;
-    const size_t smem = sizeof(float) * (vec ? 64 * nd : 64 * nd + 64 * nd);
+    const size_t smem = sizeof(float) * (vec ? 64 * nd + 8 * 2 * nd : 64 * nd + 64 * nd);
     if (smem > 48 * 1024)
         CD_CUDA(cudaFuncSetAttribute(vec ? leaf_list : leaf_list_scalar, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
@@ -721,8 +720,35 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
         B.n_h = n_h;
         B.a_v = a_v;
         B.shield = shield;
+        if (tc) {
+            // BF16: the parent prefix goes into E first, then the tensor-core leaf
+            // kernel takes the level's octs in tiles of 16 (csrc/leaf_tc.cu)
+            float *Ek = t->ws.E + t->oct_begin[k] * nd;
+            if (B.Sp) {
+                cd_status st = launch_add_parent_list(Ek, B.Sp, B.oparent, nd, no, s);
+                if (st != CD_OK) return st;
+                B.Sp = nullptr;
+            }
+            LeafLaunch b = {};
+            b.n_oct = no;
+            b.nd = nd;
+            b.dx_leaf = B.dx_leaf;
+            b.av_per_nh = B.av_per_nh;
+            b.shield_k = (float)opts.shield_k;
+            b.rho_leaf = B.rho8;
+            b.E = Ek;
+            b.Sp = nullptr;
+            b.kloc = g->kloc;
+            b.n_h = n_h;
+            b.a_v = a_v;
+            b.shield = shield;
+            b.oleaf = B.oleaf;
+            cd_status st = launch_leaf_tc(b, s);
+            if (st == CD_OK) continue;
+            if (st != CD_EUNSUPPORTED) return st;
+        }
         LaunchScope ls(CD_K_LEAF, s);
-        if (vec) leaf_list<<<grid_for(no, 16, 152 * 16), 256, smem, s>>>(B);
+        if (vec) leaf_list<<<grid_for(no, 8, 152 * 16), 256, smem, s>>>(B);
         else leaf_list_scalar<<<grid_for(no, 8, 152 * 16), 256, smem, s>>>(B);
         CD_CHECK_LAUNCH();
     }

@@ -467,11 +467,8 @@ cd_status launch_ext_tc(const ExtLaunch &a, const __nv_bfloat16 *const *brick, c
     CD_CHECK_LAUNCH();
     if (a.prefix_in && a.list) {
         // S_k[i] += S_{k-1}[parent index of receiver i]
-        const int64_t n = a.list->n_recv * a.nd;
-        LaunchScope ls(CD_K_SHELL, s);
-        add_parent_list<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
-            a.out, a.prefix_in, a.list->recv_parent, a.nd, n);
-        CD_CHECK_LAUNCH();
+        const cd_status st = launch_add_parent_list(a.out, a.prefix_in, a.list->recv_parent, a.nd, a.list->n_recv, s);
+        if (st != CD_OK) return st;
     } else if (a.prefix_in) {
         // S_k[c] += S_{k-1}[parent c]
         const int64_t n = ((int64_t)1 << (3 * a.k)) * a.nd;
@@ -479,6 +476,41 @@ cd_status launch_ext_tc(const ExtLaunch &a, const __nv_bfloat16 *const *brick, c
         add_parent_rows<<<(unsigned)std::min<int64_t>((n / 4 + 255) / 256, 152 * 16), 256, 0, s>>>(a.out, a.prefix_in, a.nd, n);
         CD_CHECK_LAUNCH();
     }
+    return CD_OK;
+}
+
+// out[i][4j .. 4j+3] += prefix[parent[i]][4j .. 4j+3]: one float4 per thread
+// (nd % 4 == 0, 16-byte aligned rows)
+__global__ void add_parent_list4(float *__restrict__ out, const float *__restrict__ prefix,
+                                 const int32_t *__restrict__ parent, int nq, int64_t n4)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / nq;
+        float4 v = reinterpret_cast<float4 *>(out)[e];
+        const float4 p = reinterpret_cast<const float4 *>(prefix)[(int64_t)parent[i] * nq + (e - i * nq)];
+        v.x += p.x;
+        v.y += p.y;
+        v.z += p.z;
+        v.w += p.w;
+        reinterpret_cast<float4 *>(out)[e] = v;
+    }
+}
+
+cd_status launch_add_parent_list(float *out, const float *prefix, const int32_t *parent, int nd, int64_t rows,
+                                 cudaStream_t s)
+{
+    const int64_t n = rows * nd;
+    if (n == 0) return CD_OK;
+    LaunchScope ls(CD_K_SHELL, s);
+    if (nd % 4 == 0 && ((uintptr_t)out & 15) == 0 && ((uintptr_t)prefix & 15) == 0) {
+        const int64_t n4 = n / 4;
+        add_parent_list4<<<(unsigned)std::min<int64_t>((n4 + 255) / 256, 152 * 32), 256, 0, s>>>(out, prefix, parent,
+                                                                                                 nd / 4, n4);
+    } else {
+        add_parent_list<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(out, prefix, parent,
+                                                                                               nd, n);
+    }
+    CD_CHECK_LAUNCH();
     return CD_OK;
 }
 

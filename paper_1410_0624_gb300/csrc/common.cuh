@@ -233,6 +233,10 @@ struct LeafLaunch {
     const float *Sp;          // [n_oct / 8][nd] or NULL: far shells shared by the 8 octs of a parent
     const float *kloc;        // [8][8][nd]
     float *n_h, *a_v, *shield;
+    // AMR list mode (leaf_tc only): oleaf[8 o + t] is the output row of child t
+    // of oct o (-1: refined); rho_leaf then holds 8 densities per oct (in list
+    // order), E already includes the parent prefix and Sp is NULL
+    const int32_t *oleaf;
 };
 cd_status launch_leaf(const LeafLaunch &a, cudaStream_t s);
 
@@ -249,5 +253,8 @@ bool tc_supported(int nd);
 cd_status build_tc_tables(cd_geom g, cudaStream_t s);
 cd_status launch_ext_tc(const ExtLaunch &a, const __nv_bfloat16 *const *brick, cd_geom g, cudaStream_t s);
 cd_status tc_fault_check();
+// out[i][d] += prefix[parent[i]][d] for n = rows * nd elements
+cd_status launch_add_parent_list(float *out, const float *prefix, const int32_t *parent, int nd, int64_t rows,
+                                 cudaStream_t s);
 
 }  // namespace cd

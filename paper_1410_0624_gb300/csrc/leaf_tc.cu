@@ -44,14 +44,15 @@ struct LeafTcArgs {
     int NP, G;                 // padded directions (MMA N), groups of 128 threads
     int64_t n_leaf, ntiles;
     float c2;                  // -shield_k av_per_nh log2(e)
-    int out_bulk;              // n_h is 16-byte aligned: tile rows leave as one bulk copy
+    int out_bulk;              // n_h is 16-byte aligned: tile rows leave by bulk copies
+    int list;                  // AMR list mode (a.oleaf): tiles of 16 octs, rows scattered
 };
 
 struct LeafTcSmem {
-    size_t bloc, bar, grp, grp_stride, aloc, out, stage, stage_bytes, st_e, st_p, st_r, total;
+    size_t bloc, bar, grp, grp_stride, aloc, out, stage, stage_bytes, st_e, st_p, st_r, st_l, total;
 };
 
-__host__ __device__ inline LeafTcSmem leaf_tc_smem(int nd, int NP, int G)
+__host__ __device__ inline LeafTcSmem leaf_tc_smem(int nd, int NP, int G, bool list)
 {
     LeafTcSmem S;
     size_t o = 0;
@@ -64,7 +65,8 @@ __host__ __device__ inline LeafTcSmem leaf_tc_smem(int nd, int NP, int G)
     S.st_e = 0;
     S.st_p = align128((size_t)16 * nd * 4);
     S.st_r = S.st_p + align128((size_t)2 * nd * 4);
-    S.stage_bytes = align128(S.st_r + 128 * 4);
+    S.st_l = S.st_r + 128 * 4;                     // list mode: the 16 octs' leaf rows
+    S.stage_bytes = align128(S.st_l + (list ? 128 * 4 : 0));
     S.stage = S.out + align128((size_t)128 * nd * 4);
     S.grp_stride = S.stage + 2 * S.stage_bytes;
     S.total = S.grp + (size_t)G * S.grp_stride;
@@ -89,23 +91,37 @@ __device__ __forceinline__ void named_barrier(int id, int threads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
-// a tile's inputs: E rows of its 16 octs, Sp rows of their 2 parents, 128 densities
+// octs in a tile (16, fewer in a list's last tile)
+template <bool kList>
+__device__ __forceinline__ int tile_octs(const LeafTcArgs &P, int64_t tile)
+{
+    if (!kList) return 16;
+    const int64_t left = P.a.n_oct - tile * 16;
+    return left < 16 ? (int)left : 16;
+}
+
+// a tile's inputs: E rows of its 16 octs, Sp rows of their 2 parents, 128
+// densities (list mode: no Sp, plus the octs' 128 leaf rows)
+template <bool kList>
 __device__ __forceinline__ void prefetch(const LeafTcArgs &P, const LeafTcSmem &S, int64_t tile, unsigned char *st,
                                          uint64_t *bar)
 {
     const int nd = P.a.nd;
-    const uint32_t be = 16u * nd * 4, bp = P.a.Sp ? 2u * nd * 4 : 0u, br = 128 * 4;
-    mbar_expect_tx(bar, be + bp + br);
+    const uint32_t nb = (uint32_t)tile_octs<kList>(P, tile);
+    const uint32_t be = nb * nd * 4, bp = P.a.Sp ? 2u * nd * 4 : 0u, br = nb * 32, bl = kList ? nb * 32 : 0u;
+    mbar_expect_tx(bar, be + bp + br + bl);
     bulk_g2s(st + S.st_e, P.a.E + tile * 16 * nd, be, bar);
     if (P.a.Sp) bulk_g2s(st + S.st_p, P.a.Sp + tile * 2 * nd, bp, bar);
     bulk_g2s(st + S.st_r, P.a.rho_leaf + tile * 128, br, bar);
+    if (kList) bulk_g2s(st + S.st_l, P.a.oleaf + tile * 128, bl, bar);
 }
 
+template <bool kList>
 __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int nd = P.a.nd, NP = P.NP, G = P.G;
-    const LeafTcSmem S = leaf_tc_smem(nd, NP, G);
+    const LeafTcSmem S = leaf_tc_smem(nd, NP, G, kList);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int g = warp >> 2, quarter = warp & 3, i = tid & 127;   // group, TMEM lane quarter, row
     // [0 .. G) group MMAs, [G + 2 g + stage] input stages
@@ -147,7 +163,7 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
     bool pending[2] = {false, false};
     bool fault = false;
     if (i == 0 && first < P.ntiles) {
-        prefetch(P, S, first, Gb + S.stage, &bar[G + 2 * g]);
+        prefetch<kList>(P, S, first, Gb + S.stage, &bar[G + 2 * g]);
         pending[0] = true;
     }
 
@@ -156,7 +172,7 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
         unsigned char *st = Gb + S.stage + stg * S.stage_bytes;
         if (i == 0) {
             if (tile + stride < P.ntiles) {
-                prefetch(P, S, tile + stride, Gb + S.stage + (stg ^ 1) * S.stage_bytes, &bar[G + 2 * g + (stg ^ 1)]);
+                prefetch<kList>(P, S, tile + stride, Gb + S.stage + (stg ^ 1) * S.stage_bytes, &bar[G + 2 * g + (stg ^ 1)]);
                 pending[stg ^ 1] = true;
             }
             if (mbar_wait_bounded(&bar[G + 2 * g + stg], sphase[stg], kMaxPolls)) pending[stg] = false;
@@ -189,8 +205,9 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
             umma_commit(&bar[g]);
             if (!mbar_wait_bounded(&bar[g], phase, kMaxPolls)) sflag[g] = 1;
             // the previous tile's rows must have left the output buffer
-            if (P.out_bulk) bulk_wait_read<0>();
+            if (P.out_bulk && !kList) bulk_wait_read<0>();
         }
+        if (kList && P.out_bulk && i < 16) bulk_wait_read<0>();   // each oct's copies were issued by thread i
         phase ^= 1;
         named_barrier(bid, 128);
         if (sflag[g]) {
@@ -199,13 +216,16 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
         }
         tc_fence_after();
         // ---- N_H = loc + E[oct] + Sp[parent]; screening factor ----
+        const int32_t *sL = reinterpret_cast<const int32_t *>(st + S.st_l);
+        const int nb = tile_octs<kList>(P, tile);
         {
-            const int64_t m = tile * 128 + i;
+            // output row of this leaf: Morton position, or the list's row (-1: none)
+            const int64_t m = kList ? ((i >> 3) < nb ? (int64_t)sL[i] : -1) : tile * 128 + i;
             const float *Ei = reinterpret_cast<const float *>(st + S.st_e) + (i >> 3) * nd;
             const float *Pi = P.a.Sp ? reinterpret_cast<const float *>(st + S.st_p) + (i >> 6) * nd : nullptr;
             float *orow = sO + (size_t)i * nd;
-            float *av = P.a.a_v ? P.a.a_v + m * nd : nullptr;
-            float *nh = P.a.n_h && !P.out_bulk ? P.a.n_h + m * nd : nullptr;
+            float *av = P.a.a_v && (!kList || m >= 0) ? P.a.a_v + m * nd : nullptr;
+            float *nh = P.a.n_h && !P.out_bulk && (!kList || m >= 0) ? P.a.n_h + m * nd : nullptr;
             float acc = 0.f;
 #pragma unroll 1
             for (int c = 0; c < nd; c += 32) {
@@ -242,13 +262,29 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
                     }
                 }
             }
-            if (P.a.shield) P.a.shield[m] = acc / (float)nd;
+            if (P.a.shield && (!kList || m >= 0)) P.a.shield[m] = acc / (float)nd;
         }
         fence_proxy_async_smem();
         tc_fence_before();
         named_barrier(bid, 128);
-        if (P.out_bulk && i == 0) {
+        if (P.out_bulk && !kList && i == 0) {
             bulk_s2g(P.a.n_h + tile * 128 * nd, sO, (uint32_t)(128 * nd * 4));
+            bulk_commit();
+        }
+        if (kList && P.out_bulk && i < nb) {
+            // oct i's children: one copy when their rows are consecutive, else one per leaf row
+            const int r0 = sL[8 * i];
+            bool run = r0 >= 0;
+#pragma unroll
+            for (int t = 1; t < 8; ++t) run = run && sL[8 * i + t] == r0 + t;
+            if (run) {
+                bulk_s2g(P.a.n_h + (int64_t)r0 * nd, sO + (size_t)8 * i * nd, (uint32_t)(8 * nd * 4));
+            } else {
+                for (int t = 0; t < 8; ++t) {
+                    const int r = sL[8 * i + t];
+                    if (r >= 0) bulk_s2g(P.a.n_h + (int64_t)r * nd, sO + (size_t)(8 * i + t) * nd, (uint32_t)(nd * 4));
+                }
+            }
             bulk_commit();
         }
     }
@@ -256,11 +292,10 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
         atomicExch(&g_leaftc_fault, 1);
         mbar_wait_bounded(&bar[g], phase ^ 1, kMaxPolls);   // let an issued product finish
     }
-    if (i == 0) {
+    if (i == 0)
         for (int b = 0; b < 2; ++b)
             if (pending[b]) mbar_wait_bounded(&bar[G + 2 * g + b], sphase[b], kMaxPolls);
-        bulk_wait_all<0>();
-    }
+    if (i == 0 || (kList && i < 16)) bulk_wait_all<0>();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -287,27 +322,32 @@ cd_status launch_leaf_tc(const LeafLaunch &a, cudaStream_t s)
 {
     const int nd = a.nd;
     const int64_t n_leaf = a.n_oct * 8;
-    if (nd % 4 != 0 || nd > 64 || n_leaf < 128 || n_leaf % 128 != 0 || !aligned16(a.E) || !aligned16(a.Sp) ||
-        !aligned16(a.rho_leaf) || !a.E)
+    const bool list = a.oleaf != nullptr;
+    if (nd % 4 != 0 || nd > 64 || !aligned16(a.E) || !aligned16(a.Sp) || !aligned16(a.rho_leaf) || !a.E)
         return CD_EUNSUPPORTED;
+    if (!list && (n_leaf < 128 || n_leaf % 128 != 0)) return CD_EUNSUPPORTED;
+    if (list && (a.Sp || !aligned16(a.oleaf) || (a.n_h && !aligned16(a.n_h)))) return CD_EUNSUPPORTED;
+    if (n_leaf == 0) return CD_OK;
     LeafTcArgs P;
     P.a = a;
+    P.list = list;
     P.NP = round16(nd);
     P.n_leaf = n_leaf;
-    P.ntiles = n_leaf / 128;
+    P.ntiles = (a.n_oct + 15) / 16;
     P.c2 = (float)(-(double)a.shield_k * (double)a.av_per_nh * 1.4426950408889634);
     P.out_bulk = a.n_h && aligned16(a.n_h);
     int dev = 0, smax = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     P.G = 4;
-    while (P.G > 1 && (int)leaf_tc_smem(nd, P.NP, P.G).total > smax) --P.G;
-    const size_t smem = leaf_tc_smem(nd, P.NP, P.G).total;
+    while (P.G > 1 && (int)leaf_tc_smem(nd, P.NP, P.G, list).total > smax) --P.G;
+    const size_t smem = leaf_tc_smem(nd, P.NP, P.G, list).total;
     if ((int)smem > smax) return CD_EUNSUPPORTED;
-    CD_CUDA(cudaFuncSetAttribute(leaf_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const auto kern = list ? leaf_tc<true> : leaf_tc<false>;
+    CD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t grid = std::min<int64_t>((P.ntiles + P.G - 1) / P.G, sms());
     LaunchScope ls(CD_K_LEAF, s);
-    leaf_tc<<<(unsigned)grid, 128 * P.G, smem, s>>>(P);
+    kern<<<(unsigned)grid, 128 * P.G, smem, s>>>(P);
     CD_CHECK_LAUNCH();
     return CD_OK;
 }
