@@ -60,15 +60,33 @@ __global__ void mark_refined(const uint64_t *__restrict__ keys, int64_t n, int l
     }
 }
 
-// The leaves of level l write their value into their cell.
-__global__ void scatter_leaves(const float *__restrict__ rho, const int8_t *__restrict__ lvl,
-                               const uint64_t *__restrict__ key, int64_t n, int l, float *__restrict__ dense)
+// The leaves of level l, from the leaf-bearing octs of level l - 1: entry e is
+// child e % 8 of oct e / 8 (row -1: refined, left as it is).
+__global__ void scatter_octs(const float *__restrict__ rho, const uint64_t *__restrict__ okey,
+                             const int32_t *__restrict__ oleaf, int64_t n, int l, float *__restrict__ dense)
 {
     const int64_t side = (int64_t)1 << l;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (lvl[i] != l) continue;
-        const uint64_t m = key[i];
-        dense[((int64_t)compact3(m >> 2) * side + compact3(m >> 1)) * side + compact3(m)] = rho[i];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 8 * n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = oleaf[e];
+        if (r < 0) continue;
+        const uint64_t m = (okey[e >> 3] << 3) | (uint64_t)(e & 7);
+        dense[((int64_t)compact3(m >> 2) * side + compact3(m >> 1)) * side + compact3(m)] = rho[r];
+    }
+}
+
+// Four cells of a row per thread (side >= 4): the parents of x .. x+3 are
+// x/2 and x/2 + 1, so one float4 store takes (a, a, b, b).
+__global__ void prolong4(const float *__restrict__ coarse, int l, float *__restrict__ fine)
+{
+    const int64_t side = (int64_t)1 << l, n4 = side * side * side / 4;
+    const int sh = l;
+    const int64_t hs = side >> 1;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = 4 * q;
+        const int64_t x = c & (side - 1), y = (c >> sh) & (side - 1), z = c >> (2 * sh);
+        const float *row = coarse + ((z >> 1) * hs + (y >> 1)) * hs + (x >> 1);
+        const float a = row[0], b = row[1];
+        reinterpret_cast<float4 *>(fine)[q] = make_float4(a, a, b, b);
     }
 }
 
@@ -552,15 +570,23 @@ cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s)
                 LaunchScope ls(CD_K_RESTRICT, s);
                 mark_refined<<<grid_for(t->n_ref[l], 256), 256, 0, s>>>(t->ref_key[l], t->n_ref[l], l, t->rho_lvl[l]);
             }
+        } else if (l >= 2) {
+            LaunchScope ls(CD_K_RESTRICT, s);
+            prolong4<<<grid_for((int64_t)1 << (3 * l - 2), 256, 152 * 64), 256, 0, s>>>(t->rho_lvl[l - 1], l,
+                                                                                       t->rho_lvl[l]);
         } else {
             LaunchScope ls(CD_K_RESTRICT, s);
             prolong<<<grid_for((int64_t)1 << (3 * l), 256, 152 * 64), 256, 0, s>>>(t->rho_lvl[l - 1], l, t->rho_lvl[l]);
         }
         CD_CHECK_LAUNCH();
-        LaunchScope ls(CD_K_RESTRICT, s);
-        scatter_leaves<<<grid_for(t->n_leaf, 256), 256, 0, s>>>(t->rho_leaf, t->leaf_lvl, t->leaf_key, t->n_leaf, l,
-                                                                 t->rho_lvl[l]);
-        CD_CHECK_LAUNCH();
+        const int64_t no = t->oct_begin[l] - t->oct_begin[l - 1];   // octs of level l - 1: their leaf children
+        if (no > 0) {
+            LaunchScope ls(CD_K_RESTRICT, s);
+            scatter_octs<<<grid_for(8 * no, 256), 256, 0, s>>>(t->rho_leaf, t->oct_key + t->oct_begin[l - 1],
+                                                               t->oct_leaf + 8 * t->oct_begin[l - 1], no, l,
+                                                               t->rho_lvl[l]);
+            CD_CHECK_LAUNCH();
+        }
     }
     const int64_t nfin = t->oct_begin[lf + 1] - t->oct_begin[lf];
     if (nfin > 0) {
