@@ -118,6 +118,47 @@ __global__ void mean_finest(const float *__restrict__ rho, const uint64_t *__res
     }
 }
 
+// Refined cells of level l take the mean of their 8 children at level l + 1
+// (octant order, then x 1/8, as the restriction): the children are leaves or
+// refined cells, all written before.
+__global__ void fill_refined(const uint64_t *__restrict__ keys, int64_t n, int l, const float *__restrict__ child,
+                             float *__restrict__ dense)
+{
+    const int64_t side = (int64_t)1 << l, cs = side * 2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t m = keys[i];
+        const int64_t x = compact3(m), y = compact3(m >> 1), z = compact3(m >> 2);
+        float sum = 0.f;
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+            sum += child[((2 * z + ((o >> 2) & 1)) * cs + 2 * y + ((o >> 1) & 1)) * cs + 2 * x + (o & 1)];
+        dense[(z * side + y) * side + x] = sum * 0.125f;
+    }
+}
+
+// The read part of the sparse finest level lf: for each listed cell of level
+// lf - 1, paint its 8 children with its value unless it is refined (then they
+// hold leaves and means already), and write their BF16 brick.
+__global__ void fill_deep(const uint64_t *__restrict__ keys, const int8_t *__restrict__ paint, int64_t n, int lf,
+                          const float *__restrict__ parent, float *__restrict__ fine, __nv_bfloat16 *__restrict__ brick)
+{
+    const int64_t ps = (int64_t)1 << (lf - 1), fs = ps * 2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t m = keys[i];
+        const int64_t x = compact3(m), y = compact3(m >> 1), z = compact3(m >> 2);
+        const int64_t p = (z * ps + y) * ps + x;
+        const float v = parent[p];
+        __align__(16) __nv_bfloat16 bv[8];
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            float *c = fine + ((2 * z + ((o >> 2) & 1)) * fs + 2 * y + ((o >> 1) & 1)) * fs + 2 * x + (o & 1);
+            if (paint[i]) *c = v;
+            bv[o] = __float2bfloat16_rn(*c);
+        }
+        *reinterpret_cast<uint4 *>(brick + 8 * p) = *reinterpret_cast<const uint4 *>(bv);
+    }
+}
+
 // Sibling densities of every oct: child o at level k+1 from the dense array,
 // or from the leaves when k+1 is the finest level.
 __global__ void gather_rho8(const uint64_t *__restrict__ okey, const int32_t *__restrict__ oleaf, int64_t n, int k,
@@ -531,6 +572,33 @@ cd_status build_amr(cd_tree t, int base, int lmax, int64_t n, const int8_t *leve
         if (!up((void **)&t->rho_lvl[l], nullptr, cells * 4)) return st;
         if (l >= 1 && !up((void **)&t->rho_brick[l], nullptr, cells * 2)) return st;
     }
+    // the read part of the finest dense level (see cd_tree_s): level-(lf-1) cells
+    // around the parents of the octs of level lf
+    if (lmax - 1 > base && lmax - 1 >= 1 && !oct[lmax - 1].empty()) {
+        const int lf = lmax - 1;
+        const int64_t ps = (int64_t)1 << (lf - 1);
+        std::vector<uint64_t> deep;
+        for (uint64_t o : oct[lf]) {
+            const uint64_t a = o >> 3;
+            const int64_t ax = compact3(a), ay = compact3(a >> 1), az = compact3(a >> 2);
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int64_t x = ax + dx, y = ay + dy, z = az + dz;
+                        if (x < 0 || y < 0 || z < 0 || x >= ps || y >= ps || z >= ps) continue;
+                        deep.push_back(morton3((uint32_t)x, (uint32_t)y, (uint32_t)z));
+                    }
+        }
+        std::sort(deep.begin(), deep.end());
+        deep.erase(std::unique(deep.begin(), deep.end()), deep.end());
+        std::vector<int8_t> paint(deep.size());
+        for (size_t j = 0; j < deep.size(); ++j)
+            paint[j] = std::binary_search(ref[lf - 1].begin(), ref[lf - 1].end(), deep[j]) ? 0 : 1;
+        t->n_deep = (int64_t)deep.size();
+        if (!up((void **)&t->deep_key, deep.data(), deep.size() * 8)) return st;
+        if (!up((void **)&t->deep_paint, paint.data(), paint.size())) return st;
+        t->sparse_finest = 1;
+    }
     // tensor-core lists of the levels the BF16 contraction serves (receiving level >= 4)
     for (int k = 4; k <= lmax - 1; ++k) {
         if (k <= lmax - 2 && (st = build_tc_list(ref[k], t->ref_parent[k], t->tc_ref[k])) != CD_OK) return st;
@@ -570,6 +638,8 @@ cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s)
                 LaunchScope ls(CD_K_RESTRICT, s);
                 mark_refined<<<grid_for(t->n_ref[l], 256), 256, 0, s>>>(t->ref_key[l], t->n_ref[l], l, t->rho_lvl[l]);
             }
+        } else if (t->sparse_finest && l == lf) {
+            // no prolongation into the finest dense level: fill_deep paints the part that is read
         } else if (l >= 2) {
             LaunchScope ls(CD_K_RESTRICT, s);
             prolong4<<<grid_for((int64_t)1 << (3 * l - 2), 256, 152 * 64), 256, 0, s>>>(t->rho_lvl[l - 1], l,
@@ -595,8 +665,24 @@ cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s)
                                                         t->oct_leaf + 8 * t->oct_begin[lf], nfin, lf, t->rho_lvl[lf]);
     }
     CD_CHECK_LAUNCH();
-    cd_status st = restrict_dense(t, lf, s);
-    if (st != CD_OK) return st;
+    cd_status st = CD_OK;
+    if (t->sparse_finest) {
+        if (t->n_ref[lf - 1]) {
+            LaunchScope ls(CD_K_RESTRICT, s);
+            fill_refined<<<grid_for(t->n_ref[lf - 1], 256), 256, 0, s>>>(t->ref_key[lf - 1], t->n_ref[lf - 1], lf - 1,
+                                                                         t->rho_lvl[lf], t->rho_lvl[lf - 1]);
+            CD_CHECK_LAUNCH();
+        }
+        if ((st = restrict_dense(t, lf - 1, s)) != CD_OK) return st;
+        if (t->n_deep) {
+            LaunchScope ls(CD_K_RESTRICT, s);
+            fill_deep<<<grid_for(t->n_deep, 256), 256, 0, s>>>(t->deep_key, t->deep_paint, t->n_deep, lf,
+                                                               t->rho_lvl[lf - 1], t->rho_lvl[lf], t->rho_brick[lf]);
+            CD_CHECK_LAUNCH();
+        }
+    } else if ((st = restrict_dense(t, lf, s)) != CD_OK) {
+        return st;
+    }
     for (int k = 0; k < lmax; ++k) {
         const int64_t no = t->oct_begin[k + 1] - t->oct_begin[k];
         if (!no) continue;

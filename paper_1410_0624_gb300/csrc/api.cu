@@ -484,7 +484,8 @@ void cd_tree_free(cd_tree t)
         if (t->ref_key[l]) cudaFree(t->ref_key[l]);
         if (t->ref_parent[l]) cudaFree(t->ref_parent[l]);
     }
-    for (void *p : {(void *)t->oct_key, (void *)t->oct_parent, (void *)t->oct_leaf, (void *)t->oct_rho8,
+    for (void *p : {(void *)t->deep_key, (void *)t->deep_paint, (void *)t->oct_key, (void *)t->oct_parent,
+                    (void *)t->oct_leaf, (void *)t->oct_rho8,
                     (void *)t->leaf_key, (void *)t->leaf_lvl, (void *)t->leaf_src})
         if (p) cudaFree(p);
     delete[] t->leaf_level_h;

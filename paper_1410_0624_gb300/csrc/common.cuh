@@ -135,6 +135,13 @@ struct cd_tree_s {
     cd::TcList tc_ref[CD_MAXL + 1];       // tensor-core lists: refined cells of level k (far-shell prefixes)
     cd::TcList tc_oct[CD_MAXL + 1];       // tensor-core lists: leaf-bearing octs of level k
     float *oct_rho8 = nullptr;            // (device) [n_oct][8] volume-mean density of child o
+    // The finest dense level lf = L-1 is filled only where it is read (when lf >
+    // base): leaves and refined cells of lf, and the children of the level-(lf-1)
+    // cells around the parents of the octs of level lf (their shells' stencils)
+    int sparse_finest = 0;
+    int64_t n_deep = 0;
+    uint64_t *deep_key = nullptr;         // (device) those level-(lf-1) cells, sorted Morton keys
+    int8_t *deep_paint = nullptr;         // (device) 1: not refined, its children take its value
     uint64_t *leaf_key = nullptr;         // (device) output order: Morton key at the leaf's level
     int8_t *leaf_lvl = nullptr;           // (device) output order: level
     int64_t *leaf_src = nullptr;          // (device) output order: index in the caller's leaf arrays
