@@ -744,7 +744,9 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
             e.dx[3] = dx(k - 2);
             e.prefix_in = (k - 1 >= 3) ? t->ws.S[k - 1] : nullptr;
             e.out = t->ws.S[k];
-            e.list = &t->tc_ref[k];
+            // a fully refined level (below the base level) keeps every cell in Morton
+            // order, so it takes the whole-level tiles of a uniform tree
+            e.list = t->n_ref[k] == ((int64_t)1 << (3 * k)) ? nullptr : &t->tc_ref[k];
             cd_status st = launch_ext_tc(e, t->rho_brick, g, s);
             if (st != CD_OK) return st;
             continue;

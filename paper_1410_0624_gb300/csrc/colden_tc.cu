@@ -279,13 +279,29 @@ __global__ void __launch_bounds__(kThreads, 2) shell_sum_tc(TcArgs P)
 #pragma unroll 4
                     for (int r = 0; r < nrows; ++r, o += rstride) *o = P.dx_k * T[r * 33 + lane];
                 } else if (P.tiles) {
-                    // row r's output row for this lane's child, broadcast from lane r
+                    // row r's output row for this lane's child, broadcast from lane r; when
+                    // the chunk's 32 columns span at most two children j0 and j0 + 1, two
+                    // shuffles a row select it
                     const int j = col < P.Nt ? col / P.nd : 0, d = col - j * P.nd;
-                    for (int r = 0; r < nrows; ++r) {
-                        const int o0 = __shfl_sync(0xffffffffu, my_out[0], r), o1 = __shfl_sync(0xffffffffu, my_out[1], r),
-                                  o2 = __shfl_sync(0xffffffffu, my_out[2], r), o3 = __shfl_sync(0xffffffffu, my_out[3], r);
-                        const int dst = j == 0 ? o0 : j == 1 ? o1 : j == 2 ? o2 : o3;
-                        if (col < P.Nt && dst >= 0) P.out[(int64_t)dst * P.nd + d] = P.dx_k * T[r * 33 + lane];
+                    const int j0 = c / P.nd, jl = (c + 31 < P.Nt ? c + 31 : P.Nt - 1) / P.nd;
+                    const int j1 = j0 + 1 < 4 ? j0 + 1 : 3;
+                    const int s0 = j0 == 0 ? my_out[0] : j0 == 1 ? my_out[1] : j0 == 2 ? my_out[2] : my_out[3];
+                    const int s1 = j1 == 1 ? my_out[1] : j1 == 2 ? my_out[2] : my_out[3];
+                    if (jl - j0 <= 1) {
+                        for (int r = 0; r < nrows; ++r) {
+                            const int a0 = __shfl_sync(0xffffffffu, s0, r), a1 = __shfl_sync(0xffffffffu, s1, r);
+                            const int dst = j == j0 ? a0 : a1;
+                            if (col < P.Nt && dst >= 0) P.out[(int64_t)dst * P.nd + d] = P.dx_k * T[r * 33 + lane];
+                        }
+                    } else {
+                        for (int r = 0; r < nrows; ++r) {
+                            const int o0 = __shfl_sync(0xffffffffu, my_out[0], r),
+                                      o1 = __shfl_sync(0xffffffffu, my_out[1], r),
+                                      o2 = __shfl_sync(0xffffffffu, my_out[2], r),
+                                      o3 = __shfl_sync(0xffffffffu, my_out[3], r);
+                            const int dst = j == 0 ? o0 : j == 1 ? o1 : j == 2 ? o2 : o3;
+                            if (col < P.Nt && dst >= 0) P.out[(int64_t)dst * P.nd + d] = P.dx_k * T[r * 33 + lane];
+                        }
                     }
                 }
                 __syncwarp();
