@@ -492,7 +492,7 @@ struct CellArgs {
     int vec;                         // n_h is 16-byte aligned: a tile's rows leave as one bulk copy
 };
 
-constexpr int kCellThreads = 256;   // two groups of 128
+constexpr int kCellThreads = 512;   // two groups of 256: two threads per leaf row, each half the columns
 
 // Shared memory of learned_cell_tc.  Shared: the weight images, the one-hot
 // block, the local-term operand B_loc [NP x 64] = dx K_loc[t][s][d] at
@@ -555,7 +555,9 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
     const CellSmem S = cell_smem(T);
     const int nd = T.nd, KC = T.KC, NP = T.NP;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int g = warp >> 2, quarter = warp & 3, i = tid & 127;   // group, TMEM lane quarter, row
+    // group g (warps 8g .. 8g+7); row i (TMEM lane quarter warp % 4); half of the columns
+    const int g = warp >> 3, quarter = warp & 3, half = (warp >> 2) & 1, i = quarter * 32 + (tid & 31);
+    const bool lead = half == 0 && i == 0;     // issues the group's copies and MMAs
     const float *sMu = reinterpret_cast<const float *>(smem + S.muc);
     const float *sSi = reinterpret_cast<const float *>(smem + S.sic);
     // [0] weights, [1 + g] group MMAs, [3 + 2 g + stage] group input stages
@@ -565,6 +567,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
     unsigned char *G = smem + S.grp + g * S.grp_stride;
     unsigned char *sOp = G + S.a;
     unsigned char *sAloc = G + S.aloc;
+    __shared__ float sAcc[2 * 2 * 128];         // [group][half][row] screening partial sums
 
     if (tid == 0) {
         for (int b = 0; b < 7; ++b) mbar_init(&bar[b], 1);
@@ -615,7 +618,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
     uint32_t phase = 0, sphase[2] = {0, 0};
     bool pending[2] = {false, false};          // leader: a prefetch into the stage has not been waited for
     bool fault = false;
-    if (i == 0 && first < A.ntiles) {
+    if (lead && first < A.ntiles) {
         prefetch_tile(A, S, first, G + S.stage, &bar[3 + 2 * g]);
         pending[0] = true;
     }
@@ -624,7 +627,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
     // leader of the group: issue, commit and wait (bounded); everyone learns
     // the outcome after the group barrier.  layer 0 = the local term.
     auto issue_and_wait = [&](int layer, uint32_t h_block) {
-        if (i == 0) {
+        if (lead) {
             // the previous tile's N rows must have left the operand buffer
             // before anyone writes it again (right after the local term)
             if (layer == 0 && bulk_out) bulk_wait_read<0>();
@@ -649,7 +652,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
             if (!ok) sflag[g] = 1;
         }
         phase ^= 1;
-        named_barrier(bid, 128);
+        named_barrier(bid, 256);
         fault = sflag[g] != 0;
         tc_fence_after();
     };
@@ -658,25 +661,23 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
     // loads in flight per wait
     auto gelu_row = [&]() {
 #pragma unroll 1
-        for (int c = 0; c < kH; c += 64) {
-            uint32_t v[2][32];
-            tmem_ld32(tD + lane_off + (uint32_t)c, v[0]);
-            tmem_ld32(tD + lane_off + (uint32_t)(c + 32), v[1]);
+        for (int c = 64 * half; c < 64 * half + 64; c += 32) {
+            uint32_t v[32];
+            tmem_ld32(tD + lane_off + (uint32_t)c, v);
             tmem_ld_wait();
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh)
+            for (int q = 0; q < 4; ++q) {
+                uint32_t o[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    uint32_t o[4];
-#pragma unroll
-                    for (int p2 = 0; p2 < 4; ++p2)
-                        o[p2] = gelu_bf16x2(pack_bf16x2(__uint_as_float(v[hh][8 * q + 2 * p2]),
-                                                        __uint_as_float(v[hh][8 * q + 2 * p2 + 1])));
-                    *reinterpret_cast<uint4 *>(sOp + op_off(i, c + 32 * hh + 8 * q, kH)) =
-                        make_uint4(o[0], o[1], o[2], o[3]);
-                }
+                for (int p2 = 0; p2 < 4; ++p2)
+                    o[p2] = gelu_bf16x2(pack_bf16x2(__uint_as_float(v[8 * q + 2 * p2]),
+                                                    __uint_as_float(v[8 * q + 2 * p2 + 1])));
+                *reinterpret_cast<uint4 *>(sOp + op_off(i, c + 8 * q, kH)) = make_uint4(o[0], o[1], o[2], o[3]);
+            }
         }
     };
+    // the row's 8-direction groups this thread takes: [gq0, gq1) of nd / 8
+    const int ngq = nd >> 3, gq0 = half * ((ngq + 1) >> 1), gq1 = half ? ngq : (ngq + 1) >> 1;
 
     int stg = 0;
     for (int64_t tile = first; tile < A.ntiles && !fault; tile += stride, stg ^= 1) {
@@ -688,7 +689,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         // the next tile's inputs go to the other stage (its last reader was the
         // previous tile, finished at that tile's final barrier); the previous
         // tile's N rows must have left the operand buffer
-        if (i == 0) {
+        if (lead) {
             if (tile + stride < A.ntiles) {
                 prefetch_tile(A, S, tile + stride, G + S.stage + (stg ^ 1) * S.stage_bytes,
                               &bar[3 + 2 * g + (stg ^ 1)]);
@@ -698,7 +699,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
             else sflag[g] = 1;
         }
         sphase[stg] ^= 1;
-        named_barrier(bid, 128);
+        named_barrier(bid, 256);
         if (sflag[g]) {
             fault = true;
             break;
@@ -707,7 +708,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         const float *sE = reinterpret_cast<const float *>(st + S.st_ext) + (i >> 3) * nd;
 
         // ---- local term on the tensor cores: A_loc row = the oct's 8 densities ----
-        {
+        if (half == 0) {
             const float4 r0 = *reinterpret_cast<const float4 *>(sR + (i & ~7));
             const float4 r1 = *reinterpret_cast<const float4 *>(sR + (i & ~7) + 4);
             const uint4 w = valid ? make_uint4(pack_bf16x2(r0.x, r0.y), pack_bf16x2(r0.z, r0.w),
@@ -717,41 +718,36 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         }
         fence_proxy_async_smem();
         tc_fence_before();
-        named_barrier(bid, 128);
+        named_barrier(bid, 256);
         issue_and_wait(0, 0);
         if (fault) break;
 
         // ---- u_cell = standardised ln(local term) (8 directions per 16-byte
         //      store), then ln n and the K padding ----
 #pragma unroll 1
-        for (int c = 0; c < nd; c += 32) {
-            uint32_t v[32];
-            tmem_ld32(tL + lane_off + (uint32_t)c, v);
+        for (int q = gq0; q < gq1; ++q) {
+            const int d0 = 8 * q;
+            uint32_t v[8];
+            tmem_ld8(tL + lane_off + (uint32_t)d0, v);
             tmem_ld_wait();
+            const float4 a0 = *reinterpret_cast<const float4 *>(sMu + d0), a1 = *reinterpret_cast<const float4 *>(sMu + d0 + 4);
+            const float4 b0 = *reinterpret_cast<const float4 *>(sSi + d0), b1 = *reinterpret_cast<const float4 *>(sSi + d0 + 4);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            float u[8];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int d0 = c + 8 * q;
-                if (d0 >= nd) break;       // nd is a multiple of 8
-                const float4 a0 = *reinterpret_cast<const float4 *>(sMu + d0), a1 = *reinterpret_cast<const float4 *>(sMu + d0 + 4);
-                const float4 b0 = *reinterpret_cast<const float4 *>(sSi + d0), b1 = *reinterpret_cast<const float4 *>(sSi + d0 + 4);
-                const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-                float u[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    u[j] = valid ? std_input(__uint_as_float(v[8 * q + j]), kCFloor, a[j], b[j]) : 0.f;
-                *reinterpret_cast<uint4 *>(sOp + op_off(i, d0, KC)) =
-                    make_uint4(pack_bf16x2(u[0], u[1]), pack_bf16x2(u[2], u[3]), pack_bf16x2(u[4], u[5]),
-                               pack_bf16x2(u[6], u[7]));
-            }
+            for (int j = 0; j < 8; ++j) u[j] = valid ? std_input(__uint_as_float(v[j]), kCFloor, a[j], b[j]) : 0.f;
+            *reinterpret_cast<uint4 *>(sOp + op_off(i, d0, KC)) =
+                make_uint4(pack_bf16x2(u[0], u[1]), pack_bf16x2(u[2], u[3]), pack_bf16x2(u[4], u[5]),
+                           pack_bf16x2(u[6], u[7]));
         }
-        for (int d0 = nd; d0 < KC; d0 += 8) {      // ln n at column nd, zeros after it
+        for (int d0 = nd + 8 * half; d0 < KC; d0 += 16) {      // ln n at column nd, zeros after it
             const float un = valid && d0 == nd ? std_input(sR[i], kNFloor, sMu[nd], sSi[nd]) : 0.f;
             *reinterpret_cast<uint4 *>(sOp + op_off(i, d0, KC)) = make_uint4(pack_bf16x2(un, 0.f), 0, 0, 0);
         }
         fence_proxy_async_smem();
         tc_fence_before();
-        named_barrier(bid, 128);
+        named_barrier(bid, 256);
         issue_and_wait(1, smem_u32(st + S.st_h));
         if (fault) break;
 
@@ -759,7 +755,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         gelu_row();
         fence_proxy_async_smem();
         tc_fence_before();
-        named_barrier(bid, 128);
+        named_barrier(bid, 256);
         issue_and_wait(2, 0);
         if (fault) break;
 
@@ -767,7 +763,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
         gelu_row();
         fence_proxy_async_smem();
         tc_fence_before();
-        named_barrier(bid, 128);
+        named_barrier(bid, 256);
         issue_and_wait(3, 0);
         if (fault) break;
 
@@ -778,14 +774,14 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
             float *nh = A.n_h && valid && !bulk_out ? A.n_h + m * nd : nullptr;
             float acc = 0.f;
 #pragma unroll 1
-            for (int c = 0; c < NP; c += 32) {
-                uint32_t v[32], w[32];
-                tmem_ld32(tD + lane_off + (uint32_t)c, v);
-                tmem_ld32(tL + lane_off + (uint32_t)c, w);
+            for (int q8 = gq0; q8 < gq1; ++q8) {
+                const int c = 8 * q8;
+                uint32_t v[8], w[8];
+                tmem_ld8(tD + lane_off + (uint32_t)c, v);
+                tmem_ld8(tL + lane_off + (uint32_t)c, w);
                 tmem_ld_wait();
 #pragma unroll
-                for (int j4 = 0; j4 < 32; j4 += 4) {
-                    if (c + j4 >= nd) break;       // nd is a multiple of 8
+                for (int j4 = 0; j4 < 8; j4 += 4) {
                     const float4 e4 = *reinterpret_cast<const float4 *>(sE + c + j4);
                     const float ev[4] = {e4.x, e4.y, e4.z, e4.w};
                     float N[4];
@@ -805,23 +801,25 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
                         for (int q = 0; q < 4; ++q) av[c + j4 + q] = N[q] * A.av_per_nh;
                 }
             }
-            if (A.shield && valid) A.shield[m] = acc / (float)nd;
+            sAcc[(g * 2 + half) * 128 + i] = acc;
         }
         fence_proxy_async_smem();
         tc_fence_before();
-        named_barrier(bid, 128);     // the stage is rewritten by later tiles
-        if (bulk_out && i == 0) {
+        named_barrier(bid, 256);     // the stage is rewritten by later tiles
+        // the row's screening factor: the two halves' sums, in a fixed order
+        if (half == 0 && A.shield && valid) A.shield[m] = (sAcc[(g * 2) * 128 + i] + sAcc[(g * 2 + 1) * 128 + i]) / (float)nd;
+        if (bulk_out && lead) {
             bulk_s2g(A.n_h + c0 * nd, sOp, (uint32_t)(rows * nd * 4));
             bulk_commit();
         }
     }
-    if (fault && i == 0) {
+    if (fault && lead) {
         atomicExch(&g_ltc_fault, 1);
         mbar_wait_bounded(&bar[1 + g], phase ^ 1, kMaxPolls);   // let an issued chain finish
     }
     // a prefetch still in flight must land, and the output copies must have
     // read the operand buffer, before the CTA exits
-    if (i == 0) {
+    if (lead) {
         for (int b = 0; b < 2; ++b)
             if (pending[b]) mbar_wait_bounded(&bar[3 + 2 * g + b], sphase[b], kMaxPolls);
         bulk_wait_all<0>();
