@@ -251,8 +251,8 @@ struct OctArgs {
     float *ext;            // [n_oct][nd]
 };
 
-constexpr int kOctThreads = 256;
-constexpr int kOctUnits = 128 * kMaxNd / 8 / kOctThreads;   // (row, 8 directions) units per thread: 3
+constexpr int kOctThreads = 384;                              // 12 warps
+constexpr int kOctUnits = 128 * kMaxNd / 8 / kOctThreads;   // (row, 8 directions) units per thread: 2
 
 // Far slots of a tile of 128 consecutive octs o0 .. o0+127 (o0 a multiple of
 // 128): Delta_l = 4 reads the 16 parents o0/8 + r/8, Delta_l = 5 the 2
@@ -435,15 +435,15 @@ __global__ void __launch_bounds__(kOctThreads, 1) learned_oct_tc(OctArgs A)
         tc_fence_after();
         // 4. h = D + b1 -> the B-operand blocks of the per-leaf kernel: block
         //    r / 16, element (n, r % 16); rows past the end are zero (a 0 x NaN
-        //    in the product would poison a real row).  Warps w and w + 4 share
-        //    TMEM lanes 32 (w % 4) .., taking columns 0-63 and 64-127.
+        //    in the product would poison a real row).  Warps w, w + 4, w + 8
+        //    share TMEM lanes 32 (w % 4) .., taking columns 0-63, 64-95, 96-127.
         {
-            const int quarter = warp & 3, half = warp >> 2;
+            const int quarter = warp & 3, part = warp >> 2;
             const int r = quarter * 32 + lane;
             unsigned char *blk = reinterpret_cast<unsigned char *>(sHb + (r >> 4) * kHBlock);
+            const int cbeg = part == 0 ? 0 : part == 1 ? 64 : 96, cend = part == 0 ? 64 : part == 1 ? 96 : 128;
 #pragma unroll 1
-            for (int cc = 0; cc < 64; cc += 32) {
-                const int c0 = half * 64 + cc;
+            for (int c0 = cbeg; c0 < cend; c0 += 32) {
                 uint32_t v[32];
                 tmem_ld32(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
                 tmem_ld_wait();
