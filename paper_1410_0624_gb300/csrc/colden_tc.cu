@@ -22,12 +22,14 @@
 // lines.  B is precomputed in global memory in the operand layout per K-chunk,
 // so each chunk is one bulk copy.
 //
-// CTA (384 threads): warp 0 issues the MMAs (M = 128, N = 8 nd split in n_mma
-// instructions, K = 16) and owns the TMEM accumulator; warp 1 bulk-copies B;
-// warps 4-7 gather A (one row each); warps 8-11 drain TMEM (lane quarter =
-// warp % 4) into E; warps 2-3 only join the final barrier.
-// A 4-stage mbarrier pipeline couples them; every wait is bounded and a
-// timeout sets a device flag instead of trapping.
+// CTA (448 threads, two per SM): warp 0 issues the MMAs (M = 128, N = 4 nd,
+// K = 16) and owns the TMEM accumulator; warp 1 bulk-copies B; warps 2-5
+// gather A (one row each); warps 6-13 drain TMEM into E, two per lane quarter
+// (warp % 4), each half of the columns (the epilogue is on the critical path:
+// eight drain warps with two stages measured faster than four with three, as
+// shared memory holds only one of the two at two CTAs per SM).  A 2-stage
+// mbarrier pipeline couples them; every wait is bounded and a timeout sets a
+// device flag instead of trapping.
 #include <algorithm>
 
 #include "common.cuh"
@@ -37,11 +39,12 @@
 namespace cd {
 namespace {
 
-constexpr int kStages = 3;
+constexpr int kStages = 2;
 constexpr int kChunkBricks = 6;                 // K = 48 per chunk (3 MMA K-steps)
 constexpr int kBricksPerTable = 30;             // 27 neighbours + 3 zero bricks
 constexpr int kChunks = 3 * kBricksPerTable / kChunkBricks;  // 15
-constexpr int kThreads = 320;                   // 10 warps
+constexpr int kThreads = 448;                   // 14 warps
+constexpr int kEpiWarps = 8;                    // two per TMEM lane quarter, each half of the columns
 constexpr uint32_t kMaxPolls = 1u << 26;
 // A stage: core matrix (row group mg, brick b) at mg * kASbo + b * kALbo; the
 // 144-byte K stride puts the bricks of one row in different bank quads
@@ -90,8 +93,8 @@ __global__ void __launch_bounds__(kThreads, 2) shell_sum_tc(TcArgs P)
     const uint32_t bhalf = (uint32_t)P.N * kChunkBricks * 16;        // one chunk of the global B
     unsigned char *sA = smem;                                        // [kStages][8 KB]
     unsigned char *sB = smem + kStages * kAStageBytes;               // [kStages][bstage]
-    float *sT = reinterpret_cast<float *>(sB + kStages * bstage);    // [4 warps][32][33] transpose
-    uint64_t *full = reinterpret_cast<uint64_t *>(sT + 4 * 32 * 33);
+    float *sT = reinterpret_cast<float *>(sB + kStages * bstage);    // [8 warps][32][33] transpose
+    uint64_t *full = reinterpret_cast<uint64_t *>(sT + kEpiWarps * 32 * 33);
     uint64_t *empty = full + kStages;
     uint64_t *acc_full = empty + kStages;
     uint64_t *acc_empty = acc_full + 1;
@@ -107,7 +110,7 @@ __global__ void __launch_bounds__(kThreads, 2) shell_sum_tc(TcArgs P)
             mbar_init(&empty[s], 1);
         }
         mbar_init(acc_full, 1);
-        mbar_init(acc_empty, 4);               // one arrival per epilogue warp
+        mbar_init(acc_empty, kEpiWarps);       // one arrival per epilogue warp
         fence_mbar_init();
         s_fault = 0;
     }
@@ -234,8 +237,9 @@ __global__ void __launch_bounds__(kThreads, 2) shell_sum_tc(TcArgs P)
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else {
-        // ---------------- epilogue: TMEM -> E (warps 6..9, TMEM lane quarter warp % 4) ----------------
+        // ---------------- epilogue: TMEM -> E (warps 6..13, TMEM lane quarter warp % 4) ----------------
         const int ew = warp - 6;
+        const int chalf = ew >> 2;             // this warp's half of the columns
         const int quarter = warp & 3;
         float *T = sT + ew * 32 * 33;
         int u = 0;
@@ -266,7 +270,8 @@ __global__ void __launch_bounds__(kThreads, 2) shell_sum_tc(TcArgs P)
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) { fault = true; break; }
             tc_fence_after();
-            for (int c = 0; c < P.Nt; c += 32) {
+            const int cmid = ((P.Nt >> 1) + 31) & ~31;   // the halves split on a 32-column chunk boundary
+            for (int c = chalf ? cmid : 0; c < (chalf ? P.Nt : cmid); c += 32) {
                 uint32_t v[32];
                 tmem_ld32(tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c, v);
                 tmem_ld_wait();
@@ -473,7 +478,8 @@ cd_status launch_ext_tc(const ExtLaunch &a, const __nv_bfloat16 *const *brick, c
         if (P.ntiles == 0) return CD_OK;
     }
     const size_t bstage = (size_t)P.Nt * kChunkBricks * 16;
-    const size_t smem = kStages * (kAStageBytes + bstage) + sizeof(float) * 4 * 32 * 33 + (2 * kStages + 2) * 8 + 16;
+    const size_t smem =
+        kStages * (kAStageBytes + bstage) + sizeof(float) * kEpiWarps * 32 * 33 + (2 * kStages + 2) * 8 + 16;
     CD_CUDA(cudaFuncSetAttribute(shell_sum_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t grid = std::min<int64_t>(P.ntiles, 2 * (int64_t)num_sms());
     {
