@@ -166,7 +166,9 @@ cd_status cd_tree_update(cd_tree tree, const float *rho, int rho_on_device, void
  *                  evaluations use only the local ones) or CD_MODE_CONE (tables averaged
  *                  over each direction's cone)
  * 1 <= number of directions <= 768.  Components below 1e-14 in magnitude are
- * set to zero and each vector renormalised. */
+ * set to zero and each vector renormalised.  The tables are built on
+ * `stream` and the call returns once they are complete (synchronous), so the
+ * geometry may serve evaluations on any stream. */
 cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs, int n_custom, int mode,
                                  void *stream, cd_geom *out);
 
@@ -175,7 +177,13 @@ cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs,
  *   a_v[t * n_dir + d]   N_H * av_per_nh (or NULL)
  *   shield[t]            (1/n_dir) sum_d exp(-shield_k * A_V) (or NULL)
  * All three are caller-owned DEVICE buffers.  opts may be NULL (defaults).
- * Scratch (per-level partial sums) is owned by the tree and reused.
+ * Scratch (per-level partial sums) and two side streams are owned by the
+ * tree and reused; the first call on a tree (which allocates them) must not
+ * run while `stream` is capturing.  The call's work starts after what was
+ * enqueued on `stream` before it, and what is enqueued on `stream` after it
+ * waits for all of it, side streams included.  Two evaluations of one tree
+ * must not overlap on the GPU (other streams or host threads): serialise
+ * them.
  * With opts->net set, N_H is the learned form N_tree exp(delta) of
  * colden_learned.h (uniform trees; the network's n_dir must equal the
  * geometry's, else CD_EINVAL; an AMR tree returns CD_EUNSUPPORTED). */
@@ -289,7 +297,12 @@ enum {
     CD_K_COUNT = 9
 };
 /* Resets the counters; with timing != 0 later launches also record CUDA
- * events on their stream (a synchronisation happens in cd_stats_get). */
+ * events on their stream (a synchronisation happens in cd_stats_get).  An
+ * evaluation normally runs its independent steps (the far-shell prefix
+ * chain, the oct shells, the leaves of each AMR level) concurrently on two
+ * internal side streams joined back into the caller's stream; while timing
+ * is on it runs every launch in order on the caller's stream instead, so
+ * that each launch's events time that launch alone. */
 void cd_stats_reset(int timing);
 /* Number of kernel launches of one kind since the reset and, if timing was
  * on, their summed device time in milliseconds (synchronises the device). */

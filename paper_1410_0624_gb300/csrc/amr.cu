@@ -733,6 +733,14 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
     }
     A.maxe = g->maxe;
     A.nd = nd;
+    // The far-shell prefix chain (S_k needs S_{k-1}) runs on s; the oct shells
+    // of every level, which need only the densities, on side stream 0; the
+    // leaves of level k+1 on side stream 1 once E of level k and S_{k-1} are
+    // done.  Small launches of one branch fill the SMs another leaves idle.
+    SideFork fork(t, s);
+    if (fork.status() != CD_OK) return fork.status();
+    cudaStream_t s_oct = fork.side(0), s_leaf = fork.side(1);
+    bool have_S[CD_MAXL + 1] = {}, have_E[CD_MAXL + 1] = {};
     // far-shell prefixes of the refined cells
     for (int k = 3; k <= L - 2 && !insitu; ++k) {
         if (!t->n_ref[k]) continue;
@@ -749,6 +757,8 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
             e.list = t->n_ref[k] == ((int64_t)1 << (3 * k)) ? nullptr : &t->tc_ref[k];
             cd_status st = launch_ext_tc(e, t->rho_brick, g, s);
             if (st != CD_OK) return st;
+            CD_CUDA(cudaEventRecord(t->ev_S[k], s));
+            have_S[k] = true;
             continue;
         }
         A.k = k;
@@ -764,17 +774,24 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
         A.parent = t->ref_parent[k];
         A.prefix = (k - 1 >= 3) ? t->ws.S[k - 1] : nullptr;
         A.out = t->ws.S[k];
-        LaunchScope ls(CD_K_SHELL, s);
-        shell_list_fp32<<<grid_for(A.n * nd, 256), 256, 0, s>>>(A);
-        CD_CHECK_LAUNCH();
+        {
+            LaunchScope ls(CD_K_SHELL, s);
+            shell_list_fp32<<<grid_for(A.n * nd, 256), 256, 0, s>>>(A);
+            CD_CHECK_LAUNCH();
+        }
+        CD_CUDA(cudaEventRecord(t->ev_S[k], s));
+        have_S[k] = true;
     }
     // the three nearest shells of every oct, level by level
     for (int k = 0; k <= L - 1; ++k) {
         const int64_t no = t->oct_begin[k + 1] - t->oct_begin[k];
         if (!no) continue;
         if (insitu) {
-            cd_status st = launch_insitu(t, g, k, no, t->oct_key + t->oct_begin[k], t->ws.E + t->oct_begin[k] * nd, s);
+            cd_status st =
+                launch_insitu(t, g, k, no, t->oct_key + t->oct_begin[k], t->ws.E + t->oct_begin[k] * nd, s_oct);
             if (st != CD_OK) return st;
+            CD_CUDA(cudaEventRecord(t->ev_E[k], s_oct));
+            have_E[k] = true;
             continue;
         }
         if (tc && k >= 4 && t->tc_oct[k].ntiles) {
@@ -785,8 +802,10 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
             for (int q = 1; q <= 3; ++q) e.dx[q] = dx(k - q + 1);
             e.out = t->ws.E + t->oct_begin[k] * nd;
             e.list = &t->tc_oct[k];
-            cd_status st = launch_ext_tc(e, t->rho_brick, g, s);
+            cd_status st = launch_ext_tc(e, t->rho_brick, g, s_oct);
             if (st != CD_OK) return st;
+            CD_CUDA(cudaEventRecord(t->ev_E[k], s_oct));
+            have_E[k] = true;
             continue;
         }
         A.k = k;
@@ -805,9 +824,13 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
         A.parent = nullptr;
         A.prefix = nullptr;
         A.out = t->ws.E + t->oct_begin[k] * nd;
-        LaunchScope ls(CD_K_SHELL, s);
-        shell_list_fp32<<<grid_for(no * nd, 256), 256, 0, s>>>(A);
-        CD_CHECK_LAUNCH();
+        {
+            LaunchScope ls(CD_K_SHELL, s_oct);
+            shell_list_fp32<<<grid_for(no * nd, 256), 256, 0, s_oct>>>(A);
+            CD_CHECK_LAUNCH();
+        }
+        CD_CUDA(cudaEventRecord(t->ev_E[k], s_oct));
+        have_E[k] = true;
     }
     // leaves: the 16-lanes-per-oct kernel when 16-byte rows are possible
     const bool vec = nd % 4 == 0 && (uintptr_t)n_h % 16 == 0 && (uintptr_t)a_v % 16 == 0;
@@ -834,12 +857,14 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
         B.n_h = n_h;
         B.a_v = a_v;
         B.shield = shield;
+        if (have_E[k]) CD_CUDA(cudaStreamWaitEvent(s_leaf, t->ev_E[k], 0));
+        if (B.Sp && have_S[k - 1]) CD_CUDA(cudaStreamWaitEvent(s_leaf, t->ev_S[k - 1], 0));
         if (tc) {
             // BF16: the parent prefix goes into E first, then the tensor-core leaf
             // kernel takes the level's octs in tiles of 16 (csrc/leaf_tc.cu)
             float *Ek = t->ws.E + t->oct_begin[k] * nd;
             if (B.Sp) {
-                cd_status st = launch_add_parent_list(Ek, B.Sp, B.oparent, nd, no, s);
+                cd_status st = launch_add_parent_list(Ek, B.Sp, B.oparent, nd, no, s_leaf);
                 if (st != CD_OK) return st;
                 B.Sp = nullptr;
             }
@@ -857,16 +882,16 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
             b.a_v = a_v;
             b.shield = shield;
             b.oleaf = B.oleaf;
-            cd_status st = launch_leaf_tc(b, s);
+            cd_status st = launch_leaf_tc(b, s_leaf);
             if (st == CD_OK) continue;
             if (st != CD_EUNSUPPORTED) return st;
         }
-        LaunchScope ls(CD_K_LEAF, s);
-        if (vec) leaf_list<<<grid_for(no, 8, 152 * 16), 256, smem, s>>>(B);
-        else leaf_list_scalar<<<grid_for(no, 8, 152 * 16), 256, smem, s>>>(B);
+        LaunchScope ls(CD_K_LEAF, s_leaf);
+        if (vec) leaf_list<<<grid_for(no, 8, 152 * 16), 256, smem, s_leaf>>>(B);
+        else leaf_list_scalar<<<grid_for(no, 8, 152 * 16), 256, smem, s_leaf>>>(B);
         CD_CHECK_LAUNCH();
     }
-    return CD_OK;
+    return fork.join();
 }
 
 }  // namespace cd

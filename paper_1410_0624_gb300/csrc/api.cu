@@ -9,7 +9,9 @@
 //      L-1 (table 1), all seen from the oct centre.
 //   3. leaves: N_H = E[oct] + S_{L-2}[parent oct] + internal + local, then A_V
 //      and the shield.
-// Every shell l = 1 .. L-1 enters exactly once (Eq. N_discret).
+// Every shell l = 1 .. L-1 enters exactly once (Eq. N_discret).  Step 2 needs
+// only the densities, so it runs on a side stream of the tree while step 1
+// runs on the caller's stream; step 3 waits for both (SideFork).
 #include <atomic>
 #include <stdarg.h>
 #include <stdio.h>
@@ -68,6 +70,79 @@ static cd_status ensure_workspace(cd_tree t, int nd)
 }
 
 static float dx_of(const cd_tree t, int l) { return (float)(t->box_cm / (double)((int64_t)1 << l)); }
+
+static void free_side_streams(cd_tree t)
+{
+    for (int i = 0; i < 2; ++i) {
+        if (t->side[i]) cudaStreamDestroy(t->side[i]);
+        if (t->ev_done[i]) cudaEventDestroy(t->ev_done[i]);
+        t->side[i] = nullptr;
+        t->ev_done[i] = nullptr;
+    }
+    for (int l = 0; l <= CD_MAXL; ++l) {
+        if (t->ev_S[l]) cudaEventDestroy(t->ev_S[l]);
+        if (t->ev_E[l]) cudaEventDestroy(t->ev_E[l]);
+        t->ev_S[l] = t->ev_E[l] = nullptr;
+    }
+    if (t->ev_fork) cudaEventDestroy(t->ev_fork);
+    t->ev_fork = nullptr;
+}
+
+// non-blocking streams (no implicit order with the legacy default stream: the
+// fork and the join order them explicitly) and timing-free events
+static cd_status ensure_side_streams(cd_tree t)
+{
+    if (t->ev_fork) return CD_OK;
+    bool ok = true;
+    for (int i = 0; i < 2 && ok; ++i)
+        ok = cudaStreamCreateWithFlags(&t->side[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&t->ev_done[i], cudaEventDisableTiming) == cudaSuccess;
+    for (int l = 0; l <= CD_MAXL && ok; ++l)
+        ok = cudaEventCreateWithFlags(&t->ev_S[l], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&t->ev_E[l], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&t->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_side_streams(t);
+        set_error("cannot create the tree's side streams");
+        return CD_ECUDA;
+    }
+    return CD_OK;
+}
+
+SideFork::SideFork(cd_tree t, cudaStream_t s) : t_(t), s_(s)
+{
+    // the events exist in both modes: the callers record and wait on them
+    // unconditionally (on s alone they order nothing new)
+    st_ = ensure_side_streams(t);
+    serial_ = stats_timing();
+    if (st_ != CD_OK || serial_) {
+        joined_ = true;   // nothing was forked
+        return;
+    }
+    if (cudaEventRecord(t->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(t->side[0], t->ev_fork, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(t->side[1], t->ev_fork, 0) != cudaSuccess) {
+        set_error("cannot order the side streams after the caller's stream: %s", cudaGetErrorString(cudaGetLastError()));
+        st_ = CD_ECUDA;
+    }
+}
+
+cd_status SideFork::join()
+{
+    if (joined_) return CD_OK;
+    joined_ = true;
+    for (int i = 0; i < 2; ++i)
+        if (cudaEventRecord(t_->ev_done[i], t_->side[i]) != cudaSuccess ||
+            cudaStreamWaitEvent(s_, t_->ev_done[i], 0) != cudaSuccess) {
+            set_error("cannot join the side streams: %s", cudaGetErrorString(cudaGetLastError()));
+            return CD_ECUDA;
+        }
+    return CD_OK;
+}
+
+cudaStream_t SideFork::side(int i) const { return serial_ ? s_ : t_->side[i]; }
+
+SideFork::~SideFork() { join(); }
 
 }  // namespace cd
 
@@ -196,6 +271,13 @@ cd_status cd_build_tree_amr(int base_level, int max_level, double box_cm, int64_
     cudaGetDevice(&t->dev);
     t->box_cm = box_cm;
     cd_status st = build_amr(t, base_level, max_level, n_leaf, level, ijk);
+    // the index arrays went up by cudaMemcpy from pageable memory, which may
+    // return before its DMA lands and orders it only on the legacy default
+    // stream: finish it before work on any other stream reads them
+    if (st == CD_OK && cudaDeviceSynchronize() != cudaSuccess) {
+        set_error("AMR tree upload failed: %s", cudaGetErrorString(cudaGetLastError()));
+        st = CD_ECUDA;
+    }
     if (st == CD_OK) st = cd_tree_update(t, rho, rho_on_device, stream);
     if (st != CD_OK) {
         cd_tree_free(t);
@@ -300,6 +382,12 @@ cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs,
     cd_status st = build_geometry_tables(g, s);
     if (st != CD_OK) return fail(st);
     if ((st = build_tc_tables(g, s)) != CD_OK) return fail(st);
+    // the tables are complete on return, so evaluations on any stream (not
+    // only those ordered after `stream`) may read them
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        set_error("geometry build failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return fail(CD_ECUDA);
+    }
     *out = g;
     return CD_OK;
 }
@@ -354,6 +442,12 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
     const bool bf16 = opts.precision == CD_BF16 && tc_supported(nd) && geom->wb != nullptr;
     const auto use_tc = [&](int k) { return bf16 && k >= 4; };
 
+    // The oct level's shells need only the densities: they run on a side
+    // stream while the far-shell prefix chain (S_k needs S_{k-1}) runs on s;
+    // the leaves wait for both.
+    SideFork fork(tree, s);
+    if ((st = fork.status()) != CD_OK) return st;
+    cudaStream_t s_oct = fork.side(0);
     for (int k = 3; k <= L - 2; ++k) {
         ExtLaunch a = {};
         a.k = k;
@@ -378,9 +472,10 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
         }
         a.prefix_in = nullptr;   // the leaf kernel adds S_{L-2}[parent]
         a.out = tree->ws.E;
-        st = use_tc(k) ? launch_ext_tc(a, tree->rho_brick, geom, s) : launch_ext_fp32(a, geom, s);
+        st = use_tc(k) ? launch_ext_tc(a, tree->rho_brick, geom, s_oct) : launch_ext_fp32(a, geom, s_oct);
         if (st != CD_OK) return st;
     }
+    if ((st = fork.join()) != CD_OK) return st;
     LeafLaunch b = {};
     b.n_oct = tree->n_oct;
     b.nd = nd;
@@ -473,6 +568,7 @@ void cd_tree_free(cd_tree t)
     if (!t) return;
     cudaDeviceSynchronize();
     free_workspace(t);
+    free_side_streams(t);
     free_level_sums(t);
     free_tc_lists(t);
     for (int l = 0; l <= CD_MAXL; ++l) {

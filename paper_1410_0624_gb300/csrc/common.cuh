@@ -148,6 +148,13 @@ struct cd_tree_s {
     int8_t *leaf_level_h = nullptr;       // host copies of the output order
     int32_t *leaf_ijk_h = nullptr;
     int64_t *leaf_src_h = nullptr;
+    // Two side streams of one evaluation: the steps that do not depend on one
+    // another (the far-shell prefix chain, the oct shells of each level, the
+    // leaves of each level) run on them concurrently, ordered by events and
+    // joined back into the caller's stream before the call returns
+    cudaStream_t side[2] = {};
+    cudaEvent_t ev_fork = nullptr, ev_done[2] = {};
+    cudaEvent_t ev_S[CD_MAXL + 1] = {}, ev_E[CD_MAXL + 1] = {};
 };
 
 struct cd_geom_s {
@@ -194,6 +201,32 @@ class LaunchScope {
 
 // learned.cu: frees the tree's LevelSums
 void free_level_sums(cd_tree t);
+
+// stats.cu: per-launch timing is on (cd_stats_reset(1))
+bool stats_timing();
+
+// api.cu: the side streams of a tree.  Fork makes both side streams wait for
+// the work enqueued on s so far; join() (or the destructor, on an early
+// return) makes s wait for everything enqueued on them since.  While
+// per-launch timing is on, side(i) is s itself: the evaluation runs in
+// order, so that each launch's events time that launch alone.
+class SideFork {
+  public:
+    SideFork(cd_tree t, cudaStream_t s);
+    ~SideFork();
+    SideFork(const SideFork &) = delete;
+    SideFork &operator=(const SideFork &) = delete;
+    cd_status status() const { return st_; }   // CD_OK once both side streams are ordered after s
+    cudaStream_t side(int i) const;
+    cd_status join();
+
+  private:
+    cd_tree t_;
+    cudaStream_t s_;
+    cd_status st_ = CD_OK;
+    bool joined_ = false;
+    bool serial_ = false;
+};
 
 // tree.cu
 cd_status restrict_uniform(cd_tree t, const float *rho_dev, cudaStream_t s);

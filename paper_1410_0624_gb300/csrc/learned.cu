@@ -458,7 +458,10 @@ cd_status cd_net_create(int n_dir, int hidden, const float *params, cd_net *out)
          cudaMemset(net->m, 0, P * sizeof(float)) == cudaSuccess &&
          cudaMemset(net->v, 0, P * sizeof(float)) == cudaSuccess &&
          cudaMemset(net->mu, 0, I * sizeof(float)) == cudaSuccess &&
-         cudaMemcpy(net->sinv, ones.data(), I * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess;
+         cudaMemcpy(net->sinv, ones.data(), I * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+         // pageable uploads and memsets may return before they land, ordered only
+         // on the legacy default stream: finish them before any stream reads the net
+         cudaDeviceSynchronize() == cudaSuccess;
     if (!ok) {
         set_error("network upload failed: %s", cudaGetErrorString(cudaGetLastError()));
         cd_net_free(net);
@@ -553,6 +556,7 @@ cd_status cd_net_set_state(cd_net net, const float *params, const float *mu, con
     if (adam_v) CD_CUDA(cudaMemcpy(net->v, adam_v, P, cudaMemcpyHostToDevice));
     if (mu) CD_CUDA(cudaMemcpy(net->mu, mu, I, cudaMemcpyHostToDevice));
     if (sinv) CD_CUDA(cudaMemcpy(net->sinv, sinv, I, cudaMemcpyHostToDevice));
+    CD_CUDA(cudaDeviceSynchronize());   // the pageable uploads have landed
     net->step = step;
     net->version += 1;
     return CD_OK;

@@ -48,6 +48,12 @@ void drain()
 
 }  // namespace
 
+bool stats_timing()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_timing;
+}
+
 LaunchScope::LaunchScope(int kind, cudaStream_t s) : kind_(kind), s_(s)
 {
     std::lock_guard<std::mutex> lk(g_mu);
