@@ -129,8 +129,9 @@ def _source_hash(name):
 
 
 def measured_traffic(kind, L, nd, precision="bf16"):
-    """DRAM bytes per launch of a kernel from the committed ncu summary
-    (profiles/traffic.json), or None when the kernel source changed since."""
+    """DRAM bytes per step of a kernel kind (all its launches of one step) from
+    the committed ncu summary (profiles/traffic.json), or None when the kernel
+    source changed since."""
     if kind == "leaf" and precision == "bf16":
         kind = "leaf_tc"
     try:
@@ -138,7 +139,7 @@ def measured_traffic(kind, L, nd, precision="bf16"):
             tr = json.load(f)
         e = tr.get("%s/L%d/nd%d" % (kind, L, nd))
         if e and e.get("source_sha256_16") == _source_hash(KERNEL_SOURCES[kind]):
-            return e["dram_bytes_per_launch"]
+            return e.get("dram_bytes_per_step", e.get("dram_bytes_per_launch"))
     except Exception:
         pass
     return None
@@ -341,11 +342,18 @@ def run_ours(args):
     err = score()
 
     # ---- dominant kernel roofline (HBM: the algorithmic bytes of the path) ----
+    # A kind may run as several launches a step (the BF16 oct level in Morton
+    # ranges): bytes per launch / mean launch time = bytes per step / its time
+    # per step, each launch timed alone (per-launch timing runs in order).
     dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
-    dom_ms = kern[dom]["ms_per_step"] / max(kern[dom]["launches_per_step"], 1)
+    dom_launches = max(kern[dom]["launches_per_step"], 1)
+    dom_ms = kern[dom]["ms_per_step"] / dom_launches
     peak, peak_kind = _peaks()
     bpu = algo_bytes_per_cell_dir(nd)
-    achieved = bpu * n_leaf * nd / (dom_ms / 1e3) / 1e9
+    achieved = bpu * n_leaf * nd / dom_launches / (dom_ms / 1e3) / 1e9
+    traffic = measured_traffic(dom, L, nd, args.precision)
+    if traffic is not None:
+        traffic /= dom_launches
 
     # ---- the heating epilogue of §5 on the step's screening factor (HBM-bound, timed alone) ----
     heat = None
@@ -416,8 +424,9 @@ def run_ours(args):
                            "parallelism": "replicas" if world > 1 else "single"},
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": measured_traffic(dom, L, nd, args.precision), "kernel": dom,
-                             "kernel_ms": dom_ms, "peak_kind": peak_kind, "algo_bytes_per_cell_dir": bpu},
+                             "frac": achieved / peak, "traffic": traffic, "kernel": dom, "kernel_ms": dom_ms,
+                             "launches_per_step": dom_launches, "peak_kind": peak_kind,
+                             "algo_bytes_per_cell_dir": bpu},
                 "step_roofline_frac": bpu * n_leaf * nd / (ms / 1e3) / 1e9 / peak,
                 "kernels": kern, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "error_vs_oracle": err}
         if heat is not None:
