@@ -451,11 +451,13 @@ def run_amr(args):
     torch.cuda.set_device(local)
     colden.load()
     t0 = time.time()
-    lv = synth.amr_leaves_grf_torch(10, 7, [1e2, 1e3, 1e4], 30.0, 2.0, seed=2)
+    lf = args.amr_level          # finest level; the base is three levels coarser
+    lb = lf - 3
+    lv = synth.amr_leaves_grf_torch(lf, lb, [1e2, 1e3, 1e4], 30.0, 2.0, seed=2)
     torch.cuda.empty_cache()
     box = 20 * synth.PC_CM
     rho = torch.from_numpy(lv["rho"]).cuda()
-    tree = colden.build_tree_amr(7, 10, box, lv["level"], lv["ijk"], lv["rho"])
+    tree = colden.build_tree_amr(lb, lf, box, lv["level"], lv["ijk"], lv["rho"])
     build_s = time.time() - t0
     geom = colden.precompute_geometry("healpix", 2)
     nd = geom.n_dir
@@ -488,8 +490,8 @@ def run_amr(args):
     if args.cpu_seconds > 0:
         olv, oijk = tree.leaves()
         rng = np.random.default_rng(3)
-        sel = np.concatenate([rng.choice(np.nonzero(olv == l)[0], 100) for l in range(7, 11)])
-        T = oracle.Tree.amr(7, 10, box, lv["level"], lv["ijk"], lv["rho"])
+        sel = np.concatenate([rng.choice(np.nonzero(olv == l)[0], 100) for l in range(lb, lf + 1)])
+        T = oracle.Tree.amr(lb, lf, box, lv["level"], lv["ijk"], lv["rho"])
         ref = T.column_density(geom.dirs, olv[sel], oijk[sel])
         rows = torch.from_numpy(sel).cuda()
         err = _errors(n_h.reshape(-1, nd)[rows].double().cpu().numpy(), sh[rows].double().cpu().numpy(), ref)
@@ -514,9 +516,10 @@ def run_amr(args):
     line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16" if prec == colden.BF16 else "f32", "data": "synthetic",
-            "config": {"workload": "AMR: base 128^3 + 3 levels (1024^3 effective), 20 pc, k^-11/3 log-normal "
+            "config": {"workload": ("AMR: base %d^3 + 3 levels (%d^3 effective), 20 pc, k^-11/3 log-normal "
+                                    % (1 << lb, 1 << lf)) +
                                    "(mean 30, sigma_ln 2, seed 2), 48 HEALPix dirs, N_H + shield out",
-                       "leaves": int(tree.n_leaf), "leaves_per_level": np.bincount(lv["level"])[7:].tolist(),
+                       "leaves": int(tree.n_leaf), "leaves_per_level": np.bincount(lv["level"])[lb:].tolist(),
                        "refined_octs": int(tree.n_oct), "precision": args.precision, "build_s": build_s,
                        "l2": "512 MB buffer written between timed steps"},
             "gpu_launches": int(launches), "kernels": kern,
@@ -878,6 +881,8 @@ def main():
     ap.add_argument("--ray-leaves", type=int, default=100_000, help="learned: leaves scored against the ray-marcher")
     ap.add_argument("--eval-level", type=int, default=9, help="learned: leaf level of the evaluation field")
     ap.add_argument("--boxes", type=int, default=64)
+    ap.add_argument("--amr-level", type=int, default=10,
+                    help="amr: finest level of the mesh (base three levels coarser); 9 is a small case for profiling")
     ap.add_argument("--e2e-steps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
