@@ -11,7 +11,8 @@
 //      and the shield.
 // Every shell l = 1 .. L-1 enters exactly once (Eq. N_discret).  Step 2 needs
 // only the densities, so it runs on a side stream of the tree while step 1
-// runs on the caller's stream; step 3 waits for both (SideFork).
+// runs on the tree's high-priority side stream; step 3 waits for both
+// (SideFork).
 #include <atomic>
 #include <stdarg.h>
 #include <stdio.h>
@@ -71,6 +72,9 @@ static cd_status ensure_workspace(cd_tree t, int nd)
 
 static float dx_of(const cd_tree t, int l) { return (float)(t->box_cm / (double)((int64_t)1 << l)); }
 
+// tiles per CTA of the oct level's tensor-core shells in a concurrent evaluation
+constexpr int kOctTilesPerCta = 8;
+
 static void free_side_streams(cd_tree t)
 {
     for (int i = 0; i < 2; ++i) {
@@ -93,9 +97,13 @@ static void free_side_streams(cd_tree t)
 static cd_status ensure_side_streams(cd_tree t)
 {
     if (t->ev_fork) return CD_OK;
-    bool ok = true;
+    // side stream 1 at the highest priority: its pending CTAs are placed first
+    // when CTAs of other launches retire
+    int least = 0, greatest = 0;
+    bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess;
     for (int i = 0; i < 2 && ok; ++i)
-        ok = cudaStreamCreateWithFlags(&t->side[i], cudaStreamNonBlocking) == cudaSuccess &&
+        ok = cudaStreamCreateWithPriority(&t->side[i], cudaStreamNonBlocking, i == 1 ? greatest : least) ==
+                 cudaSuccess &&
              cudaEventCreateWithFlags(&t->ev_done[i], cudaEventDisableTiming) == cudaSuccess;
     for (int l = 0; l <= CD_MAXL && ok; ++l)
         ok = cudaEventCreateWithFlags(&t->ev_S[l], cudaEventDisableTiming) == cudaSuccess &&
@@ -442,12 +450,13 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
     const bool bf16 = opts.precision == CD_BF16 && tc_supported(nd) && geom->wb != nullptr;
     const auto use_tc = [&](int k) { return bf16 && k >= 4; };
 
-    // The oct level's shells need only the densities: they run on a side
-    // stream while the far-shell prefix chain (S_k needs S_{k-1}) runs on s;
-    // the leaves wait for both.
+    // The oct level's shells need only the densities: they run on side stream
+    // 0 in launches of kOctTilesPerCta tiles per CTA, while the far-shell prefix
+    // chain (S_k needs S_{k-1}) runs on side stream 1, the high-priority one, so
+    // its CTAs take SMs as the oct level's retire; the leaves wait for both.
     SideFork fork(tree, s);
     if ((st = fork.status()) != CD_OK) return st;
-    cudaStream_t s_oct = fork.side(0);
+    cudaStream_t s_oct = fork.side(0), s_chain = fork.side(1);
     for (int k = 3; k <= L - 2; ++k) {
         ExtLaunch a = {};
         a.k = k;
@@ -457,7 +466,7 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
         a.dx[3] = dx_of(tree, k - 2);
         a.prefix_in = (k > 3) ? tree->ws.S[k - 1] : nullptr;
         a.out = tree->ws.S[k];
-        st = use_tc(k) ? launch_ext_tc(a, tree->rho_brick, geom, s) : launch_ext_fp32(a, geom, s);
+        st = use_tc(k) ? launch_ext_tc(a, tree->rho_brick, geom, s_chain) : launch_ext_fp32(a, geom, s_chain);
         if (st != CD_OK) return st;
     }
     if (L >= 2) {
@@ -472,6 +481,7 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
         }
         a.prefix_in = nullptr;   // the leaf kernel adds S_{L-2}[parent]
         a.out = tree->ws.E;
+        a.tiles_per_cta = fork.serial() ? 0 : kOctTilesPerCta;
         st = use_tc(k) ? launch_ext_tc(a, tree->rho_brick, geom, s_oct) : launch_ext_fp32(a, geom, s_oct);
         if (st != CD_OK) return st;
     }

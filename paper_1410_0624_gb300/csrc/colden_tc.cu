@@ -481,7 +481,10 @@ cd_status launch_ext_tc(const ExtLaunch &a, const __nv_bfloat16 *const *brick, c
     const size_t smem =
         kStages * (kAStageBytes + bstage) + sizeof(float) * kEpiWarps * 32 * 33 + (2 * kStages + 2) * 8 + 16;
     CD_CUDA(cudaFuncSetAttribute(shell_sum_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int64_t grid = std::min<int64_t>(P.ntiles, 2 * (int64_t)num_sms());
+    // persistent CTAs hold every SM until the last tile; n tiles per CTA let the
+    // CTAs of other streams' launches in as these retire
+    const int64_t grid = a.tiles_per_cta > 0 ? (P.ntiles + a.tiles_per_cta - 1) / a.tiles_per_cta
+                                             : std::min<int64_t>(P.ntiles, 2 * (int64_t)num_sms());
     {
         LaunchScope ls(CD_K_SHELL, s);
         shell_sum_tc<<<(unsigned)grid, kThreads, smem, s>>>(P);

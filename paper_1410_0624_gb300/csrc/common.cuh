@@ -218,6 +218,7 @@ class SideFork {
     SideFork &operator=(const SideFork &) = delete;
     cd_status status() const { return st_; }   // CD_OK once both side streams are ordered after s
     cudaStream_t side(int i) const;
+    bool serial() const { return serial_; }
     cd_status join();
 
   private:
@@ -260,6 +261,7 @@ struct ExtLaunch {
     const float *prefix_in;   // S_{k-1} (Morton) or NULL
     float *out;               // Morton [8^k][nd], or [n_recv][nd] with a list
     const TcList *list;       // tensor-core form only: receivers of an AMR level (NULL: every cell of level k)
+    int tiles_per_cta;        // tensor-core form: 0 = persistent CTAs (two per SM); n = one CTA per n tiles
 };
 cd_status launch_ext_fp32(const ExtLaunch &a, cd_geom g, cudaStream_t s);
 
