@@ -54,7 +54,7 @@ typedef enum {
     CD_ENOMEM = -2,        /* device allocation failed */
     CD_ECUDA = -3,         /* a CUDA runtime call failed */
     CD_ETIMEOUT = -4,      /* a bounded device-side wait gave up */
-    CD_EUNSUPPORTED = -5   /* valid request this build does not provide */
+    CD_EUNSUPPORTED = -5   /* valid request the library does not provide */
 } cd_status;
 
 /* Direction sets (§3.2). */

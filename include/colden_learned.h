@@ -31,7 +31,7 @@
  *
  * Conventions are those of colden.h (status codes, cd_last_error, stream
  * semantics, leaf order).  Row-major device arrays, float32 unless stated.
- * This build serves uniform trees (cd_build_tree_uniform) in these entry
+ * The library serves uniform trees (cd_build_tree_uniform) in these entry
  * points; an AMR tree returns CD_EUNSUPPORTED.
  */
 #ifndef COLDEN_LEARNED_H

@@ -187,7 +187,7 @@ cd_status check_tree_geom(cd_tree t, cd_geom g)
         return CD_EINVAL;
     }
     if (t->amr) {
-        set_error("the learned form and the ray-marcher serve uniform trees in this build");
+        set_error("the learned form and the ray-marcher serve uniform trees only");
         return CD_EUNSUPPORTED;
     }
     return CD_OK;
