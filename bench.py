@@ -49,6 +49,34 @@ def _rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def init_replicas(backend: str = "nccl"):
+    """One process per GPU, launched by torch.distributed.run: (rank, world,
+    local_rank, dist or None).  The process group exists only when WORLD_SIZE
+    > 1; the replicas share nothing but the timing barrier and the max over
+    ranks (the path has no exchange step).  With nccl the caller has set the
+    CUDA device of local_rank."""
+    rank, world, local = _rank()
+    if world == 1:
+        return rank, world, local, None
+    import torch
+    import torch.distributed as dist
+    if backend == "nccl":
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist.init_process_group(backend)
+    return rank, world, local, dist
+
+
+def max_over_ranks(x: float, dist, device=None) -> float:
+    """The largest x over the ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -262,12 +290,8 @@ def run_ours(args):
     import torch
     from paper_1410_0624_gb300 import colden
 
-    rank, world, local = _rank()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(_rank()[2])
+    rank, world, local, dist = init_replicas("nccl")
     colden.load()
     forms = {"fp32": colden.FP32, "bf16": colden.BF16}
 
@@ -295,12 +319,8 @@ def run_ours(args):
             colden.column_density(tree, geom, n_h=n_h, shield=sh, precision=forms[prec], stream=stream)
         return step
 
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def max_ranks(x):
+        return max_over_ranks(x, dist, dev)
 
     # ---- the FP64 oracle on a seeded leaf sample: CPU baseline and reference values ----
     cpu = sample = None
@@ -336,7 +356,7 @@ def run_ours(args):
     launches = sum(colden.stats_get(k)[0] for k in range(len(colden.KERNEL_KINDS)))
     if dist:
         dist.barrier()
-    ms = max_over_ranks(ms)
+    ms = max_ranks(ms)
     value = n_leaf * nd * world / (ms / 1e3)
     kern = _kernel_breakdown(colden, step, flush, args.steps)
     err = score()
@@ -380,7 +400,7 @@ def run_ours(args):
             flush.zero_()
             ostep()
         torch.cuda.synchronize()
-        oms = max_over_ranks(_time_steps(ostep, flush, stream, args.steps))
+        oms = max_ranks(_time_steps(ostep, flush, stream, args.steps))
         other = {"precision": other_name, "value": n_leaf * nd * world / (oms / 1e3), "ms_per_step": oms,
                  "kernels": _kernel_breakdown(colden, ostep, flush, args.steps), "error_vs_oracle": score()}
 
@@ -405,7 +425,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             if s > 0:
                 times.append(a.elapsed_time(b))
-        e_ms = max_over_ranks(float(np.mean(times)))
+        e_ms = max_ranks(float(np.mean(times)))
         e2e = {"value": n_leaf * nd * world / (e_ms / 1e3), "unit": UNIT, "ms_per_step": e_ms,
                "h2d_bytes_per_step": 4 * n_leaf, "d2h_bytes_per_step": 4 * n_leaf * nd + 4 * n_leaf}
 
