@@ -77,6 +77,10 @@ def max_over_ranks(x: float, dist, device=None) -> float:
     return float(t.item())
 
 
+# nominal HBM3e bandwidth of the part, beside the measured copy peak
+NOMINAL_HBM_GBS = 8000.0
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -446,7 +450,8 @@ def run_ours(args):
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic, "kernel": dom, "kernel_ms": dom_ms,
                              "launches_per_step": dom_launches, "peak_kind": peak_kind,
-                             "algo_bytes_per_cell_dir": bpu},
+                             "algo_bytes_per_cell_dir": bpu, "nominal_peak": NOMINAL_HBM_GBS,
+                             "frac_of_nominal": achieved / NOMINAL_HBM_GBS},
                 "step_roofline_frac": bpu * n_leaf * nd / (ms / 1e3) / 1e9 / peak,
                 "kernels": kern, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "error_vs_oracle": err}
         if heat is not None:
@@ -546,8 +551,9 @@ def run_amr(args):
             "roofline": {"bound": "hbm", "achieved": bpu * units / (dom_ms / 1e3) / 1e9, "peak": peak,
                          "unit": "GB/s", "frac": bpu * units / (dom_ms / 1e3) / 1e9 / peak, "traffic": None,
                          "kernel": dom, "kernel_ms": dom_ms, "peak_kind": peak_kind,
-                         "algo_bytes_per_cell_dir": bpu, "note": "algorithmic bytes of the whole path over the "
-                                                                  "dominant kernel kind's time"},
+                         "algo_bytes_per_cell_dir": bpu, "nominal_peak": NOMINAL_HBM_GBS,
+                         "frac_of_nominal": bpu * units / (dom_ms / 1e3) / 1e9 / NOMINAL_HBM_GBS,
+                         "note": "algorithmic bytes of the whole path over the dominant kernel kind's time"},
             "step_roofline_frac": bpu * units / (ms / 1e3) / 1e9 / peak, "dominant_kernel": dom,
             "clocks": clk, "error_vs_oracle": err}
     if other is not None:
