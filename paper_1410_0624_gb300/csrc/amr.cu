@@ -160,25 +160,38 @@ __global__ void fill_deep(const uint64_t *__restrict__ keys, const int8_t *__res
 }
 
 // Sibling densities of every oct: child o at level k+1 from the dense array,
-// or from the leaves when k+1 is the finest level.
-__global__ void gather_rho8(const uint64_t *__restrict__ okey, const int32_t *__restrict__ oleaf, int64_t n, int k,
-                            const float *__restrict__ dense_k1, const float *__restrict__ rho_leaf,
-                            float *__restrict__ rho8)
+// or from the leaves when k+1 is the finest level.  One launch over the octs
+// of every level (they are stored level by level, oct_begin[k] .. oct_begin[k+1]).
+struct Rho8Args {
+    const uint64_t *okey;
+    const int32_t *oleaf;
+    const float *rho_leaf;
+    float *rho8;
+    int64_t n8;                          // 8 x all octs
+    int nlev;                            // levels 0 .. nlev-1 hold octs
+    int64_t begin[CD_MAXL + 2];          // oct_begin
+    const float *dense[CD_MAXL + 1];     // level k+1 as a dense array, or NULL: from the leaves
+};
+
+__global__ void gather_rho8(const __grid_constant__ Rho8Args A)
 {
-    const int64_t side = (int64_t)1 << (k + 1);
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 8 * n; e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < A.n8; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e >> 3;
         const int o = (int)(e & 7);
+        int k = 0;
+        while (k + 1 < A.nlev && i >= A.begin[k + 1]) ++k;
+        const float *dense_k1 = A.dense[k];
         float v;
         if (dense_k1) {
-            const uint64_t m = okey[i];
+            const int64_t side = (int64_t)1 << (k + 1);
+            const uint64_t m = A.okey[i];
             const int64_t x = 2 * (int64_t)compact3(m) + (o & 1), y = 2 * (int64_t)compact3(m >> 1) + ((o >> 1) & 1),
                           z = 2 * (int64_t)compact3(m >> 2) + ((o >> 2) & 1);
             v = dense_k1[(z * side + y) * side + x];
         } else {
-            v = rho_leaf[oleaf[e]];
+            v = A.rho_leaf[A.oleaf[e]];
         }
-        rho8[e] = v;
+        A.rho8[e] = v;
     }
 }
 
@@ -683,13 +696,18 @@ cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s)
     } else if ((st = restrict_dense(t, lf, s)) != CD_OK) {
         return st;
     }
-    for (int k = 0; k < lmax; ++k) {
-        const int64_t no = t->oct_begin[k + 1] - t->oct_begin[k];
-        if (!no) continue;
+    Rho8Args R = {};
+    R.okey = t->oct_key;
+    R.oleaf = t->oct_leaf;
+    R.rho_leaf = t->rho_leaf;
+    R.rho8 = t->oct_rho8;
+    R.n8 = 8 * t->oct_begin[lmax];
+    R.nlev = lmax;
+    for (int k = 0; k <= lmax; ++k) R.begin[k] = t->oct_begin[k];
+    for (int k = 0; k < lmax; ++k) R.dense[k] = k + 1 <= lf ? t->rho_lvl[k + 1] : nullptr;
+    if (R.n8 > 0) {
         LaunchScope ls(CD_K_RESTRICT, s);
-        gather_rho8<<<grid_for(8 * no, 256), 256, 0, s>>>(t->oct_key + t->oct_begin[k], t->oct_leaf + 8 * t->oct_begin[k],
-                                                          no, k, k + 1 <= lf ? t->rho_lvl[k + 1] : nullptr,
-                                                          t->rho_leaf, t->oct_rho8 + 8 * t->oct_begin[k]);
+        gather_rho8<<<grid_for(R.n8, 256), 256, 0, s>>>(R);
         CD_CHECK_LAUNCH();
     }
     return CD_OK;
