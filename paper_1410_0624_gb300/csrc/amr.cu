@@ -35,13 +35,6 @@ inline unsigned grid_for(int64_t n, int block, int cap = 152 * 32)
 
 // ---- update kernels ------------------------------------------------------------
 
-__global__ void gather_leaves(const float *__restrict__ in, const int64_t *__restrict__ src, int64_t n,
-                              float *__restrict__ out)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = in[src[i]];
-}
-
 // The dense level arrays above the base are built top-down: a cell inside a
 // leaf of a coarser level takes the value its parent already holds (a
 // coalesced pass per level), the leaves of the level are scattered in, and a
@@ -50,13 +43,21 @@ __global__ void gather_leaves(const float *__restrict__ in, const int64_t *__res
 // Leaf densities are finite (checked on the host path), so NaN is free as a
 // marker.
 
-// NaN at the refined cells of level l (a sorted Morton key list).
-__global__ void mark_refined(const uint64_t *__restrict__ keys, int64_t n, int l, float *__restrict__ dense)
+// One launch for two independent passes over disjoint arrays: entries [0, n)
+// gather the caller's leaf densities into output order, entries [n, n + nr)
+// mark the base level's refined cells NaN
+__global__ void gather_and_mark(const float *__restrict__ in, const int64_t *__restrict__ src, int64_t n,
+                                float *__restrict__ out, const uint64_t *__restrict__ keys, int64_t nr, int l,
+                                float *__restrict__ dense)
 {
     const int64_t side = (int64_t)1 << l;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t m = keys[i];
-        dense[((int64_t)compact3(m >> 2) * side + compact3(m >> 1)) * side + compact3(m)] = __int_as_float(0x7fc00000);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n + nr; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < n) {
+            out[i] = in[src[i]];
+        } else {
+            const uint64_t m = keys[i - n];
+            dense[((int64_t)compact3(m >> 2) * side + compact3(m >> 1)) * side + compact3(m)] = __int_as_float(0x7fc00000);
+        }
     }
 }
 
@@ -640,17 +641,18 @@ cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s)
 {
     const int lmax = t->L, lf = lmax - 1;
     {
+        // leaves into output order, and the base level's refined cells marked NaN
+        const int64_t nr = t->n_ref[t->base];
         LaunchScope ls(CD_K_RESTRICT, s);
-        gather_leaves<<<grid_for(t->n_leaf, 256), 256, 0, s>>>(rho_dev, t->leaf_src, t->n_leaf, t->rho_leaf);
+        gather_and_mark<<<grid_for(t->n_leaf + nr, 256), 256, 0, s>>>(rho_dev, t->leaf_src, t->n_leaf, t->rho_leaf,
+                                                                        t->ref_key[t->base], nr, t->base,
+                                                                        t->rho_lvl[t->base]);
     }
     CD_CHECK_LAUNCH();
-    // dense levels base .. lf, top-down (the base level's refined cells as NaN)
+    // dense levels base .. lf, top-down
     for (int l = t->base; l <= lf; ++l) {
         if (l == t->base) {
-            if (t->n_ref[l]) {
-                LaunchScope ls(CD_K_RESTRICT, s);
-                mark_refined<<<grid_for(t->n_ref[l], 256), 256, 0, s>>>(t->ref_key[l], t->n_ref[l], l, t->rho_lvl[l]);
-            }
+            // done above
         } else if (t->sparse_finest && l == lf) {
             // no prolongation into the finest dense level: fill_deep paints the part that is read
         } else if (l >= 2) {
