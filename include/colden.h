@@ -212,6 +212,8 @@ cd_status cd_batch_run(cd_batch batch, void *stream);
 /* Chosen branch count, eager milliseconds measured for W = 1, 2, 4, 8 (-1 where
  * not tried; any pointer may be NULL) and kernel launches one run contains. */
 cd_status cd_batch_info(cd_batch batch, int *width, double *ms_tried, int64_t *kernel_nodes);
+/* Releases the graph and the internal streams (synchronises the device first);
+ * the trees, geometries and outputs stay the caller's.  NULL is ignored. */
 void cd_batch_free(cd_batch batch);
 
 /* Same evaluation as cd_column_density (FP32, uniform trees), but its scratch
@@ -308,8 +310,13 @@ void cd_stats_reset(int timing);
  * on, their summed device time in milliseconds (synchronises the device). */
 cd_status cd_stats_get(int kind, int64_t *launches, double *ms);
 
+/* Release a handle and every device buffer, stream and event it owns, after
+ * synchronising the device (work still enqueued on it finishes first).  NULL
+ * is ignored; a handle must not be used after it is freed. */
 void cd_tree_free(cd_tree tree);
 void cd_geom_free(cd_geom geom);
+/* The message of the last failed call on this host thread (thread-local,
+ * library-owned, valid until the thread's next failing call). */
 const char *cd_last_error(void);
 
 #ifdef __cplusplus

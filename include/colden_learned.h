@@ -130,6 +130,8 @@ cd_status cd_net_get_state(cd_net net, float *params, float *mu, float *sinv, fl
 cd_status cd_net_set_state(cd_net net, const float *params, const float *mu, const float *sinv,
                            const float *adam_m, const float *adam_v, int64_t step);
 
+/* The network's direction count, hidden width and parameter count (any
+ * pointer may be NULL); CD_EINVAL for a NULL handle. */
 cd_status cd_net_info(cd_net net, int *n_dir, int *hidden, int64_t *num_params);
 
 /* Frees the network (synchronises the device first). */
