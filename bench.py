@@ -266,7 +266,8 @@ def _time_steps(step, flush, stream, steps):
 
 
 def _kernel_breakdown(colden, step, flush, steps):
-    """Per-kind launches and device ms per step (events on the launching stream)."""
+    """Per-kind launches, device ms and dense tensor-core flops per step
+    (events on the launching stream)."""
     import torch
     colden.stats_reset(timing=True)
     for _ in range(steps):
@@ -278,8 +279,25 @@ def _kernel_breakdown(colden, step, flush, steps):
         n, kms = colden.stats_get(k)
         if n:
             out[name] = {"launches_per_step": n / steps, "ms_per_step": kms / steps}
+            fl = colden.stats_flops(k)
+            if fl > 0:
+                out[name]["tensor_flops_per_step"] = fl / steps
     colden.stats_reset(timing=False)
     return out
+
+
+def _tensor_fraction(kern):
+    """Dense BF16 tensor throughput of each kernel kind that issues tcgen05
+    MMAs (its flops per step over its device time per step), against the
+    measured sustained BF16 peak: these kernels run inside a longer step."""
+    peak, kind = _tensor_peak(sustained=True)
+    out = {}
+    for name, k in kern.items():
+        fl = k.get("tensor_flops_per_step", 0.0)
+        if fl > 0 and k["ms_per_step"] > 0:
+            tf = fl / (k["ms_per_step"] / 1e3) / 1e12
+            out[name] = {"TFLOP/s": tf, "frac": tf / peak, "flops_per_step": fl}
+    return {"peak": peak, "peak_kind": kind, "unit": "TFLOP/s", "kernels": out} if out else None
 
 
 def _errors(got_nh, got_sh, ref):
@@ -511,15 +529,28 @@ def run_amr(args):
     units = tree.n_leaf * nd
     peak, peak_kind = _peaks()
     bpu = algo_bytes_per_cell_dir(nd)
-    err = None
+    err = cpu = None
     if args.cpu_seconds > 0:
+        # the FP64 oracle on a seeded sample of >= 1e5 leaves (uniform over the
+        # output rows, plus 100 of every level), timed on the host cores and
+        # extrapolated to the whole mesh; the same rows give the error
         olv, oijk = tree.leaves()
         rng = np.random.default_rng(3)
-        sel = np.concatenate([rng.choice(np.nonzero(olv == l)[0], 100) for l in range(lb, lf + 1)])
+        n_s = int(min(tree.n_leaf, max(100_000, args.amr_sample)))
+        sel = np.unique(np.concatenate([rng.choice(tree.n_leaf, n_s, replace=False)] +
+                                       [rng.choice(np.nonzero(olv == l)[0], 100) for l in range(lb, lf + 1)]))
         T = oracle.Tree.amr(lb, lf, box, lv["level"], lv["ijk"], lv["rho"])
-        ref = T.column_density(geom.dirs, olv[sel], oijk[sel])
+        t0 = time.perf_counter()
+        ref = T.column_density(oracle.dirs_healpix(2), olv[sel], oijk[sel])
+        dt = time.perf_counter() - t0
         rows = torch.from_numpy(sel).cuda()
         err = _errors(n_h.reshape(-1, nd)[rows].double().cpu().numpy(), sh[rows].double().cpu().numpy(), ref)
+        rate = len(sel) * nd / dt
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d seeded leaves (uniform over the output rows + 100 per level) x %d dirs (%.1f s); "
+                         "extrapolated to all %d leaves: %.1f s per step" % (len(sel), nd, dt, tree.n_leaf,
+                                                                           units / rate)}
     dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
     dom_ms = kern[dom]["ms_per_step"]
     # the other form (FP32 list kernels vs BF16 tensor-core lists), same mesh
@@ -555,7 +586,7 @@ def run_amr(args):
                          "frac_of_nominal": bpu * units / (dom_ms / 1e3) / 1e9 / NOMINAL_HBM_GBS,
                          "note": "algorithmic bytes of the whole path over the dominant kernel kind's time"},
             "step_roofline_frac": bpu * units / (ms / 1e3) / 1e9 / peak, "dominant_kernel": dom,
-            "clocks": clk, "error_vs_oracle": err}
+            "tensor": _tensor_fraction(kern), "clocks": clk, "cpu_baseline": cpu, "error_vs_oracle": err}
     if other is not None:
         line["compare"] = other
         line["speedup_vs_" + other["precision"]] = other["ms_per_step"] / ms
@@ -573,7 +604,7 @@ def run_batch(args):
     colden.load()
     rng = np.random.default_rng(4)
     g12, g48 = colden.precompute_geometry("healpix", 1), colden.precompute_geometry("healpix", 2)
-    trees, geoms, desc = [], [], []
+    trees, geoms, desc, srcs = [], [], [], []
     t0 = time.time()
     for i in range(args.boxes):
         base = int(rng.choice([5, 6, 7, 8]))
@@ -587,8 +618,10 @@ def run_batch(args):
             rho = np.zeros((n, n, n), np.float32)
             rho[lv["ijk"][:, 2], lv["ijk"][:, 1], lv["ijk"][:, 0]] = lv["rho"]
             trees.append(colden.build_tree_uniform(torch.from_numpy(rho).cuda(), 10 * synth.PC_CM))
+            srcs.append(("u", rho))
         else:
             trees.append(colden.build_tree_amr(base, base + ref, 10 * synth.PC_CM, lv["level"], lv["ijk"], lv["rho"]))
+            srcs.append(("a", lv))
         geoms.append(g12 if nd == 12 else g48)
         desc.append((1 << base, ref, nd, trees[-1].n_leaf))
         torch.cuda.empty_cache()
@@ -611,14 +644,64 @@ def run_batch(args):
         return a.elapsed_time(b) / args.steps
 
     colden.stats_reset(timing=False)
-    ms_eager = timed(lambda: colden.column_density_batch(trees, geoms, shield=sh, precision=prec, stream=stream))
+    eager = lambda: colden.column_density_batch(trees, geoms, shield=sh, precision=prec, stream=stream)
+    ms_eager = timed(eager)
     batch = colden.Batch(trees, geoms, shield=sh, precision=prec, stream=stream)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
+    colden.stats_reset(timing=False)
     ms_graph = timed(lambda: batch.run(stream=stream))
     clk = clocks.stop()
     info = batch.info()
+    flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda")
+    kern = _kernel_breakdown(colden, eager, flush, 1)
+
+    # ---- roofline: screening factor only, so the binding roof is the tensor
+    # pipe of the shell contraction (the HBM bytes are ~9 B per leaf) ----
+    tens = _tensor_fraction(kern)
+    dom = "shell" if tens and "shell" in tens["kernels"] else max(kern, key=lambda k: kern[k]["ms_per_step"])
+    roof = None
+    if tens and dom in tens["kernels"]:
+        t = tens["kernels"][dom]
+        roof = {"bound": "tensor", "achieved": t["TFLOP/s"], "peak": tens["peak"], "unit": "TFLOP/s",
+                "frac": t["frac"], "traffic": None, "kernel": dom, "kernel_ms": kern[dom]["ms_per_step"],
+                "launches_per_step": kern[dom]["launches_per_step"], "peak_kind": tens["peak_kind"],
+                "flops_per_step": t["flops_per_step"],
+                "note": "dense BF16 MMA flops the shell kernels issue (2 M N K, padded tiles included) over their "
+                        "summed device time, each launch timed alone in a per-box pass"}
+
+    # ---- FP64 oracle: every box on a seeded leaf sample (error of the replayed
+    # screening factor), timed on the host cores ----
+    cpu = err = None
+    if args.cpu_seconds > 0:
+        import oracle
+        torch.cuda.synchronize()
+        batch.run(stream=stream)
+        torch.cuda.synchronize()
+        srng = np.random.default_rng(17)
+        per = max(200, int(args.batch_sample / len(trees)))
+        t_or, n_or, worst, per_box = 0.0, 0, 0.0, []
+        for (kind, data), t, g, out in zip(srcs, trees, geoms, sh):
+            T = oracle.Tree.uniform(data, 10 * synth.PC_CM) if kind == "u" else \
+                oracle.Tree.amr(data["base"], data["lmax"], 10 * synth.PC_CM, data["level"], data["ijk"], data["rho"])
+            olv, oijk = t.leaves()
+            rows = np.sort(srng.choice(t.n_leaf, size=min(per, t.n_leaf), replace=False))
+            ta = time.perf_counter()
+            ref = T.column_density(oracle.dirs_healpix(1 if g.n_dir == 12 else 2), olv[rows], oijk[rows])
+            t_or += time.perf_counter() - ta
+            n_or += len(rows) * g.n_dir
+            e = float(np.max(np.abs(out.cpu().numpy()[rows] - oracle.shield(ref))))
+            per_box.append(e)
+            worst = max(worst, e)
+            del T
+        cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        cpu = {"value": n_or / t_or, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d seeded leaves per box x its directions, all %d boxes (%.1f s)"
+                         % (per, len(trees), t_or)}
+        err = {"shield_abs_max": worst, "shield_abs_max_per_box": per_box, "leaves_per_box": per,
+               "tolerance": 5e-3 if prec == colden.BF16 else 1e-5}
+
     line = {"metric": METRIC, "value": units / (ms_graph / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16", "data": "synthetic",
@@ -626,10 +709,13 @@ def run_batch(args):
                                    "sigma_ln U[1,2.5], 12 or 48 HEALPix dirs, 10 pc, screening factor out"
                                    % args.boxes, "cell_dirs_per_step": units, "precision": args.precision,
                        "boxes": [{"base": b, "refined_levels": r, "n_dir": d, "leaves": n} for b, r, d, n in desc],
-                       "generation_s": gen_s},
+                       "generation_s": gen_s,
+                       "l2": "inputs (%.1f GB of densities and levels) larger than L2" % (
+                           sum(t.n_leaf for t in trees) * 4.6 / 1e9)},
             "gpu_launches": info["kernel_nodes"] * args.steps,
             "batch": {"graph_ms": ms_graph, "per_box_launches_ms": ms_eager, "speedup": ms_eager / ms_graph,
                       "autotune": info},
+            "kernels": kern, "roofline": roof, "tensor": tens, "cpu_baseline": cpu, "error_vs_oracle": err,
             "clocks": clk}
     print(json.dumps(line), flush=True)
     batch.free()
@@ -804,13 +890,15 @@ def run_learned(args):
     return 0
 
 
-def _tensor_peak():
+def _tensor_peak(sustained=False):
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
+        if sustained:
+            return float(p["bf16_tflops_sustained"]), "measured sustained"
         return float(p["bf16_tflops"]), "measured burst"
     except Exception:
-        return 1900.0, "fallback"
+        return (1700.0, "fallback sustained") if sustained else (1900.0, "fallback")
 
 
 def _learned_oracle_checks(colden, synth, tree, geom, rho, box, L, cpu_seconds):
@@ -910,6 +998,8 @@ def main():
     ap.add_argument("--amr-level", type=int, default=10,
                     help="amr: finest level of the mesh (base three levels coarser); 9 is a small case for profiling")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--amr-sample", type=int, default=100_000, help="amr: leaves of the oracle sample (>= 1e5)")
+    ap.add_argument("--batch-sample", type=int, default=64_000, help="batch: oracle leaves over all boxes")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

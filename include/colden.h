@@ -205,7 +205,14 @@ cd_status cd_column_density_batch(int n, const cd_tree *trees, const cd_geom *ge
  * on `stream`: one launch evaluates every box with its tree's current
  * densities (cd_tree_update between runs is seen).  The trees, geometries and
  * output buffers given at creation must stay alive and must not be resized
- * until cd_batch_free.  Creation must not happen while `stream` is capturing. */
+ * until cd_batch_free.  Creation must not happen while `stream` is capturing.
+ * The graph holds each tree's scratch buffers, so while the batch lives they
+ * are pinned: cd_column_density on one of its trees with a geometry of
+ * another direction count (which would reallocate them) returns CD_EINVAL.
+ * Errors at creation: CD_EINVAL for NULL entries or a tree listed twice with
+ * geometries of different direction counts; CD_EUNSUPPORTED for a learned
+ * correction in opts (its cached per-level sums are not replay-safe: use
+ * cd_column_density_batch). */
 cd_status cd_batch_create(int n, const cd_tree *trees, const cd_geom *geoms, const cd_opts *opts, float *const *n_h,
                           float *const *a_v, float *const *shield, void *stream, cd_batch *out);
 cd_status cd_batch_run(cd_batch batch, void *stream);
@@ -227,8 +234,12 @@ void cd_batch_free(cd_batch batch);
  *   rounding) must fit in 4 Mi floats, e.g. L <= 6 with 48 directions; larger
  *   trees get CD_EINVAL with the required size in cd_last_error().
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
+ *   (cudaGetSymbolAddress) with that device current.  That lookup is also
+ *   what makes the CUDA runtime load the library's module holding the array
+ *   on that device (modules load lazily), i.e. where the 16 MiB are taken.
+ *   So make one call during set-up, before the time-step loop and before any
+ *   stream capture: a call with all three outputs NULL does the lookup and
+ *   enqueues nothing.
  *   Every call on a device shares the one array and leaves its contents
  *   behind; nothing in it needs clearing (each element read is written
  *   earlier in the same call).  Calls that overlap on the GPU (different
@@ -285,6 +296,17 @@ cd_status cd_geom_rays(cd_geom geom, int *n_sub, double *rays);
  * its outputs are then incomplete. */
 cd_status cd_device_status(void *stream);
 
+/* Testing hook of the failure detection above (no counterpart in the paper).
+ * polls >= 0 caps the pipeline waits of the BF16 leaf kernel (its input
+ * copies landing, its tensor-core product completing) at `polls` polls; with
+ * 0 they give up at once, so every CTA takes the timeout path: it records the
+ * flag, still waits (with the full limit) for the copies and products it has
+ * issued, frees its tensor memory and returns, and cd_device_status then
+ * reports CD_ETIMEOUT while the context stays usable.  polls < 0 restores the
+ * default limit.  Process-wide; applies to launches enqueued after the call.
+ * Never set it outside tests: the outputs of capped launches are incomplete. */
+void cd_debug_wait_polls(int64_t polls);
+
 /* Launch statistics of this process, for benchmarks.  Kernel kinds: */
 enum {
     CD_K_RESTRICT = 0,     /* level restriction and leaf reordering */
@@ -309,6 +331,12 @@ void cd_stats_reset(int timing);
 /* Number of kernel launches of one kind since the reset and, if timing was
  * on, their summed device time in milliseconds (synchronises the device). */
 cd_status cd_stats_get(int kind, int64_t *launches, double *ms);
+/* Dense tensor-core work, in flops, that the launches of one kind issued
+ * since the reset: 2 M N K summed over their tcgen05 MMAs, zero rows and
+ * columns of padded tiles included (0 for kinds that run on the CUDA cores).
+ * Counted on the host at launch time, so launches replayed from a CUDA graph
+ * (cd_batch_run) are not counted. */
+cd_status cd_stats_flops(int kind, double *flops);
 
 /* Release a handle and every device buffer, stream and event it owns, after
  * synchronising the device (work still enqueued on it finishes first).  NULL

@@ -29,13 +29,14 @@ EXPORTS = (
     "cd_stats_get", "cd_heating",
     "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_column_density_noalloc", "cd_device_status",
     "cd_column_density_batch", "cd_batch_create", "cd_batch_run", "cd_batch_info", "cd_batch_free",
+    "cd_debug_wait_polls", "cd_stats_flops",
     # include/colden_learned.h
     "cd_adam_default", "cd_net_num_params", "cd_raymarch", "cd_learned_features", "cd_learned_targets",
     "cd_net_create", "cd_net_fit_normaliser", "cd_net_forward", "cd_net_loss_grad", "cd_net_train_step",
     "cd_net_get_state", "cd_net_set_state", "cd_net_info", "cd_net_free",
 )
 _VOID = ("cd_opts_default", "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_stats_reset", "cd_batch_free",
-         "cd_adam_default", "cd_net_free", "cd_net_num_params")
+         "cd_adam_default", "cd_net_free", "cd_net_num_params", "cd_debug_wait_polls")
 K_RESTRICT, K_SHELL, K_LEAF, K_OTHER, K_NET, K_FEATURES, K_RAYMARCH, K_LEARNED, K_HEATING = range(9)
 KERNEL_KINDS = ("restrict", "shell", "leaf", "other", "net", "features", "raymarch", "learned", "heating")
 
@@ -84,10 +85,13 @@ def load(build_if_missing: bool = False):
     L.cd_stats_reset.argtypes = [I]
     L.cd_stats_reset.restype = None
     L.cd_stats_get.argtypes = [I, ctypes.POINTER(I64), ctypes.POINTER(D)]
+    L.cd_stats_flops.argtypes = [I, ctypes.POINTER(D)]
     L.cd_precompute_geometry.argtypes = [I, I, I, P, I, I, P, ctypes.POINTER(P)]
     L.cd_column_density.argtypes = [P, P, ctypes.POINTER(Opts), P, P, P, P]
     L.cd_column_density_noalloc.argtypes = [P, P, ctypes.POINTER(Opts), P, P, P, P]
     L.cd_device_status.argtypes = [P]
+    L.cd_debug_wait_polls.argtypes = [I64]
+    L.cd_debug_wait_polls.restype = None
     L.cd_column_density_batch.argtypes = [I, P, P, ctypes.POINTER(Opts), P, P, P, P]
     L.cd_batch_create.argtypes = [I, P, P, ctypes.POINTER(Opts), P, P, P, P, ctypes.POINTER(P)]
     L.cd_batch_run.argtypes = [P, P]
@@ -143,12 +147,31 @@ def _stream_ptr(stream) -> Optional[int]:
     return stream.cuda_stream
 
 
-def _dptr(t):
+def _dptr(t, numel=None, device=None, name="buffer"):
+    """Device pointer of a contiguous float32 CUDA tensor (or None).  Raises
+    ValueError, before anything is enqueued, when the tensor has the wrong
+    type, holds fewer than `numel` elements or lives on another device than
+    `device` (the tree's)."""
+    return _checked_ptr(t, "float32", numel, device, name)
+
+
+def _checked_ptr(t, dtype_name, numel, device, name):
     if t is None:
         return None
     import torch
-    assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and t.dtype == torch.float32
+    dtype = getattr(torch, dtype_name)
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous %s CUDA tensor" % (name, dtype_name))
+    if numel is not None and t.numel() < numel:
+        raise ValueError("%s holds %d elements but %d are needed" % (name, t.numel(), numel))
+    if device is not None and t.device.index != device:
+        raise ValueError("%s is on cuda:%s but the tree is on cuda:%s" % (name, t.device.index, device))
     return t.data_ptr()
+
+
+def _current_device():
+    import torch
+    return torch.cuda.current_device()
 
 
 def opts_default() -> Opts:
@@ -167,6 +190,7 @@ class Tree:
         _check(load().cd_tree_info(self._h, ctypes.byref(n_leaf), ctypes.byref(lmax), ctypes.byref(base),
                                    ctypes.byref(n_oct)))
         self.n_leaf, self.max_level, self.base_level, self.n_oct = n_leaf.value, lmax.value, base.value, n_oct.value
+        self.device = _current_device()   # trees live on the device current at build time
 
     @property
     def handle(self):
@@ -231,8 +255,7 @@ def build_tree_uniform(rho, box_cm: float, stream=None) -> Tree:
     tensor (device path) or a numpy array / CPU tensor (host path)."""
     import torch
     if isinstance(rho, torch.Tensor) and rho.is_cuda:
-        assert rho.dtype == torch.float32 and rho.is_contiguous()
-        ptr, on_dev, keep = rho.data_ptr(), 1, rho
+        ptr, on_dev, keep = _dptr(rho, name="rho"), 1, rho
     else:
         keep = np.ascontiguousarray(rho.cpu().numpy() if isinstance(rho, torch.Tensor) else rho, dtype=np.float32)
         ptr, on_dev = keep.ctypes.data, 0
@@ -253,12 +276,16 @@ def build_tree_amr(base_level: int, max_level: int, box_cm: float, level, ijk, r
     lv = np.ascontiguousarray(level, dtype=np.int8).reshape(-1)
     ix = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
     if isinstance(rho, torch.Tensor) and rho.is_cuda:
-        assert rho.dtype == torch.float32 and rho.is_contiguous() and rho.numel() == lv.shape[0]
-        ptr, on_dev = rho.data_ptr(), 1
+        if rho.numel() != lv.shape[0]:
+            raise ValueError("rho holds %d values for %d leaves" % (rho.numel(), lv.shape[0]))
+        ptr, on_dev = _dptr(rho, name="rho"), 1
     else:
         keep = np.ascontiguousarray(rho.cpu().numpy() if isinstance(rho, torch.Tensor) else rho, dtype=np.float32)
-        assert keep.size == lv.shape[0]
+        if keep.size != lv.shape[0]:
+            raise ValueError("rho holds %d values for %d leaves" % (keep.size, lv.shape[0]))
         ptr, on_dev = keep.ctypes.data, 0
+    if ix.shape[0] != lv.shape[0]:
+        raise ValueError("ijk holds %d rows for %d leaves" % (ix.shape[0], lv.shape[0]))
     h = ctypes.c_void_p()
     _check(load().cd_build_tree_amr(int(base_level), int(max_level), float(box_cm), lv.shape[0],
                                     lv.ctypes.data_as(ctypes.c_void_p), ix.ctypes.data_as(ctypes.c_void_p),
@@ -271,11 +298,13 @@ def tree_update(tree: Tree, rho, stream=None) -> Tree:
     """cd_tree_update: new leaf densities for an existing uniform tree."""
     import torch
     if isinstance(rho, torch.Tensor) and rho.is_cuda:
-        assert rho.dtype == torch.float32 and rho.is_contiguous() and rho.numel() == tree.n_leaf
-        ptr, on_dev = rho.data_ptr(), 1
+        if rho.numel() != tree.n_leaf:
+            raise ValueError("rho holds %d values for %d leaves" % (rho.numel(), tree.n_leaf))
+        ptr, on_dev = _dptr(rho, device=tree.device, name="rho"), 1
     else:
         keep = np.ascontiguousarray(rho.cpu().numpy() if isinstance(rho, torch.Tensor) else rho, dtype=np.float32)
-        assert keep.size == tree.n_leaf
+        if keep.size != tree.n_leaf:
+            raise ValueError("rho holds %d values for %d leaves" % (keep.size, tree.n_leaf))
         ptr, on_dev = keep.ctypes.data, 0
     _check(load().cd_tree_update(tree.handle, ctypes.c_void_p(ptr), on_dev, ctypes.c_void_p(_stream_ptr(stream))))
     return tree
@@ -286,8 +315,22 @@ def device_status(stream=None):
     _check(load().cd_device_status(ctypes.c_void_p(_stream_ptr(stream))))
 
 
+def debug_wait_polls(polls: int):
+    """cd_debug_wait_polls (tests only): cap the BF16 leaf kernel's pipeline
+    waits at `polls` polls (0: they give up at once); negative restores the
+    default."""
+    load().cd_debug_wait_polls(int(polls))
+
+
 def stats_reset(timing: bool = False):
     load().cd_stats_reset(1 if timing else 0)
+
+
+def stats_flops(kind: int) -> float:
+    """Dense tensor-core flops issued by one kernel kind since the last reset."""
+    f = ctypes.c_double()
+    _check(load().cd_stats_flops(int(kind), ctypes.byref(f)))
+    return f.value
 
 
 def stats_get(kind: int):
@@ -324,9 +367,19 @@ def column_density(tree: Tree, geom: Geometry, n_h=None, a_v=None, shield=None, 
     o.precision = int(precision)
     o.av_per_nh = float(av_per_nh)
     o.shield_k = float(shield_k)
-    _check(load().cd_column_density(tree.handle, geom.handle, ctypes.byref(o), _dptr(n_h), _dptr(a_v),
-                                    _dptr(shield), ctypes.c_void_p(_stream_ptr(stream))))
+    ptrs = _outputs(tree, geom, n_h, a_v, shield)
+    _check(load().cd_column_density(tree.handle, geom.handle, ctypes.byref(o), *ptrs,
+                                    ctypes.c_void_p(_stream_ptr(stream))))
     return n_h, a_v, shield
+
+
+def _outputs(tree: Tree, geom: Geometry, n_h, a_v, shield, box=None):
+    """Checked device pointers of one box's outputs: n_h and a_v need
+    n_leaf * n_dir floats, shield n_leaf, all on the tree's device."""
+    tag = "" if box is None else " of box %d" % box
+    nd = tree.n_leaf * geom.n_dir
+    return (_dptr(n_h, nd, tree.device, "n_h" + tag), _dptr(a_v, nd, tree.device, "a_v" + tag),
+            _dptr(shield, tree.n_leaf, tree.device, "shield" + tag))
 
 
 def heating(tree: Tree, chi, T=None, n_e=None, G0: float = 1.7, g0_eff=None, gamma_uv=None, gamma_cr=None,
@@ -334,8 +387,10 @@ def heating(tree: Tree, chi, T=None, n_e=None, G0: float = 1.7, g0_eff=None, gam
     """cd_heating: G0_eff = chi G0, the photoelectric rate (needs T and n_e)
     and the cosmic-ray rate per leaf, into caller-owned CUDA float32 tensors
     (any may be None)."""
-    _check(load().cd_heating(tree.handle, _dptr(chi), _dptr(T), _dptr(n_e), float(G0), _dptr(g0_eff),
-                             _dptr(gamma_uv), _dptr(gamma_cr), ctypes.c_void_p(_stream_ptr(stream))))
+    n, dev = tree.n_leaf, tree.device
+    ins = [_dptr(v, n, dev, k) for k, v in (("chi", chi), ("T", T), ("n_e", n_e))]
+    outs = [_dptr(v, n, dev, k) for k, v in (("g0_eff", g0_eff), ("gamma_uv", gamma_uv), ("gamma_cr", gamma_cr))]
+    _check(load().cd_heating(tree.handle, *ins, float(G0), *outs, ctypes.c_void_p(_stream_ptr(stream))))
     return g0_eff, gamma_uv, gamma_cr
 
 
@@ -349,8 +404,9 @@ def column_density_noalloc(tree: Tree, geom: Geometry, n_h=None, a_v=None, shiel
     o.precision = FP32
     o.av_per_nh = float(av_per_nh)
     o.shield_k = float(shield_k)
-    _check(load().cd_column_density_noalloc(tree.handle, geom.handle, ctypes.byref(o), _dptr(n_h), _dptr(a_v),
-                                            _dptr(shield), ctypes.c_void_p(_stream_ptr(stream))))
+    ptrs = _outputs(tree, geom, n_h, a_v, shield)
+    _check(load().cd_column_density_noalloc(tree.handle, geom.handle, ctypes.byref(o), *ptrs,
+                                            ctypes.c_void_p(_stream_ptr(stream))))
     return n_h, a_v, shield
 
 
@@ -361,10 +417,21 @@ def _ptr_array(items, get):
     return arr
 
 
-def _out_array(ts, n):
-    if ts is None:
-        return None
-    return _ptr_array(ts, lambda t: _dptr(t) if t is not None else None)
+def _batch_outputs(trees, geoms, n_h, a_v, shield):
+    """Per-box checked pointer arrays (ctypes) for the batch entry points, or
+    None where the caller gives no list."""
+    n = len(trees)
+    if len(geoms) != n:
+        raise ValueError("%d trees but %d geometries" % (n, len(geoms)))
+    for name, ts in (("n_h", n_h), ("a_v", a_v), ("shield", shield)):
+        if ts is not None and len(ts) != n:
+            raise ValueError("%s lists %d buffers for %d boxes" % (name, len(ts), n))
+    cols = [[None] * n, [None] * n, [None] * n]
+    for i in range(n):
+        pick = lambda ts: ts[i] if ts is not None else None
+        for j, p in enumerate(_outputs(trees[i], geoms[i], pick(n_h), pick(a_v), pick(shield), box=i)):
+            cols[j][i] = p
+    return tuple(None if ts is None else _ptr_array(c, lambda p: p) for ts, c in zip((n_h, a_v, shield), cols))
 
 
 def column_density_batch(trees, geoms, n_h=None, a_v=None, shield=None, precision: int = FP32,
@@ -373,10 +440,10 @@ def column_density_batch(trees, geoms, n_h=None, a_v=None, shield=None, precisio
     n = len(trees)
     o = opts_default()
     o.precision, o.av_per_nh, o.shield_k = int(precision), float(av_per_nh), float(shield_k)
+    outs = _batch_outputs(trees, geoms, n_h, a_v, shield)
     _check(load().cd_column_density_batch(n, _ptr_array(trees, lambda t: t.handle.value),
                                           _ptr_array(geoms, lambda g: g.handle.value), ctypes.byref(o),
-                                          _out_array(n_h, n), _out_array(a_v, n), _out_array(shield, n),
-                                          ctypes.c_void_p(_stream_ptr(stream))))
+                                          *outs, ctypes.c_void_p(_stream_ptr(stream))))
 
 
 class Batch:
@@ -388,11 +455,11 @@ class Batch:
         n = len(trees)
         o = opts_default()
         o.precision, o.av_per_nh, o.shield_k = int(precision), float(av_per_nh), float(shield_k)
+        outs = _batch_outputs(trees, geoms, n_h, a_v, shield)
         h = ctypes.c_void_p()
         _check(load().cd_batch_create(n, _ptr_array(trees, lambda t: t.handle.value),
                                       _ptr_array(geoms, lambda g: g.handle.value), ctypes.byref(o),
-                                      _out_array(n_h, n), _out_array(a_v, n), _out_array(shield, n),
-                                      ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
+                                      *outs, ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
         self._h = h
 
     def run(self, stream=None):
@@ -424,13 +491,10 @@ class Batch:
 SLOTS = 8
 
 
-def _iptr(t):
-    """Device pointer of an int64 CUDA tensor (or None)."""
-    if t is None:
-        return None
-    import torch
-    assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and t.dtype == torch.int64
-    return t.data_ptr()
+def _iptr(t, numel=None, device=None, name="index buffer"):
+    """Device pointer of a contiguous int64 CUDA tensor (or None); raises
+    ValueError as _dptr does."""
+    return _checked_ptr(t, "int64", numel, device, name)
 
 
 def net_num_params(n_dir: int, hidden: int) -> int:
@@ -447,7 +511,8 @@ def raymarch(tree: Tree, geom: Geometry, n_ray, leaves=None, stream=None):
     """cd_raymarch: exact columns [n, n_dir] from the centres of `leaves`
     (int64 CUDA tensor, or None for the first n_ray.shape[0] leaves)."""
     n = n_ray.shape[0]
-    _check(load().cd_raymarch(tree.handle, geom.handle, n, _iptr(leaves), _dptr(n_ray),
+    _check(load().cd_raymarch(tree.handle, geom.handle, n, _iptr(leaves, n, tree.device, "leaves"),
+                              _dptr(n_ray, n * geom.n_dir, tree.device, "n_ray"),
                               ctypes.c_void_p(_stream_ptr(stream))))
     return n_ray
 
@@ -456,15 +521,19 @@ def learned_features(tree: Tree, geom: Geometry, x, n_tree=None, leaves=None, st
     """cd_learned_features: network inputs x [n, 8 n_dir + 1] and (optionally)
     the plain column n_tree [n, n_dir] of `leaves` (None: the first n)."""
     n = x.shape[0]
-    _check(load().cd_learned_features(tree.handle, geom.handle, n, _iptr(leaves), _dptr(x), _dptr(n_tree),
+    dev = tree.device
+    _check(load().cd_learned_features(tree.handle, geom.handle, n, _iptr(leaves, n, dev, "leaves"),
+                                      _dptr(x, n * (SLOTS * geom.n_dir + 1), dev, "x"),
+                                      _dptr(n_tree, n * geom.n_dir, dev, "n_tree"),
                                       ctypes.c_void_p(_stream_ptr(stream))))
     return x, n_tree
 
 
 def learned_targets(n_ray, n_tree, y, stream=None):
     """cd_learned_targets: y = ln(n_ray / n_tree)."""
-    _check(load().cd_learned_targets(n_ray.numel(), _dptr(n_ray), _dptr(n_tree), _dptr(y),
-                                     ctypes.c_void_p(_stream_ptr(stream))))
+    n = n_ray.numel()
+    _check(load().cd_learned_targets(n, _dptr(n_ray, n, None, "n_ray"), _dptr(n_tree, n, None, "n_tree"),
+                                     _dptr(y, n, None, "y"), ctypes.c_void_p(_stream_ptr(stream))))
     return y
 
 

@@ -721,6 +721,8 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
     const int nd = g->n_dir, L = t->L;
     // workspace: S_k over the refined cells of levels 3 .. L-2, E over all octs
     if (t->ws.ndir != nd) {
+        const cd_status pin = check_workspace_pinned(t, nd);
+        if (pin != CD_OK) return pin;
         for (int k = 0; k <= CD_MAXL; ++k) {
             if (t->ws.S[k]) cudaFree(t->ws.S[k]);
             t->ws.S[k] = nullptr;

@@ -44,9 +44,20 @@ static void free_workspace(cd_tree t)
     t->ws.ndir = 0;
 }
 
+cd_status check_workspace_pinned(cd_tree t, int nd)
+{
+    if (t->ws.ndir == nd || t->batch_refs == 0) return CD_OK;
+    set_error("the tree's scratch is sized for %d directions and held by %d live batch object(s); an evaluation "
+              "with %d directions would reallocate it under the batch's graph (free the batch first)",
+              t->ws.ndir, t->batch_refs, nd);
+    return CD_EINVAL;
+}
+
 static cd_status ensure_workspace(cd_tree t, int nd)
 {
     if (t->ws.ndir == nd) return CD_OK;
+    cd_status pin = check_workspace_pinned(t, nd);
+    if (pin != CD_OK) return pin;
     free_workspace(t);
     for (int k = 3; k <= t->L - 2; ++k) {
         const size_t bytes = sizeof(float) * ((size_t)1 << (3 * k)) * nd;
@@ -505,6 +516,8 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
     }
     return launch_leaf(b, s);
 }
+
+void cd_debug_wait_polls(int64_t polls) { set_leaf_tc_wait_polls(polls); }
 
 cd_status cd_device_status(void *stream)
 {

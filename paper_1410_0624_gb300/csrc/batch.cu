@@ -11,7 +11,9 @@
 // the whole batch with independent boxes overlapping on the GPU.  The graph
 // reads the trees' current densities at every replay (cd_tree_update between
 // replays is seen), but it holds the trees, geometries and output pointers
-// given at creation: they must outlive the batch.
+// given at creation: they must outlive the batch.  While a batch lives, its
+// trees' scratch is pinned: an evaluation that would reallocate it (another
+// direction count) returns CD_EINVAL.
 #include <algorithm>
 #include <numeric>
 #include <vector>
@@ -31,6 +33,7 @@ struct cd_batch_s {
     std::vector<cudaStream_t> streams;       // W - 1 side streams
     std::vector<cudaEvent_t> events;
     int64_t kernel_nodes = 0;
+    bool pinned = false;                     // batch_refs of the distinct trees were raised
 };
 
 namespace cd {
@@ -73,6 +76,10 @@ cd_status enqueue(cd_batch_s &b, int W, cudaStream_t s)
 
 void destroy(cd_batch_s *b)
 {
+    if (b->pinned)
+        for (size_t i = 0; i < b->trees.size(); ++i)
+            if (std::find(b->trees.begin(), b->trees.begin() + i, b->trees[i]) == b->trees.begin() + i)
+                --b->trees[i]->batch_refs;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (auto s : b->streams) cudaStreamDestroy(s);
@@ -111,6 +118,21 @@ cd_status cd_batch_create(int n, const cd_tree *trees, const cd_geom *geoms, con
         return CD_EINVAL;
     }
     *out = nullptr;
+    if (opts && opts->net) {
+        // the learned form caches per-level sums between calls and skips their
+        // launches when the densities have not changed, so a captured graph
+        // would replay stale sums after cd_tree_update
+        set_error("batches evaluate the plain tree method; call cd_column_density_batch for the learned form");
+        return CD_EUNSUPPORTED;
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j)
+            if (trees[i] && trees[i] == trees[j] && geoms[i] && geoms[j] && geoms[i]->n_dir != geoms[j]->n_dir) {
+                // one scratch per tree: the graph would hold the one sized last
+                set_error("batch entries %d and %d share a tree with %d and %d directions", j, i, geoms[j]->n_dir,
+                          geoms[i]->n_dir);
+                return CD_EINVAL;
+            }
     cd_batch_s *b = new cd_batch_s();
     if (opts) b->opts = *opts; else cd_opts_default(&b->opts);
     for (int i = 0; i < n; ++i) {
@@ -225,6 +247,11 @@ cd_status cd_batch_create(int n, const cd_tree *trees, const cd_geom *geoms, con
         set_error("batch tuning failed: %s", cudaGetErrorString(cudaGetLastError()));
         return CD_ECUDA;
     }
+    // the graph now holds every tree's scratch pointers: pin them
+    for (size_t i = 0; i < b->trees.size(); ++i)
+        if (std::find(b->trees.begin(), b->trees.begin() + i, b->trees[i]) == b->trees.begin() + i)
+            ++b->trees[i]->batch_refs;
+    b->pinned = true;
     *out = b;
     return CD_OK;
 }

@@ -11,7 +11,10 @@
 // and then call this entry point every step.
 //
 // The scratch array is 16 MiB.  Every GPU that loads the library holds it
-// until the process exits.
+// until the process exits.  The module holding it is loaded on a device the
+// first time its address is looked up there (lazy module loading), which is
+// the first call of this entry point on that device, outputs or not: callers
+// make that call during set-up.
 #include <mutex>
 
 #include "common.cuh"
@@ -74,6 +77,11 @@ extern "C" cd_status cd_column_density_noalloc(cd_tree tree, cd_geom geom, const
         set_error("cd_column_density_noalloc serves uniform trees in the precalculated form without a learned correction");
         return CD_EUNSUPPORTED;
     }
+    // the lookup loads this file's module (and its array) on the device, so a
+    // set-up call with no outputs already takes the 16 MiB
+    float *base = nullptr;
+    cd_status st = scratch_address(&base);
+    if (st != CD_OK) return st;
     if (!n_h && !a_v && !shield) return CD_OK;
     const int nd = geom->n_dir, L = tree->L;
 
@@ -92,10 +100,6 @@ extern "C" cd_status cd_column_density_noalloc(cd_tree tree, cd_geom geom, const
                   need, need * 4.0 / (1 << 20), kScratchFloats);
         return CD_EINVAL;
     }
-    float *base = nullptr;
-    cd_status st = scratch_address(&base);
-    if (st != CD_OK) return st;
-
     // Every scratch element the kernels read is written earlier in this call,
     // so nothing needs clearing between calls.
     cudaStream_t s = (cudaStream_t)stream;

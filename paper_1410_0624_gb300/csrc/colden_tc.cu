@@ -486,7 +486,8 @@ cd_status launch_ext_tc(const ExtLaunch &a, const __nv_bfloat16 *const *brick, c
     const int64_t grid = a.tiles_per_cta > 0 ? (P.ntiles + a.tiles_per_cta - 1) / a.tiles_per_cta
                                              : std::min<int64_t>(P.ntiles, 2 * (int64_t)num_sms());
     {
-        LaunchScope ls(CD_K_SHELL, s);
+        // every tile runs its chunks' MMAs over 128 rows and Nt columns, K = 48 a chunk
+        LaunchScope ls(CD_K_SHELL, s, 2.0 * (double)P.ntiles * 128.0 * (P.c1 - P.c0) * (kChunkBricks * 8) * P.Nt);
         shell_sum_tc<<<(unsigned)grid, kThreads, smem, s>>>(P);
     }
     CD_CHECK_LAUNCH();

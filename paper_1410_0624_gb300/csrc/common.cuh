@@ -155,6 +155,9 @@ struct cd_tree_s {
     cudaStream_t side[2] = {};
     cudaEvent_t ev_fork = nullptr, ev_done[2] = {};
     cudaEvent_t ev_S[CD_MAXL + 1] = {}, ev_E[CD_MAXL + 1] = {};
+    // live cd_batch objects whose graph holds this tree's scratch pointers:
+    // while it is non-zero an evaluation must not reallocate the scratch
+    int batch_refs = 0;
 };
 
 struct cd_geom_s {
@@ -185,10 +188,12 @@ struct cd_geom_s {
 namespace cd {
 
 // stats.cu: counts (and optionally times) one kernel launch on stream s for
-// the lifetime of the scope; construct it right before the launch.
+// the lifetime of the scope; construct it right before the launch.  flops:
+// the dense tensor-core work the launch issues (2 M N K per MMA, padding
+// included), 0 for CUDA-core kernels.
 class LaunchScope {
   public:
-    LaunchScope(int kind, cudaStream_t s);
+    LaunchScope(int kind, cudaStream_t s, double flops = 0.0);
     ~LaunchScope();
     LaunchScope(const LaunchScope &) = delete;
     LaunchScope &operator=(const LaunchScope &) = delete;
@@ -228,6 +233,11 @@ class SideFork {
     bool joined_ = false;
     bool serial_ = false;
 };
+
+// api.cu: CD_EINVAL (with a message) when the tree's scratch, sized for
+// ws.ndir directions, would have to be reallocated for nd while a batch graph
+// holds its pointers
+cd_status check_workspace_pinned(cd_tree t, int nd);
 
 // tree.cu
 cd_status restrict_uniform(cd_tree t, const float *rho_dev, cudaStream_t s);
@@ -289,6 +299,8 @@ cd_status leaf_fault_check();
 // cores; CD_EUNSUPPORTED (no error text) when the sizes do not fit it
 cd_status launch_leaf_tc(const LeafLaunch &a, cudaStream_t s);
 cd_status leaf_tc_fault_check();
+// cd_debug_wait_polls: poll limit of the BF16 leaf kernel's pipeline waits (< 0: default)
+void set_leaf_tc_wait_polls(int64_t polls);
 
 // colden_tc.cu: BF16 tensor-core shell contraction for receiving levels >= 4
 bool tc_supported(int nd);

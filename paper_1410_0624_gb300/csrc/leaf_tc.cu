@@ -19,6 +19,7 @@
 // one group's epilogue overlaps another's MMA.  Every wait is bounded; a
 // timeout sets a device flag (cd_device_status).
 #include <algorithm>
+#include <atomic>
 
 #include "common.cuh"
 #include "umma.cuh"
@@ -30,6 +31,8 @@ constexpr uint32_t kMaxPolls = 1u << 26;
 constexpr int kK = 64;                  // 8 octant blocks x 8 siblings
 
 static __device__ int g_leaftc_fault;
+// cd_debug_wait_polls: < 0 = the default limit
+static std::atomic<int64_t> g_pipe_polls{-1};
 
 __host__ __device__ constexpr size_t align128(size_t v) { return (v + 127) & ~(size_t)127; }
 __host__ __device__ constexpr int round16(int v) { return (v + 15) & ~15; }
@@ -46,6 +49,8 @@ struct LeafTcArgs {
     float c2;                  // -shield_k av_per_nh log2(e)
     int out_bulk;              // n_h is 16-byte aligned: tile rows leave by bulk copies
     int list;                  // AMR list mode (a.oleaf): tiles of 16 octs, rows scattered
+    uint32_t pipe_polls;       // poll limit of the pipeline waits (cd_debug_wait_polls); the exit
+                               // waits for the CTA's own copies and products keep kMaxPolls
 };
 
 struct LeafTcSmem {
@@ -175,10 +180,15 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
                 prefetch<kList>(P, S, tile + stride, Gb + S.stage + (stg ^ 1) * S.stage_bytes, &bar[G + 2 * g + (stg ^ 1)]);
                 pending[stg ^ 1] = true;
             }
-            if (mbar_wait_bounded(&bar[G + 2 * g + stg], sphase[stg], kMaxPolls)) pending[stg] = false;
-            else sflag[g] = 1;
+            // the phase bit advances only once the copy has landed: after a
+            // timeout the exit below still waits for this stage's copy
+            if (mbar_wait_bounded(&bar[G + 2 * g + stg], sphase[stg], P.pipe_polls)) {
+                pending[stg] = false;
+                sphase[stg] ^= 1;
+            } else {
+                sflag[g] = 1;
+            }
         }
-        sphase[stg] ^= 1;
         named_barrier(bid, 128);
         if (sflag[g]) {
             fault = true;
@@ -203,7 +213,7 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
                 umma_bf16(tD, umma_smem_desc(a0 + ks * 256, 128, kK * 16), umma_smem_desc(b0 + ks * 256, 128, kK * 16),
                           idesc, ks > 0 ? 1u : 0u);
             umma_commit(&bar[g]);
-            if (!mbar_wait_bounded(&bar[g], phase, kMaxPolls)) sflag[g] = 1;
+            if (!mbar_wait_bounded(&bar[g], phase, P.pipe_polls)) sflag[g] = 1;
             // the previous tile's rows must have left the output buffer
             if (P.out_bulk && !kList) bulk_wait_read<0>();
         }
@@ -336,6 +346,10 @@ cd_status launch_leaf_tc(const LeafLaunch &a, cudaStream_t s)
     P.ntiles = (a.n_oct + 15) / 16;
     P.c2 = (float)(-(double)a.shield_k * (double)a.av_per_nh * 1.4426950408889634);
     P.out_bulk = a.n_h && aligned16(a.n_h);
+    {
+        const int64_t cap = g_pipe_polls.load();
+        P.pipe_polls = cap < 0 ? kMaxPolls : (uint32_t)std::min<int64_t>(cap, kMaxPolls);
+    }
     int dev = 0, smax = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -346,11 +360,13 @@ cd_status launch_leaf_tc(const LeafLaunch &a, cudaStream_t s)
     const auto kern = list ? leaf_tc<true> : leaf_tc<false>;
     CD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t grid = std::min<int64_t>((P.ntiles + P.G - 1) / P.G, sms());
-    LaunchScope ls(CD_K_LEAF, s);
+    LaunchScope ls(CD_K_LEAF, s, 2.0 * (double)P.ntiles * 128.0 * kK * P.NP);
     kern<<<(unsigned)grid, 128 * P.G, smem, s>>>(P);
     CD_CHECK_LAUNCH();
     return CD_OK;
 }
+
+void set_leaf_tc_wait_polls(int64_t polls) { g_pipe_polls.store(polls < 0 ? -1 : polls); }
 
 cd_status leaf_tc_fault_check()
 {

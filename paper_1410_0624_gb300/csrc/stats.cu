@@ -18,6 +18,7 @@ struct Pending {
 std::mutex g_mu;
 int64_t g_count[CD_K_COUNT] = {};
 double g_ms[CD_K_COUNT] = {};
+double g_flops[CD_K_COUNT] = {};
 bool g_timing = false;
 std::vector<Pending> g_pending;
 std::vector<cudaEvent_t> g_pool;
@@ -54,10 +55,11 @@ bool stats_timing()
     return g_timing;
 }
 
-LaunchScope::LaunchScope(int kind, cudaStream_t s) : kind_(kind), s_(s)
+LaunchScope::LaunchScope(int kind, cudaStream_t s, double flops) : kind_(kind), s_(s)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     ++g_count[kind];
+    g_flops[kind] += flops;
     if (g_timing) {
         a_ = take_event();
         b_ = take_event();
@@ -84,6 +86,7 @@ void cd_stats_reset(int timing)
     for (int k = 0; k < CD_K_COUNT; ++k) {
         cd::g_count[k] = 0;
         cd::g_ms[k] = 0.0;
+        cd::g_flops[k] = 0.0;
     }
     cd::g_timing = timing != 0;
 }
@@ -98,6 +101,17 @@ cd_status cd_stats_get(int kind, int64_t *launches, double *ms)
     cd::drain();
     if (launches) *launches = cd::g_count[kind];
     if (ms) *ms = cd::g_ms[kind];
+    return CD_OK;
+}
+
+cd_status cd_stats_flops(int kind, double *flops)
+{
+    if (kind < 0 || kind >= CD_K_COUNT) {
+        cd::set_error("unknown kernel kind %d", kind);
+        return CD_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(cd::g_mu);
+    if (flops) *flops = cd::g_flops[kind];
     return CD_OK;
 }
 

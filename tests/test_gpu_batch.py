@@ -1,13 +1,25 @@
-"""Batched evaluation: per-box launches and the captured graph against
-per-box cd_column_density calls (bitwise: the same kernels on the same data)."""
+"""Batched evaluation (many independent boxes per call).
+
+Every box of a mixed batch (uniform and AMR meshes, 12 and 48 HEALPix
+directions) is compared with the FP64 oracle of the tree method (§3.2, §3.3,
+Eqs. N_discret1 and N_discret) on seeded samples of its leaves, for the
+per-box launches and for the captured graph, in FP32 (1e-5 relative on N_H,
+1e-5 absolute on the screening factor) and BF16 (1e-2 relative, 5e-3 absolute;
+the tolerances of the single-box parity tests).  The batch paths must also be
+bitwise equal to per-box cd_column_density calls (the same kernels on the same
+data), see density updates between graph replays, and refuse the requests that
+would leave a captured graph pointing at reallocated scratch."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1410_0624_gb300 import colden, synth
 
 PC = synth.PC_CM
+BOX = 10 * PC
 pytestmark = pytest.mark.gpu
+TOL = {colden.FP32: (1e-5, 1e-5), colden.BF16: (1e-2, 5e-3)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -15,25 +27,32 @@ def _lib():
     colden.load(build_if_missing=True)
 
 
+# (kind, size, directions): uniform boxes of 2^size per axis, AMR boxes on a
+# base of size / 4 per axis with two refined levels
+SPECS = [("u", 3, 48), ("u", 4, 12), ("a", 16, 12), ("u", 5, 48), ("a", 32, 48), ("u", 6, 12), ("u", 4, 48)]
+
+
 def _boxes(seed=0):
-    """Uneven boxes: uniform 8^3 .. 64^3 and AMR meshes, 12 or 48 directions."""
+    """Uneven boxes; returns trees, geometries, flat leaf densities (the
+    caller's order) and the oracle's view of each box."""
     rng = np.random.default_rng(seed)
-    specs = [("u", 3, 48), ("u", 4, 12), ("a", 16, 12), ("u", 5, 48), ("a", 32, 48), ("u", 6, 12), ("u", 4, 48)]
-    trees, geoms, rhos = [], [], []
+    trees, geoms, rhos, srcs = [], [], [], []
     g12, g48 = colden.precompute_geometry("healpix", 1), colden.precompute_geometry("healpix", 2)
-    for kind, size, nd in specs:
+    for kind, size, nd in SPECS:
         sig = float(rng.uniform(1.0, 2.5))
         if kind == "u":
             rho = synth.lognormal_grf(1 << size, 30.0, sig, seed=int(rng.integers(1 << 30)))
-            trees.append(colden.build_tree_uniform(torch.from_numpy(rho).cuda(), 10 * PC))
+            trees.append(colden.build_tree_uniform(torch.from_numpy(rho).cuda(), BOX))
             rhos.append(rho.reshape(-1))
+            srcs.append(("u", rho))
         else:
             fine = synth.lognormal_grf(size, 30.0, sig, seed=int(rng.integers(1 << 30)))
             lv = synth.amr_leaves(fine, int(np.log2(size)) - 2, [60.0, 120.0])
-            trees.append(colden.build_tree_amr(lv["base"], lv["lmax"], 10 * PC, lv["level"], lv["ijk"], lv["rho"]))
+            trees.append(colden.build_tree_amr(lv["base"], lv["lmax"], BOX, lv["level"], lv["ijk"], lv["rho"]))
             rhos.append(lv["rho"])
+            srcs.append(("a", lv))
         geoms.append(g12 if nd == 12 else g48)
-    return trees, geoms, rhos
+    return trees, geoms, rhos, srcs
 
 
 def _outs(trees, geoms):
@@ -50,13 +69,49 @@ def _ref(trees, geoms, precision):
     return [x.cpu() for x in nh], [x.cpu() for x in sh]
 
 
+def _sample(tree, rng, n=48):
+    """Leaf rows to check: the first and last, every level's first leaf and a
+    seeded random set."""
+    lv, ijk = tree.leaves()
+    rows = {0, tree.n_leaf - 1}
+    for l in np.unique(lv):
+        rows.add(int(np.flatnonzero(lv == l)[0]))
+    rows.update(int(r) for r in rng.choice(tree.n_leaf, size=min(n, tree.n_leaf), replace=False))
+    rows = np.array(sorted(rows))
+    return rows, lv[rows], ijk[rows]
+
+
+def _oracle_rows(src, trees, geoms, rng):
+    """Oracle N_H of sampled leaves of every box: [(rows, N_H [rows, nd])]."""
+    out = []
+    for (kind, data), t, g in zip(src, trees, geoms):
+        T = oracle.Tree.uniform(data, BOX) if kind == "u" else \
+            oracle.Tree.amr(data["base"], data["lmax"], BOX, data["level"], data["ijk"], data["rho"])
+        rows, lv, ijk = _sample(t, rng)
+        dirs = oracle.dirs_healpix(1 if g.n_dir == 12 else 2)
+        out.append((rows, T.column_density(dirs, lv, ijk)))
+    return out
+
+
+def _check_oracle(nh, sh, ref_rows, geoms, precision, what):
+    rtol, satol = TOL[precision]
+    for b, ((rows, ref), a, s, g) in enumerate(zip(ref_rows, nh, sh, geoms)):
+        got = a.cpu().numpy().reshape(-1, g.n_dir)[rows].astype(np.float64)
+        rel = np.max(np.abs(got - ref) / ref)
+        dsh = np.max(np.abs(s.cpu().numpy()[rows] - oracle.shield(ref)))
+        assert rel <= rtol, "%s box %d (%s): max rel N_H error %.3g" % (what, b, SPECS[b], rel)
+        assert dsh <= satol, "%s box %d (%s): max shield error %.3g" % (what, b, SPECS[b], dsh)
+
+
 @pytest.mark.parametrize("precision", [colden.FP32, colden.BF16])
-def test_batch_eager_and_graph_equal_per_box(precision):
-    trees, geoms, rhos = _boxes()
+def test_batch_eager_and_graph_match_oracle_and_per_box(precision):
+    trees, geoms, rhos, srcs = _boxes()
+    ref_rows = _oracle_rows(srcs, trees, geoms, np.random.default_rng(7))
     rn, rs = _ref(trees, geoms, precision)
     nh, sh = _outs(trees, geoms)
     colden.column_density_batch(trees, geoms, n_h=nh, shield=sh, precision=precision)
     torch.cuda.synchronize()
+    _check_oracle(nh, sh, ref_rows, geoms, precision, "per-box launches")
     for a, b in zip(nh + sh, rn + rs):
         assert torch.equal(a.cpu(), b)
     nh2, sh2 = _outs(trees, geoms)
@@ -67,6 +122,7 @@ def test_batch_eager_and_graph_equal_per_box(precision):
         x.fill_(-1.0)
     batch.run()
     torch.cuda.synchronize()
+    _check_oracle(nh2, sh2, ref_rows, geoms, precision, "graph replay")
     for a, b in zip(nh2 + sh2, rn + rs):
         assert torch.equal(a.cpu(), b)
     colden.device_status()
@@ -74,7 +130,7 @@ def test_batch_eager_and_graph_equal_per_box(precision):
 
 
 def test_graph_replay_sees_updated_densities():
-    trees, geoms, rhos = _boxes(seed=1)
+    trees, geoms, rhos, srcs = _boxes(seed=1)
     nh, sh = _outs(trees, geoms)
     batch = colden.Batch(trees, geoms, n_h=nh, shield=sh)
     rng = np.random.default_rng(5)
@@ -87,4 +143,82 @@ def test_graph_replay_sees_updated_densities():
     rn, rs = _ref(trees, geoms, colden.FP32)
     for a, b in zip(got, rn + rs):
         assert torch.equal(a, b)
+    # the replayed columns are those of the new densities, per the oracle
+    src_new = []
+    for (kind, data), r in zip(srcs, new):
+        if kind == "u":
+            src_new.append(("u", r.reshape(data.shape)))
+        else:
+            d = dict(data)
+            d["rho"] = r
+            src_new.append(("a", d))
+    ref_rows = _oracle_rows(src_new, trees, geoms, np.random.default_rng(8))
+    _check_oracle(nh, sh, ref_rows, geoms, colden.FP32, "replay after update")
     batch.free()
+
+
+def test_batched_tree_scratch_is_pinned_while_the_batch_lives():
+    """A tree held by a live batch graph must not have its scratch reallocated
+    (another direction count): the call is refused, the batch still replays
+    correctly, and after the batch is freed the evaluation goes through."""
+    rho = synth.lognormal_grf(32, 30.0, 2.0, seed=3)
+    tree = colden.build_tree_uniform(torch.from_numpy(rho).cuda(), BOX)
+    g12, g48 = colden.precompute_geometry("healpix", 1), colden.precompute_geometry("healpix", 2)
+    nh = torch.empty(tree.n_leaf * 48, device="cuda")
+    ref = torch.empty_like(nh)
+    colden.column_density(tree, g48, n_h=ref)
+    batch = colden.Batch([tree], [g48], n_h=[nh])
+    other = torch.empty(tree.n_leaf * 12, device="cuda")
+    with pytest.raises(colden.ColdenError) as e:
+        colden.column_density(tree, g12, n_h=other)
+    assert e.value.code == colden.CD_EINVAL and "batch" in str(e.value)
+    # same direction count: no reallocation, allowed
+    colden.column_density(tree, g48, n_h=ref)
+    nh.fill_(-1.0)
+    batch.run()
+    torch.cuda.synchronize()
+    assert torch.equal(nh, ref)
+    batch.free()
+    colden.column_density(tree, g12, n_h=other)
+    torch.cuda.synchronize()
+    assert torch.all(other > 0)
+
+
+def test_batch_rejects_shared_tree_with_two_direction_counts_and_learned_form():
+    rho = synth.lognormal_grf(16, 30.0, 2.0, seed=4)
+    tree = colden.build_tree_uniform(torch.from_numpy(rho).cuda(), BOX)
+    g12, g48 = colden.precompute_geometry("healpix", 1), colden.precompute_geometry("healpix", 2)
+    with pytest.raises(colden.ColdenError) as e:
+        colden.Batch([tree, tree], [g12, g48],
+                     shield=[torch.empty(tree.n_leaf, device="cuda") for _ in range(2)])
+    assert e.value.code == colden.CD_EINVAL
+    # one tree twice with the same geometry is fine
+    b = colden.Batch([tree, tree], [g48, g48], shield=[torch.empty(tree.n_leaf, device="cuda") for _ in range(2)])
+    b.free()
+    params = synth.mlp_init(48, 128, seed=0)
+    net = colden.Net(48, 128, params)
+    L = colden.load()
+    o = colden.opts_default()
+    o.net = net.handle.value
+    trees = (colden.ctypes.c_void_p * 1)(tree.handle.value)
+    geoms = (colden.ctypes.c_void_p * 1)(g48.handle.value)
+    sh = torch.empty(tree.n_leaf, device="cuda")
+    shp = (colden.ctypes.c_void_p * 1)(sh.data_ptr())
+    h = colden.ctypes.c_void_p()
+    rc = L.cd_batch_create(1, trees, geoms, colden.ctypes.byref(o), None, None, shp, None, colden.ctypes.byref(h))
+    assert rc == colden.CD_EUNSUPPORTED and not h.value
+
+
+def test_batch_outputs_checked_before_launch():
+    rho = synth.lognormal_grf(16, 30.0, 2.0, seed=5)
+    tree = colden.build_tree_uniform(torch.from_numpy(rho).cuda(), BOX)
+    g48 = colden.precompute_geometry("healpix", 2)
+    short = torch.empty(tree.n_leaf * 48 - 1, device="cuda")
+    colden.stats_reset()
+    with pytest.raises(ValueError):
+        colden.column_density_batch([tree], [g48], n_h=[short])
+    with pytest.raises(ValueError):
+        colden.Batch([tree], [g48], n_h=[short])
+    with pytest.raises(ValueError):
+        colden.column_density(tree, g48, shield=torch.empty(tree.n_leaf - 1, device="cuda"))
+    assert all(colden.stats_get(k)[0] == 0 for k in range(len(colden.KERNEL_KINDS)))

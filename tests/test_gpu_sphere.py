@@ -23,6 +23,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1410_0624_gb300 import colden, synth
 
 PC = synth.PC_CM
@@ -92,22 +93,88 @@ def _pixel_cells(lmax=9):
     return cells
 
 
-def test_sphere_extinction_maps_vs_ray_marcher_table2():
-    box, R = 50 * PC, 12.5 * PC
-    fine = synth.sphere(512, box, R, 1000.0, 10.0)
+SETS = {6: ("axes", 0, 0), 12: ("mxn", 3, 4), 40: ("mxn", 5, 8), 84: ("mxn", 7, 12)}
+BOX, RADIUS = 50 * PC, 12.5 * PC
+
+
+def _oracle_dirs(scheme, p0, p1):
+    return oracle.dirs_axes() if scheme == "axes" else oracle.dirs_mxn(p0, p1)
+
+
+@pytest.fixture(scope="module")
+def sphere_mesh():
+    """The §4.1 cloud: the fine 512^3 field, its AMR leaves (base 128^3, two
+    refined levels where the block mean exceeds 10.5 cm^-3, i.e. every block
+    touching the sphere), the library's AMR tree and the uniform 512^3 tree the
+    ray-marcher walks."""
+    fine = synth.sphere(512, BOX, RADIUS, 1000.0, 10.0)
     lv = synth.amr_leaves(fine, 7, [10.5, 10.5])
+    tree = colden.build_tree_amr(7, 9, BOX, lv["level"], lv["ijk"], lv["rho"])
+    uni = colden.build_tree_uniform(torch.from_numpy(fine).cuda(), BOX)
+    return lv, tree, uni
+
+
+def test_sphere_mesh_columns_match_oracle(sphere_mesh):
+    """The tree-method columns of the spherical-cloud mesh (FP32, AMR lists)
+    and the exact ray-marcher's columns from the map's pixel cells, against the
+    FP64 oracle on the same mesh and the same M x N / axis direction sets of
+    Table 2: 1e-5 relative on N_H (the FP32 parity tolerance) and 2e-5 on the
+    ray-marcher (FP32 sums over up to 1.5 x 512 cell crossings).  Sampled: 300
+    pixel cells spread over the three midplanes, plus pixels at the sphere's
+    edge, where the maxima of Table 2 sit."""
+    lv, tree, uni = sphere_mesh
+    T = oracle.Tree.amr(lv["base"], lv["lmax"], BOX, lv["level"], lv["ijk"], lv["rho"])
+    olv, oijk = tree.leaves()
+    maps = _plane_maps(olv, oijk)
+    cells = _pixel_cells()
+    rng = np.random.default_rng(21)
+    half = 256
+    u, v = np.meshgrid(np.arange(512), np.arange(512), indexing="ij")
+    r_pix = np.hypot(u + 0.5 - half, v + 0.5 - half).reshape(-1)   # pixel distance (cells) from the sphere's axis
+    edge = np.flatnonzero(np.abs(r_pix - RADIUS / BOX * 512) < 1.0)
+    picks = []   # (plane, pixel)
+    for axis in range(3):
+        picks += [(axis, int(p)) for p in rng.choice(512 * 512, size=100, replace=False)]
+        picks += [(axis, int(p)) for p in rng.choice(edge, size=8, replace=False)]
+    leaf_rows = np.array([maps[a].reshape(-1)[p] for a, p in picks])
+    pix_keys = np.array([cells[a][p] for a, p in picks], dtype=np.uint64)
+    pix_ijk = np.stack([_compact(pix_keys >> np.uint64(q)) for q in range(3)], axis=1).astype(np.int32)
+    pix_lv = np.full(len(picks), 9, dtype=np.int32)
+    for ndir, (scheme, p0, p1) in SETS.items():
+        geom = colden.precompute_geometry(scheme, p0, p1)
+        dirs = _oracle_dirs(scheme, p0, p1)
+        n_h = torch.empty(tree.n_leaf * ndir, device="cuda")
+        colden.column_density(tree, geom, n_h=n_h, precision=colden.FP32)
+        got = n_h.reshape(-1, ndir)[torch.from_numpy(leaf_rows).cuda()].double().cpu().numpy()
+        ref = T.column_density(dirs, olv[leaf_rows], oijk[leaf_rows])
+        rel = np.max(np.abs(got - ref) / ref)
+        assert rel <= 1e-5, "%d directions: max rel N_H error %.3g vs the oracle" % (ndir, rel)
+        ray = torch.empty((len(picks), ndir), device="cuda")
+        colden.raymarch(uni, geom, ray, leaves=torch.from_numpy(pix_keys.astype(np.int64)).cuda())
+        ref_ray = T.raymarch(dirs, pix_lv, pix_ijk)
+        rel_ray = np.max(np.abs(ray.double().cpu().numpy() - ref_ray) / ref_ray)
+        assert rel_ray <= 2e-5, "%d directions: max rel ray-marcher error %.3g vs the oracle" % (ndir, rel_ray)
+        colden.device_status()
+
+
+def _compact(v):
+    v = np.asarray(v, dtype=np.uint64)
+    out = np.zeros_like(v)
+    for b in range(10):
+        out |= ((v >> np.uint64(3 * b)) & np.uint64(1)) << np.uint64(b)
+    return out
+
+
+def test_sphere_extinction_maps_vs_ray_marcher_table2(sphere_mesh):
+    lv, tree, uni = sphere_mesh
     counts = np.bincount(lv["level"], minlength=10)[7:]
     assert np.all(counts > 0)
-    tree = colden.build_tree_amr(7, 9, box, lv["level"], lv["ijk"], lv["rho"])
-    uni = colden.build_tree_uniform(torch.from_numpy(fine).cuda(), box)
-    del fine
     olv, oijk = tree.leaves()
     maps = [torch.from_numpy(m.reshape(-1)).cuda() for m in _plane_maps(olv, oijk)]
     cells = [torch.from_numpy(c).cuda() for c in _pixel_cells()]
     table = _table2()
     got = {}
-    for ndir, (scheme, p0, p1) in {6: ("axes", 0, 0), 12: ("mxn", 3, 4), 40: ("mxn", 5, 8),
-                                   84: ("mxn", 7, 12)}.items():
+    for ndir, (scheme, p0, p1) in SETS.items():
         geom = colden.precompute_geometry(scheme, p0, p1)
         n_h = torch.empty(tree.n_leaf * ndir, device="cuda")
         colden.column_density(tree, geom, n_h=n_h, precision=colden.FP32)

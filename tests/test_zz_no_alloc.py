@@ -52,6 +52,40 @@ def test_noalloc_matches_regular_entry_point_twice(L, nside):
         assert np.max(np.abs(g[2] - r[2])) <= SHIELD_ATOL
 
 
+def test_noalloc_allocates_nothing_per_call():
+    """The property the entry point exists for: once its set-up call (all
+    outputs NULL) has loaded the fixed array, calls on a fresh tree that never
+    went through cd_column_density leave the device's free memory unchanged
+    (the regular entry point would allocate the tree's scratch on its first
+    call: about 10 MB here), and their output matches the oracle."""
+    import oracle
+    L, box = 6, 10 * synth.PC_CM
+    geom = colden.precompute_geometry("healpix", 2)
+    nd = geom.n_dir
+    rho = synth.lognormal_grf(1 << L, 30.0, 2.0, seed=77)
+    tree = colden.build_tree_uniform(torch.from_numpy(rho).cuda(), box)
+    out = _outputs(tree, nd)
+    colden.column_density_noalloc(tree, geom)          # set-up call: no outputs
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        colden.column_density_noalloc(tree, geom, n_h=out[0], a_v=out[1], shield=out[2])
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    lv, ijk = tree.leaves()
+    rows = np.random.default_rng(9).choice(tree.n_leaf, size=200, replace=False)
+    ref = oracle.Tree.uniform(rho, box).column_density(oracle.dirs_healpix(2), lv[rows], ijk[rows])
+    got = out[0].reshape(-1, nd)[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+    assert np.max(np.abs(got - ref) / ref) <= RTOL
+    # the regular entry point on the same kind of fresh tree does allocate
+    tree2 = colden.build_tree_uniform(torch.from_numpy(rho).cuda(), box)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    colden.column_density(tree2, geom, n_h=out[0])
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] < free1
+
+
 def test_noalloc_rejects_trees_beyond_the_fixed_scratch():
     geom = colden.precompute_geometry("healpix", 2)
     rho = np.ones((128, 128, 128), np.float32)
