@@ -149,7 +149,7 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-# source file of each kernel kind (the BF16 form's leaf kernel lives in leaf_tc.cu)
+# source file of each kernel kind (the BF16 form.s leaf kernel lives in leaf_tc.cu)
 KERNEL_SOURCES = {"leaf": "leaf.cu", "leaf_tc": "leaf_tc.cu", "shell": "colden_tc.cu", "restrict": "tree.cu"}
 
 

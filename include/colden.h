@@ -297,8 +297,9 @@ cd_status cd_geom_rays(cd_geom geom, int *n_sub, double *rays);
 cd_status cd_device_status(void *stream);
 
 /* Testing hook of the failure detection above (no counterpart in the paper).
- * polls >= 0 caps the pipeline waits of the BF16 leaf kernel (its input
- * copies landing, its tensor-core product completing) at `polls` polls; with
+ * polls >= 0 caps the pipeline waits of the tensor-core leaf kernel (the
+ * BF16 leaf epilogue: its input copies landing, its product completing) at
+ * `polls` polls; with
  * 0 they give up at once, so every CTA takes the timeout path: it records the
  * flag, still waits (with the full limit) for the copies and products it has
  * issued, frees its tensor memory and returns, and cd_device_status then

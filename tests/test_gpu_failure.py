@@ -4,9 +4,11 @@ Every pipeline wait of the library's kernels is bounded: a wait that runs out
 sets a device flag, the kernel lets the copies and tensor-core products it has
 issued land (with the full limit), frees its tensor memory and returns, and
 cd_device_status reports CD_ETIMEOUT.  The testing hook cd_debug_wait_polls(0)
-makes the BF16 leaf kernel's pipeline waits give up without polling, so every
-CTA takes that path; nothing traps and the context stays usable: the flag is
-cleared by the report and the next evaluation matches the FP64 oracle."""
+makes the pipeline waits of the tensor-core leaf kernel (the BF16 leaf
+epilogue; here with 24 M x N directions) give up without polling, so every
+CTA takes that path; nothing
+traps and the context stays usable: the flag is cleared by the report and the
+next evaluation matches the FP64 oracle."""
 import numpy as np
 import pytest
 import torch
@@ -25,7 +27,7 @@ def _lib():
 
 def _oracle_check(tree, rho, n_h, sh, nd, rows):
     lv, ijk = tree.leaves()
-    ref = oracle.Tree.uniform(rho, BOX).column_density(oracle.dirs_healpix(2), lv[rows], ijk[rows])
+    ref = oracle.Tree.uniform(rho, BOX).column_density(oracle.dirs_mxn(4, 6), lv[rows], ijk[rows])
     got = n_h.reshape(-1, nd)[torch.from_numpy(rows).cuda()].double().cpu().numpy()
     assert np.max(np.abs(got - ref) / ref) <= 1e-2
     assert np.max(np.abs(sh.cpu().numpy()[rows] - oracle.shield(ref))) <= 5e-3
@@ -34,7 +36,7 @@ def _oracle_check(tree, rho, n_h, sh, nd, rows):
 def test_bounded_wait_runs_out_and_the_context_recovers():
     rho = synth.lognormal_grf(32, 30.0, 2.0, seed=61)
     tree = colden.build_tree_uniform(torch.from_numpy(rho).cuda(), BOX)
-    geom = colden.precompute_geometry("healpix", 2)
+    geom = colden.precompute_geometry("mxn", 4, 6)     # 24 directions
     nd = geom.n_dir
     n_h = torch.full((tree.n_leaf * nd,), -1.0, device="cuda")
     sh = torch.full((tree.n_leaf,), -1.0, device="cuda")
