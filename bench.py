@@ -655,7 +655,11 @@ def run_batch(args):
     clk = clocks.stop()
     info = batch.info()
     flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda")
-    kern = _kernel_breakdown(colden, eager, flush, 1)
+    # per-kind device time of the batch's own launches (with per-launch timing
+    # on, cd_batch_run enqueues them directly instead of replaying the graph),
+    # and of the per-box launches for comparison
+    kern = _kernel_breakdown(colden, lambda: batch.run(stream=stream), flush, 1)
+    kern_per_box = _kernel_breakdown(colden, eager, flush, 1)
 
     # ---- roofline: screening factor only, so the binding roof is the tensor
     # pipe of the shell contraction (the HBM bytes are ~9 B per leaf) ----
@@ -669,7 +673,7 @@ def run_batch(args):
                 "launches_per_step": kern[dom]["launches_per_step"], "peak_kind": tens["peak_kind"],
                 "flops_per_step": t["flops_per_step"],
                 "note": "dense BF16 MMA flops the shell kernels issue (2 M N K, padded tiles included) over their "
-                        "summed device time, each launch timed alone in a per-box pass"}
+                        "summed device time, each launch of the batch timed alone"}
 
     # ---- FP64 oracle: every box on a seeded leaf sample (error of the replayed
     # screening factor), timed on the host cores ----
@@ -715,7 +719,8 @@ def run_batch(args):
             "gpu_launches": info["kernel_nodes"] * args.steps,
             "batch": {"graph_ms": ms_graph, "per_box_launches_ms": ms_eager, "speedup": ms_eager / ms_graph,
                       "autotune": info},
-            "kernels": kern, "roofline": roof, "tensor": tens, "cpu_baseline": cpu, "error_vs_oracle": err,
+            "kernels": kern, "kernels_per_box_launches": kern_per_box, "roofline": roof, "tensor": tens,
+            "cpu_baseline": cpu, "error_vs_oracle": err,
             "clocks": clk}
     print(json.dumps(line), flush=True)
     batch.free()

@@ -198,10 +198,13 @@ cd_status cd_column_density_batch(int n, const cd_tree *trees, const cd_geom *ge
                                   float *const *n_h, float *const *a_v, float *const *shield, void *stream);
 
 /* A batch captured once into a single CUDA graph.  cd_batch_create evaluates
- * the batch eagerly to tune it (the number W of concurrent branches in
- * {1, 2, 4, 8}, boxes placed largest first on the least loaded branch), then
- * captures every box's kernels on W forked streams; it synchronises and
- * returns with the outputs of one evaluation.  cd_batch_run launches the graph
+ * the batch once eagerly (allocating every box's scratch), then autotunes it:
+ * each candidate form is captured into a graph and its replay timed, and the
+ * fastest graph is kept.  The candidates are the persistent form below (BF16
+ * batches it serves, each shell tile shape and CTA count) and every box's own
+ * kernels on W forked streams, W in {1, 2, 4, 8} (boxes placed largest first
+ * on the least loaded branch).  It synchronises and returns with the outputs
+ * of the last replay.  cd_batch_run launches the graph
  * on `stream`: one launch evaluates every box with its tree's current
  * densities (cd_tree_update between runs is seen).  The trees, geometries and
  * output buffers given at creation must stay alive and must not be resized
@@ -216,9 +219,32 @@ cd_status cd_column_density_batch(int n, const cd_tree *trees, const cd_geom *ge
 cd_status cd_batch_create(int n, const cd_tree *trees, const cd_geom *geoms, const cd_opts *opts, float *const *n_h,
                           float *const *a_v, float *const *shield, void *stream, cd_batch *out);
 cd_status cd_batch_run(cd_batch batch, void *stream);
-/* Chosen branch count, eager milliseconds measured for W = 1, 2, 4, 8 (-1 where
- * not tried; any pointer may be NULL) and kernel launches one run contains. */
+/* Chosen branch count (per-box form), graph replay milliseconds measured for
+ * W = 1, 2, 4, 8 (-1 where not tried; any pointer may be NULL) and the kernel
+ * launches one run contains. */
 cd_status cd_batch_info(cd_batch batch, int *width, double *ms_tried, int64_t *kernel_nodes);
+/* The persistent form (BF16 batches the tensor-core path serves: see below).
+ * *persistent = 1 when the graph holds the persistent launches, 0 when it
+ * holds every box's kernels (then the other outputs are 0 / -1).  The
+ * autotuner's choice: *full_tiles = 1 when shell tiles cover all 8 children
+ * (N = 8 n_dir, boxes with n_dir <= 32), 0 for half the children (N = 4 n_dir);
+ * *ctas_per_sm = 1 or 2 persistent shell CTAs per SM; ms_tried[4] = graph
+ * replay milliseconds for (half, 1), (half, 2), (full, 1), (full, 2), -1
+ * where not tried.  Any pointer may be NULL.
+ *
+ * Persistent form.  Per batch: one FP32 launch for the level-3 far shells of
+ * every box; one persistent tensor-core launch over a device work list of
+ * (box, level, tile) for every shell of levels >= 4 (the far shells level by
+ * level, each adding its box's S_{k-1} once that level is complete, then the
+ * oct levels); one persistent leaf launch per direction set over (box, tile).
+ * The waits between levels are bounded spins on per-job counters inside the
+ * launch; a spin that runs out sets the flag cd_device_status reports as
+ * CD_ETIMEOUT (it can only run out if other work holds SMs for seconds while
+ * the batch runs).  Results agree with per-box evaluation within the BF16
+ * tolerance, not bitwise: the level-3 shells of uniform boxes go through the
+ * list kernel and the local term carries dx in the epilogue instead of the
+ * BF16 operand. */
+cd_status cd_batch_plan(cd_batch batch, int *persistent, int *full_tiles, int *ctas_per_sm, double *ms_tried);
 /* Releases the graph and the internal streams (synchronises the device first);
  * the trees, geometries and outputs stay the caller's.  NULL is ignored. */
 void cd_batch_free(cd_batch batch);
@@ -307,6 +333,12 @@ cd_status cd_device_status(void *stream);
  * default limit.  Process-wide; applies to launches enqueued after the call.
  * Never set it outside tests: the outputs of capped launches are incomplete. */
 void cd_debug_wait_polls(int64_t polls);
+
+/* Testing hook of the batch autotuner (no counterpart in the paper): form = 0
+ * restricts later cd_batch_create calls to the per-box form, 1 to the
+ * persistent form where the batch supports it (else the per-box form), < 0
+ * restores the autotuner's choice between them.  Process-wide. */
+void cd_debug_batch_form(int form);
 
 /* Launch statistics of this process, for benchmarks.  Kernel kinds: */
 enum {

@@ -28,15 +28,15 @@ EXPORTS = (
     "cd_column_density", "cd_tree_info", "cd_tree_leaves", "cd_geom_info", "cd_geom_rays", "cd_stats_reset",
     "cd_stats_get", "cd_heating",
     "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_column_density_noalloc", "cd_device_status",
-    "cd_column_density_batch", "cd_batch_create", "cd_batch_run", "cd_batch_info", "cd_batch_free",
-    "cd_debug_wait_polls", "cd_stats_flops",
+    "cd_column_density_batch", "cd_batch_create", "cd_batch_run", "cd_batch_info", "cd_batch_plan", "cd_batch_free",
+    "cd_debug_wait_polls", "cd_debug_batch_form", "cd_stats_flops",
     # include/colden_learned.h
     "cd_adam_default", "cd_net_num_params", "cd_raymarch", "cd_learned_features", "cd_learned_targets",
     "cd_net_create", "cd_net_fit_normaliser", "cd_net_forward", "cd_net_loss_grad", "cd_net_train_step",
     "cd_net_get_state", "cd_net_set_state", "cd_net_info", "cd_net_free",
 )
 _VOID = ("cd_opts_default", "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_stats_reset", "cd_batch_free",
-         "cd_adam_default", "cd_net_free", "cd_net_num_params", "cd_debug_wait_polls")
+         "cd_adam_default", "cd_net_free", "cd_net_num_params", "cd_debug_wait_polls", "cd_debug_batch_form")
 K_RESTRICT, K_SHELL, K_LEAF, K_OTHER, K_NET, K_FEATURES, K_RAYMARCH, K_LEARNED, K_HEATING = range(9)
 KERNEL_KINDS = ("restrict", "shell", "leaf", "other", "net", "features", "raymarch", "learned", "heating")
 
@@ -92,10 +92,13 @@ def load(build_if_missing: bool = False):
     L.cd_device_status.argtypes = [P]
     L.cd_debug_wait_polls.argtypes = [I64]
     L.cd_debug_wait_polls.restype = None
+    L.cd_debug_batch_form.argtypes = [I]
+    L.cd_debug_batch_form.restype = None
     L.cd_column_density_batch.argtypes = [I, P, P, ctypes.POINTER(Opts), P, P, P, P]
     L.cd_batch_create.argtypes = [I, P, P, ctypes.POINTER(Opts), P, P, P, P, ctypes.POINTER(P)]
     L.cd_batch_run.argtypes = [P, P]
     L.cd_batch_info.argtypes = [P, ctypes.POINTER(I), P, ctypes.POINTER(I64)]
+    L.cd_batch_plan.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), P]
     L.cd_batch_free.argtypes = [P]
     L.cd_batch_free.restype = None
     L.cd_tree_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I64)]
@@ -322,6 +325,13 @@ def debug_wait_polls(polls: int):
     load().cd_debug_wait_polls(int(polls))
 
 
+def debug_batch_form(form: int):
+    """cd_debug_batch_form (tests only): 0 = later Batch objects use the per-box
+    form, 1 = the persistent form where supported, negative = the autotuner
+    chooses."""
+    load().cd_debug_batch_form(int(form))
+
+
 def stats_reset(timing: bool = False):
     load().cd_stats_reset(1 if timing else 0)
 
@@ -469,8 +479,14 @@ class Batch:
         w, nodes = ctypes.c_int(), ctypes.c_int64()
         ms = (ctypes.c_double * 4)()
         _check(load().cd_batch_info(self._h, ctypes.byref(w), ms, ctypes.byref(nodes)))
+        per, full, ctas = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        pms = (ctypes.c_double * 4)()
+        _check(load().cd_batch_plan(self._h, ctypes.byref(per), ctypes.byref(full), ctypes.byref(ctas), pms))
+        shapes = (("half", 1), ("half", 2), ("full", 1), ("full", 2))
         return {"width": w.value, "ms_tried": {W: ms[i] for i, W in enumerate((1, 2, 4, 8)) if ms[i] >= 0},
-                "kernel_nodes": nodes.value}
+                "kernel_nodes": nodes.value, "persistent": bool(per.value),
+                "full_tiles": bool(full.value), "ctas_per_sm": ctas.value,
+                "plan_ms": {"%s/%d" % sh: pms[i] for i, sh in enumerate(shapes) if pms[i] >= 0}}
 
     def free(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -22,6 +22,8 @@
 #include <numeric>
 #include <vector>
 
+#include <string.h>
+
 #include "common.cuh"
 
 namespace cd {
@@ -214,10 +216,10 @@ struct ShellListArgs {
 
 // Eq. N_discret for a list of receiving cells: thread per (cell, direction),
 // stencil densities read from the dense level arrays (zero outside the box).
-__global__ void __launch_bounds__(256) shell_list_fp32(ShellListArgs P)
+__device__ __forceinline__ void shell_list_body(const ShellListArgs &P, int64_t e0, int64_t step)
 {
     const int nd = P.nd;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P.n * nd; e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = e0; e < P.n * nd; e += step) {
         const int64_t i = e / nd;
         const int d = (int)(e - i * nd);
         const uint64_t m = P.keys[i];
@@ -244,6 +246,18 @@ __global__ void __launch_bounds__(256) shell_list_fp32(ShellListArgs P)
         }
         P.out[e] = acc;
     }
+}
+
+__global__ void __launch_bounds__(256) shell_list_fp32(ShellListArgs P)
+{
+    shell_list_body(P, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+
+// many lists in one launch: blockIdx.y selects the list (cd_batch)
+__global__ void __launch_bounds__(256) shell_list_fp32_batch(const ShellListArgs *jobs)
+{
+    const ShellListArgs P = jobs[blockIdx.y];
+    shell_list_body(P, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 struct LeafListArgs {
@@ -712,6 +726,39 @@ cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s)
         gather_rho8<<<grid_for(R.n8, 256), 256, 0, s>>>(R);
         CD_CHECK_LAUNCH();
     }
+    return CD_OK;
+}
+
+size_t list_job_bytes() { return sizeof(ShellListArgs); }
+
+void list_job_fill_far3(cd_tree t, cd_geom g, const uint64_t *keys512, void *dst)
+{
+    ShellListArgs A = {};
+    A.k = 3;
+    A.nd = g->n_dir;
+    A.tmask = 4;
+    A.lvl[3] = t->rho_lvl[1];
+    A.dx[3] = (float)(t->box_cm / 2.0);
+    A.keys = keys512;
+    A.n = 512;
+    A.parent = nullptr;
+    A.prefix = nullptr;
+    A.out = t->ws.S[3];
+    for (int q = 0; q < 4; ++q) {
+        A.tab[q] = g->tab[q];
+        A.cmax[q] = g->cmax[q];
+    }
+    A.maxe = g->maxe;
+    memcpy(dst, &A, sizeof(A));
+}
+
+cd_status launch_list_batch(const void *jobs, int n_jobs, int64_t max_elems, cudaStream_t s)
+{
+    if (n_jobs <= 0) return CD_OK;
+    LaunchScope ls(CD_K_SHELL, s);
+    const dim3 grid((unsigned)((max_elems + 255) / 256), (unsigned)n_jobs);
+    shell_list_fp32_batch<<<grid, 256, 0, s>>>(static_cast<const ShellListArgs *>(jobs));
+    CD_CHECK_LAUNCH();
     return CD_OK;
 }
 

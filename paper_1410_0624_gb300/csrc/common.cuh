@@ -250,6 +250,12 @@ cd_status build_amr(cd_tree t, int base, int lmax, int64_t n, const int8_t *leve
 cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s);
 cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n_h, float *a_v, float *shield,
                              cudaStream_t s);
+// Batched FP32 list shells (cd_batch): the far shells of level 3 (table 3)
+// of a tree whose level 3 is complete, into ws.S[3], over the 512 Morton keys
+// keys512; many such lists run as one launch (blockIdx.y = list).
+size_t list_job_bytes();
+void list_job_fill_far3(cd_tree t, cd_geom g, const uint64_t *keys512, void *dst);
+cd_status launch_list_batch(const void *jobs, int n_jobs, int64_t max_elems, cudaStream_t s);
 
 // insitu.cu: the external column of n octs of level k (keys NULL: every oct of
 // a uniform tree), every shell seen from the oct centre (§4.3)
@@ -299,6 +305,17 @@ cd_status leaf_fault_check();
 // cores; CD_EUNSUPPORTED (no error text) when the sizes do not fit it
 cd_status launch_leaf_tc(const LeafLaunch &a, cudaStream_t s);
 cd_status leaf_tc_fault_check();
+// Batched leaf jobs (batch.cu): one job is one launch_leaf_tc's worth (a
+// uniform tree's leaves, or an AMR level's oct list); all jobs of one launch
+// share the direction table (nd, kloc) and the output form (which of Sp,
+// n_h, A_V and the screening factor the rows use, list or Morton tiles: the
+// kernel branches on it as a launch constant).  tile counts as tc_job_fill.
+size_t leaf_tc_job_bytes();
+int64_t leaf_tc_job_fill(const LeafLaunch &a, void *dst);
+int leaf_tc_job_form(const void *job);
+double leaf_tc_job_flops(const void *job);
+cd_status launch_leaf_tc_batch(const void *jobs, const int2 *tile_ref, int64_t total, int nd, const float *kloc,
+                               int form, double flops, cudaStream_t s);
 // cd_debug_wait_polls: poll limit of the BF16 leaf kernel's pipeline waits (< 0: default)
 void set_leaf_tc_wait_polls(int64_t polls);
 
@@ -307,6 +324,31 @@ bool tc_supported(int nd);
 cd_status build_tc_tables(cd_geom g, cudaStream_t s);
 cd_status launch_ext_tc(const ExtLaunch &a, const __nv_bfloat16 *const *brick, cd_geom g, cudaStream_t s);
 cd_status tc_fault_check();
+// Batched shell jobs (batch.cu): one job is one launch's worth of
+// launch_ext_tc (a level, a run of tables, uniform or list tiles), optionally
+// with tiles covering all 8 children (N = 8 nd, nd <= 32) and the prefix rows
+// S_{k-1} added in the epilogue once job wait_job is complete.
+struct TcJobDesc {
+    ExtLaunch a;
+    int full;
+    const float *prefix;         // or NULL
+    const int32_t *prefix_row;   // list jobs: prefix row of each output row
+    int wait_job, wait_count;
+};
+size_t tc_job_bytes();
+// writes the job's kernel arguments to dst (tc_job_bytes() bytes of host
+// memory); returns its tile count, or -1 if the tensor-core form cannot serve it
+int64_t tc_job_fill(const TcJobDesc &d, const __nv_bfloat16 *const *brick, cd_geom g, void *dst);
+double tc_job_flops(const void *job);
+uint32_t tc_job_bstage(const void *job);
+// marks a job that another job waits on (its tiles count themselves done)
+void tc_job_set_signal(void *job);
+// one persistent launch over `total` tiles of the device job array
+// (tile_ref[g] = {job, tile within the job} of global tile g)
+// (*ctas_used: the CTAs per SM launched, at most ctas_per_sm and what fits an SM)
+// (*claim: the work counter, zero at the launch)
+cd_status launch_tc_batch(const void *jobs, const int2 *tile_ref, int64_t total, int *done, int *claim,
+                          uint32_t bstage_max, int ctas_per_sm, double flops, cudaStream_t s, int *ctas_used = nullptr);
 // out[i][d] += prefix[parent[i]][d] for n = rows * nd elements
 cd_status launch_add_parent_list(float *out, const float *prefix, const int32_t *parent, int nd, int64_t rows,
                                  cudaStream_t s);

@@ -20,6 +20,7 @@
 // timeout sets a device flag (cd_device_status).
 #include <algorithm>
 #include <atomic>
+#include <string.h>
 
 #include "common.cuh"
 #include "umma.cuh"
@@ -51,7 +52,18 @@ struct LeafTcArgs {
     int list;                  // AMR list mode (a.oleaf): tiles of 16 octs, rows scattered
     uint32_t pipe_polls;       // poll limit of the pipeline waits (cd_debug_wait_polls); the exit
                                // waits for the CTA's own copies and products keep kMaxPolls
+    int form;                  // kForm* bits; batched: the same for every job of the launch
 };
+
+// what a leaf row reads and writes: the parent prefix, staged rows (bulk
+// stores) or direct n_h rows, A_V, the screening factor, list tiles
+constexpr int kFormSp = 1, kFormBulk = 2, kFormNh = 4, kFormAv = 8, kFormShield = 16, kFormList = 32;
+
+__host__ __device__ inline int leaf_form(const LeafLaunch &a, bool out_bulk, bool list)
+{
+    return (a.Sp ? kFormSp : 0) | (out_bulk ? kFormBulk : (a.n_h ? kFormNh : 0)) | (a.a_v ? kFormAv : 0) |
+           (a.shield ? kFormShield : 0) | (list ? kFormList : 0);
+}
 
 struct LeafTcSmem {
     size_t bloc, bar, grp, grp_stride, aloc, out, stage, stage_bytes, st_e, st_p, st_r, st_l, total;
@@ -97,38 +109,135 @@ __device__ __forceinline__ void named_barrier(int id, int threads)
 }
 
 // octs in a tile (16, fewer in a list's last tile)
-template <bool kList>
-__device__ __forceinline__ int tile_octs(const LeafTcArgs &P, int64_t tile)
+__device__ __forceinline__ int tile_octs(const LeafTcArgs &P, int64_t tile, bool list)
 {
-    if (!kList) return 16;
+    if (!list) return 16;
     const int64_t left = P.a.n_oct - tile * 16;
     return left < 16 ? (int)left : 16;
 }
 
 // a tile's inputs: E rows of its 16 octs, Sp rows of their 2 parents, 128
 // densities (list mode: no Sp, plus the octs' 128 leaf rows)
-template <bool kList>
 __device__ __forceinline__ void prefetch(const LeafTcArgs &P, const LeafTcSmem &S, int64_t tile, unsigned char *st,
-                                         uint64_t *bar)
+                                         uint64_t *bar, bool list)
 {
     const int nd = P.a.nd;
-    const uint32_t nb = (uint32_t)tile_octs<kList>(P, tile);
-    const uint32_t be = nb * nd * 4, bp = P.a.Sp ? 2u * nd * 4 : 0u, br = nb * 32, bl = kList ? nb * 32 : 0u;
+    const uint32_t nb = (uint32_t)tile_octs(P, tile, list);
+    const uint32_t be = nb * nd * 4, bp = P.a.Sp ? 2u * nd * 4 : 0u, br = nb * 32, bl = list ? nb * 32 : 0u;
     mbar_expect_tx(bar, be + bp + br + bl);
     bulk_g2s(st + S.st_e, P.a.E + tile * 16 * nd, be, bar);
     if (P.a.Sp) bulk_g2s(st + S.st_p, P.a.Sp + tile * 2 * nd, bp, bar);
     bulk_g2s(st + S.st_r, P.a.rho_leaf + tile * 128, br, bar);
-    if (kList) bulk_g2s(st + S.st_l, P.a.oleaf + tile * 128, bl, bar);
+    if (list) bulk_g2s(st + S.st_l, P.a.oleaf + tile * 128, bl, bar);
 }
 
-template <bool kList>
-__global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
+// Leaf jobs of many boxes (cd_batch) walked by one persistent launch: global
+// tile g is tile tile_ref[g].y of job tile_ref[g].x.  All jobs
+// of a launch share the direction set; their leaf cell sizes differ, so the
+// local-term operand holds Kloc in units of dx and the epilogue scales it.
+struct LeafBatch {
+    const LeafTcArgs *jobs;
+    const int2 *tile_ref;        // global tile -> {job, tile within the job}
+    int64_t total;
+};
+
+template <class T>
+__device__ __forceinline__ T ldg_copy(const T *p)
 {
+    static_assert(sizeof(T) % 8 == 0, "8-byte words");
+    T v;
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(p);
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(&v);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 8); ++i) dst[i] = __ldg(src + i);
+    return v;
+}
+
+// One leaf row of a tile: N_H[d] = loc[d] (x dx when kScale) + E[d] (+ Sp[d]),
+// written to the staging row (kOut 1) or straight to n_h (kOut 2, rows with
+// ok only), optionally A_V = N_H av_per_nh; returns sum_d 2^(c2 N_H[d]).  All
+// 32 lanes of a warp take the same instance (the form is a launch constant).
+template <bool kSp, int kOut, bool kAv, bool kScale>
+__device__ __forceinline__ float leaf_rows(uint32_t taddr, int nd, const float *Ei, const float *Pi, float *orow,
+                                           float *nh, float *av, bool ok, float c2, float avk, float dxs)
+{
+    float acc = 0.f;
+#pragma unroll 1
+    for (int c = 0; c < nd; c += 32) {
+        uint32_t v[32];
+        tmem_ld32(taddr + (uint32_t)c, v);
+        tmem_ld_wait();
+#pragma unroll
+        for (int j4 = 0; j4 < 32; j4 += 4) {
+            if (c + j4 >= nd) break;       // nd is a multiple of 4
+            float4 e = *reinterpret_cast<const float4 *>(Ei + c + j4);
+            if (kSp) {
+                const float4 p = *reinterpret_cast<const float4 *>(Pi + c + j4);
+                e.x += p.x;
+                e.y += p.y;
+                e.z += p.z;
+                e.w += p.w;
+            }
+            float4 N;
+            if (kScale) {
+                N = make_float4(fmaf(__uint_as_float(v[j4]), dxs, e.x), fmaf(__uint_as_float(v[j4 + 1]), dxs, e.y),
+                                fmaf(__uint_as_float(v[j4 + 2]), dxs, e.z), fmaf(__uint_as_float(v[j4 + 3]), dxs, e.w));
+            } else {
+                N = make_float4(__uint_as_float(v[j4]) + e.x, __uint_as_float(v[j4 + 1]) + e.y,
+                                __uint_as_float(v[j4 + 2]) + e.z, __uint_as_float(v[j4 + 3]) + e.w);
+            }
+            acc += (fast_exp2(c2 * N.x) + fast_exp2(c2 * N.y)) + (fast_exp2(c2 * N.z) + fast_exp2(c2 * N.w));
+            if (kOut == 1) *reinterpret_cast<float4 *>(orow + c + j4) = N;
+            if (kOut == 2 && ok) {
+                nh[c + j4] = N.x;
+                nh[c + j4 + 1] = N.y;
+                nh[c + j4 + 2] = N.z;
+                nh[c + j4 + 3] = N.w;
+            }
+            if (kAv && ok) {
+                av[c + j4] = N.x * avk;
+                av[c + j4 + 1] = N.y * avk;
+                av[c + j4 + 2] = N.z * avk;
+                av[c + j4 + 3] = N.w * avk;
+            }
+        }
+    }
+    return acc;
+}
+
+// kMode 0: uniform tiles (P0); 1: list tiles (P0); 2: the jobs of Bt (P0 holds
+// the launch-wide nd, NP, G, kloc and screening constant)
+template <int kMode>
+__global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P0, LeafBatch Bt)
+{
+    constexpr bool kList = kMode == 1;
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int nd = P.a.nd, NP = P.NP, G = P.G;
-    const LeafTcSmem S = leaf_tc_smem(nd, NP, G, kList);
+    const int nd = P0.a.nd, NP = P0.NP, G = P0.G;
+    const LeafTcSmem S = leaf_tc_smem(nd, NP, G, kMode != 0);
+    const int64_t total = kMode == 2 ? Bt.total : P0.ntiles;
+    // global tile -> its job's arguments, the tile within the job and its kind
+    auto job_of = [&](int64_t gt, int64_t &lt, bool &list) -> LeafTcArgs {
+        if (kMode == 2) {
+            const int2 ref = __ldg(Bt.tile_ref + gt);
+            lt = ref.y;
+            const LeafTcArgs J = ldg_copy(Bt.jobs + ref.x);
+            list = J.list != 0;
+            return J;
+        }
+        lt = gt;
+        list = kList;
+        return P0;
+    };
     const int tid = threadIdx.x, warp = tid >> 5;
     const int g = warp >> 2, quarter = warp & 3, i = tid & 127;   // group, TMEM lane quarter, row
+    // batched: job arguments and tile index per group in three rotating slots
+    // (iteration n uses slot n % 3; during n the group's thread 0 fills slot
+    // (n + 1) % 3 for the next tile's prefetch while threads finishing n - 1
+    // may still read slot (n - 1) % 3); a job's arguments are copied only when
+    // the slot held another job
+    __shared__ LeafTcArgs s_job[kMode == 2 ? 4 : 1][3];
+    __shared__ int s_job_id[kMode == 2 ? 4 : 1][3];
+    __shared__ int s_tile[kMode == 2 ? 4 : 1][3];
     // [0 .. G) group MMAs, [G + 2 g + stage] input stages
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S.bar);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 3 * G);
@@ -142,11 +251,11 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
         fence_mbar_init();
         for (int q = 0; q < G; ++q) sflag[q] = 0;
     }
-    // B[d][8 t + s] = dx Kloc[t][s][d] (BF16), directions past nd zero
+    // B[d][8 t + s] = dx Kloc[t][s][d] (BF16; batched: dx = 1, the epilogue scales), directions past nd zero
     for (int e = tid; e < NP * kK; e += blockDim.x) {
         const int n = e / kK, k = e % kK;
         const int t = k >> 3, s = k & 7;
-        const float v = n < nd ? P.a.dx_leaf * P.a.kloc[(t * 8 + s) * nd + n] : 0.f;
+        const float v = n < nd ? (kMode == 2 ? 1.f : P0.a.dx_leaf) * P0.a.kloc[(t * 8 + s) * nd + n] : 0.f;
         *reinterpret_cast<__nv_bfloat16 *>(smem + S.bloc + op_off(n, k, kK)) = __float2bfloat16_rn(v);
     }
     // every group's A starts all zero; a tile rewrites only each row's own block
@@ -167,22 +276,56 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
     uint32_t phase = 0, sphase[2] = {0, 0};
     bool pending[2] = {false, false};
     bool fault = false;
-    if (i == 0 && first < P.ntiles) {
-        prefetch<kList>(P, S, first, Gb + S.stage, &bar[G + 2 * g]);
+    // thread 0 (batched): the reference of the tile after the next one
+    int2 ref_next = make_int2(0, 0);
+    auto fill_slot = [&](int sl, int2 ref) {   // thread 0, batched
+        if (s_job_id[g][sl] != ref.x) {
+            s_job[g][sl] = ldg_copy(Bt.jobs + ref.x);
+            s_job_id[g][sl] = ref.x;
+        }
+        s_tile[g][sl] = ref.y;
+    };
+    if (i == 0 && first < total) {
+        if (kMode == 2) {
+            for (int sl = 0; sl < 3; ++sl) s_job_id[g][sl] = -1;
+            fill_slot(0, __ldg(Bt.tile_ref + first));
+            prefetch(s_job[g][0], S, s_tile[g][0], Gb + S.stage, &bar[G + 2 * g], P0.list != 0);
+            if (first + stride < total) ref_next = __ldg(Bt.tile_ref + first + stride);
+        } else {
+            int64_t lt;
+            bool lst;
+            const LeafTcArgs J = job_of(first, lt, lst);
+            prefetch(J, S, lt, Gb + S.stage, &bar[G + 2 * g], lst);
+        }
         pending[0] = true;
     }
 
-    int stg = 0;
-    for (int64_t tile = first; tile < P.ntiles && !fault; tile += stride, stg ^= 1) {
+    int stg = 0, it = 0;
+    for (int64_t gt = first; gt < total && !fault; gt += stride, stg ^= 1, ++it) {
+        int64_t tile;
+        bool lst;
+        const int slot = it % 3;
+        const LeafTcArgs &P = kMode == 2 ? s_job[g][slot] : P0;
         unsigned char *st = Gb + S.stage + stg * S.stage_bytes;
         if (i == 0) {
-            if (tile + stride < P.ntiles) {
-                prefetch<kList>(P, S, tile + stride, Gb + S.stage + (stg ^ 1) * S.stage_bytes, &bar[G + 2 * g + (stg ^ 1)]);
+            if (gt + stride < total) {
+                if (kMode == 2) {
+                    const int nsl = (it + 1) % 3;
+                    fill_slot(nsl, ref_next);
+                    prefetch(s_job[g][nsl], S, s_tile[g][nsl], Gb + S.stage + (stg ^ 1) * S.stage_bytes,
+                             &bar[G + 2 * g + (stg ^ 1)], P0.list != 0);
+                    if (gt + 2 * stride < total) ref_next = __ldg(Bt.tile_ref + gt + 2 * stride);
+                } else {
+                    int64_t lt;
+                    bool ln;
+                    const LeafTcArgs J = job_of(gt + stride, lt, ln);
+                    prefetch(J, S, lt, Gb + S.stage + (stg ^ 1) * S.stage_bytes, &bar[G + 2 * g + (stg ^ 1)], ln);
+                }
                 pending[stg ^ 1] = true;
             }
             // the phase bit advances only once the copy has landed: after a
             // timeout the exit below still waits for this stage's copy
-            if (mbar_wait_bounded(&bar[G + 2 * g + stg], sphase[stg], P.pipe_polls)) {
+            if (mbar_wait_bounded(&bar[G + 2 * g + stg], sphase[stg], P0.pipe_polls)) {
                 pending[stg] = false;
                 sphase[stg] ^= 1;
             } else {
@@ -194,6 +337,9 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
             fault = true;
             break;
         }
+        // read after the barrier: thread 0 filled this tile's slot
+        lst = kMode == 2 ? P0.list != 0 : kList;
+        tile = kMode == 2 ? (int64_t)s_tile[g][slot] : gt;
         const float *sR = reinterpret_cast<const float *>(st + S.st_r);
         // ---- A row: the oct's densities in block t ----
         {
@@ -213,11 +359,12 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
                 umma_bf16(tD, umma_smem_desc(a0 + ks * 256, 128, kK * 16), umma_smem_desc(b0 + ks * 256, 128, kK * 16),
                           idesc, ks > 0 ? 1u : 0u);
             umma_commit(&bar[g]);
-            if (!mbar_wait_bounded(&bar[g], phase, P.pipe_polls)) sflag[g] = 1;
+            if (!mbar_wait_bounded(&bar[g], phase, P0.pipe_polls)) sflag[g] = 1;
             // the previous tile's rows must have left the output buffer
-            if (P.out_bulk && !kList) bulk_wait_read<0>();
+            if (P0.out_bulk && !(kMode == 2 ? P0.list != 0 : kList)) bulk_wait_read<0>();
         }
-        if (kList && P.out_bulk && i < 16) bulk_wait_read<0>();   // each oct's copies were issued by thread i
+        // each oct's copies were issued by thread i (list tiles)
+        if (P0.out_bulk && (kMode == 2 ? P0.list != 0 : kList) && i < 16) bulk_wait_read<0>();
         phase ^= 1;
         named_barrier(bid, 128);
         if (sflag[g]) {
@@ -227,61 +374,51 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
         tc_fence_after();
         // ---- N_H = loc + E[oct] + Sp[parent]; screening factor ----
         const int32_t *sL = reinterpret_cast<const int32_t *>(st + S.st_l);
-        const int nb = tile_octs<kList>(P, tile);
+        const int nb = tile_octs(P, tile, lst);
+        const float dxs = kMode == 2 ? P.a.dx_leaf : 1.f;   // batched: Kloc in units of dx
         {
             // output row of this leaf: Morton position, or the list's row (-1: none)
-            const int64_t m = kList ? ((i >> 3) < nb ? (int64_t)sL[i] : -1) : tile * 128 + i;
+            const int64_t m = lst ? ((i >> 3) < nb ? (int64_t)sL[i] : -1) : tile * 128 + i;
+            const bool ok = m >= 0;
+            const int64_t mr = ok ? m : 0;
             const float *Ei = reinterpret_cast<const float *>(st + S.st_e) + (i >> 3) * nd;
-            const float *Pi = P.a.Sp ? reinterpret_cast<const float *>(st + S.st_p) + (i >> 6) * nd : nullptr;
+            const float *Pi = reinterpret_cast<const float *>(st + S.st_p) + (i >> 6) * nd;
             float *orow = sO + (size_t)i * nd;
-            float *av = P.a.a_v && (!kList || m >= 0) ? P.a.a_v + m * nd : nullptr;
-            float *nh = P.a.n_h && !P.out_bulk && (!kList || m >= 0) ? P.a.n_h + m * nd : nullptr;
-            float acc = 0.f;
-#pragma unroll 1
-            for (int c = 0; c < nd; c += 32) {
-                uint32_t v[32];
-                tmem_ld32(tD + lane_off + (uint32_t)c, v);
-                tmem_ld_wait();
-#pragma unroll
-                for (int j4 = 0; j4 < 32; j4 += 4) {
-                    if (c + j4 >= nd) break;       // nd is a multiple of 4
-                    float4 e = *reinterpret_cast<const float4 *>(Ei + c + j4);
-                    if (Pi) {
-                        const float4 p = *reinterpret_cast<const float4 *>(Pi + c + j4);
-                        e.x += p.x;
-                        e.y += p.y;
-                        e.z += p.z;
-                        e.w += p.w;
-                    }
-                    const float4 N = make_float4(__uint_as_float(v[j4]) + e.x, __uint_as_float(v[j4 + 1]) + e.y,
-                                                 __uint_as_float(v[j4 + 2]) + e.z, __uint_as_float(v[j4 + 3]) + e.w);
-                    acc += (fast_exp2(P.c2 * N.x) + fast_exp2(P.c2 * N.y)) + (fast_exp2(P.c2 * N.z) + fast_exp2(P.c2 * N.w));
-                    if (P.out_bulk) {
-                        *reinterpret_cast<float4 *>(orow + c + j4) = N;
-                    } else if (nh) {
-                        nh[c + j4] = N.x;
-                        nh[c + j4 + 1] = N.y;
-                        nh[c + j4 + 2] = N.z;
-                        nh[c + j4 + 3] = N.w;
-                    }
-                    if (av) {
-                        av[c + j4] = N.x * P.a.av_per_nh;
-                        av[c + j4 + 1] = N.y * P.a.av_per_nh;
-                        av[c + j4 + 2] = N.z * P.a.av_per_nh;
-                        av[c + j4 + 3] = N.w * P.a.av_per_nh;
-                    }
-                }
+            const float c2 = P.c2, avk = P.a.av_per_nh;
+            // the output form is a launch constant (kernel parameter): pick the
+            // loop once, outside the per-direction work
+            const int fm = P0.form;
+            float *av = (fm & kFormAv) ? P.a.a_v + mr * nd : nullptr;
+            float *nh = (fm & kFormNh) ? P.a.n_h + mr * nd : nullptr;
+            float *shp = (fm & kFormShield) ? P.a.shield + mr : nullptr;
+            const int form = fm & (kFormSp | kFormBulk | kFormNh | kFormAv);
+            const uint32_t taddr = tD + lane_off;
+            float acc;
+            __syncwarp();
+            switch (form) {
+            case 0: acc = leaf_rows<false, 0, false, kMode == 2>(taddr, nd, Ei, Pi, orow, nh, av, ok, c2, avk, dxs); break;
+            case 1: acc = leaf_rows<true, 0, false, kMode == 2>(taddr, nd, Ei, Pi, orow, nh, av, ok, c2, avk, dxs); break;
+            case 2: acc = leaf_rows<false, 1, false, kMode == 2>(taddr, nd, Ei, Pi, orow, nh, av, ok, c2, avk, dxs); break;
+            case 3: acc = leaf_rows<true, 1, false, kMode == 2>(taddr, nd, Ei, Pi, orow, nh, av, ok, c2, avk, dxs); break;
+            case 4: acc = leaf_rows<false, 2, false, kMode == 2>(taddr, nd, Ei, Pi, orow, nh, av, ok, c2, avk, dxs); break;
+            case 5: acc = leaf_rows<true, 2, false, kMode == 2>(taddr, nd, Ei, Pi, orow, nh, av, ok, c2, avk, dxs); break;
+            case 8: acc = leaf_rows<false, 0, true, kMode == 2>(taddr, nd, Ei, Pi, orow, nh, av, ok, c2, avk, dxs); break;
+            case 9: acc = leaf_rows<true, 0, true, kMode == 2>(taddr, nd, Ei, Pi, orow, nh, av, ok, c2, avk, dxs); break;
+            case 10: acc = leaf_rows<false, 1, true, kMode == 2>(taddr, nd, Ei, Pi, orow, nh, av, ok, c2, avk, dxs); break;
+            case 11: acc = leaf_rows<true, 1, true, kMode == 2>(taddr, nd, Ei, Pi, orow, nh, av, ok, c2, avk, dxs); break;
+            case 12: acc = leaf_rows<false, 2, true, kMode == 2>(taddr, nd, Ei, Pi, orow, nh, av, ok, c2, avk, dxs); break;
+            default: acc = leaf_rows<true, 2, true, kMode == 2>(taddr, nd, Ei, Pi, orow, nh, av, ok, c2, avk, dxs); break;
             }
-            if (P.a.shield && (!kList || m >= 0)) P.a.shield[m] = acc / (float)nd;
+            if ((fm & kFormShield) && ok) *shp = acc / (float)nd;
         }
         fence_proxy_async_smem();
         tc_fence_before();
         named_barrier(bid, 128);
-        if (P.out_bulk && !kList && i == 0) {
+        if (P0.out_bulk && !lst && i == 0) {
             bulk_s2g(P.a.n_h + tile * 128 * nd, sO, (uint32_t)(128 * nd * 4));
             bulk_commit();
         }
-        if (kList && P.out_bulk && i < nb) {
+        if (lst && P0.out_bulk && i < nb) {
             // oct i's children: one copy when their rows are consecutive, else one per leaf row
             const int r0 = sL[8 * i];
             bool run = r0 >= 0;
@@ -305,7 +442,7 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P)
     if (i == 0)
         for (int b = 0; b < 2; ++b)
             if (pending[b]) mbar_wait_bounded(&bar[G + 2 * g + b], sphase[b], kMaxPolls);
-    if (i == 0 || (kList && i < 16)) bulk_wait_all<0>();
+    if (i == 0 || (kMode != 0 && i < 16)) bulk_wait_all<0>();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -346,6 +483,7 @@ cd_status launch_leaf_tc(const LeafLaunch &a, cudaStream_t s)
     P.ntiles = (a.n_oct + 15) / 16;
     P.c2 = (float)(-(double)a.shield_k * (double)a.av_per_nh * 1.4426950408889634);
     P.out_bulk = a.n_h && aligned16(a.n_h);
+    P.form = leaf_form(a, P.out_bulk, list);
     {
         const int64_t cap = g_pipe_polls.load();
         P.pipe_polls = cap < 0 ? kMaxPolls : (uint32_t)std::min<int64_t>(cap, kMaxPolls);
@@ -357,13 +495,88 @@ cd_status launch_leaf_tc(const LeafLaunch &a, cudaStream_t s)
     while (P.G > 1 && (int)leaf_tc_smem(nd, P.NP, P.G, list).total > smax) --P.G;
     const size_t smem = leaf_tc_smem(nd, P.NP, P.G, list).total;
     if ((int)smem > smax) return CD_EUNSUPPORTED;
-    const auto kern = list ? leaf_tc<true> : leaf_tc<false>;
+    const auto kern = list ? leaf_tc<1> : leaf_tc<0>;
     CD_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t grid = std::min<int64_t>((P.ntiles + P.G - 1) / P.G, sms());
     LaunchScope ls(CD_K_LEAF, s, 2.0 * (double)P.ntiles * 128.0 * kK * P.NP);
-    kern<<<(unsigned)grid, 128 * P.G, smem, s>>>(P);
+    kern<<<(unsigned)grid, 128 * P.G, smem, s>>>(P, LeafBatch{});
     CD_CHECK_LAUNCH();
     return CD_OK;
+}
+
+size_t leaf_tc_job_bytes() { return sizeof(LeafTcArgs); }
+
+int64_t leaf_tc_job_fill(const LeafLaunch &a, void *dst)
+{
+    const int nd = a.nd;
+    const int64_t n_leaf = a.n_oct * 8;
+    const bool list = a.oleaf != nullptr;
+    if (nd % 4 != 0 || nd > 64 || !aligned16(a.E) || !aligned16(a.Sp) || !aligned16(a.rho_leaf) || !a.E) return -1;
+    if (!list && (n_leaf < 128 || n_leaf % 128 != 0)) return -1;
+    if (list && (a.Sp || !aligned16(a.oleaf) || (a.n_h && !aligned16(a.n_h)))) return -1;
+    LeafTcArgs P = {};
+    P.a = a;
+    P.list = list;
+    P.NP = round16(nd);
+    P.n_leaf = n_leaf;
+    P.ntiles = (a.n_oct + 15) / 16;
+    P.c2 = (float)(-(double)a.shield_k * (double)a.av_per_nh * 1.4426950408889634);
+    P.out_bulk = a.n_h && aligned16(a.n_h);
+    P.form = leaf_form(a, P.out_bulk, list);
+    P.pipe_polls = kMaxPolls;
+    memcpy(dst, &P, sizeof(P));
+    return P.ntiles;
+}
+
+int leaf_tc_job_form(const void *job)
+{
+    LeafTcArgs P;
+    memcpy(&P, job, sizeof(P));
+    return P.form;
+}
+
+cd_status launch_leaf_tc_batch(const void *jobs, const int2 *tile_ref, int64_t total, int nd, const float *kloc,
+                               int form, double flops, cudaStream_t s)
+{
+    if (total <= 0) return CD_OK;
+    LeafTcArgs P = {};
+    P.a.nd = nd;
+    P.a.kloc = kloc;
+    P.NP = round16(nd);
+    P.form = form;
+    P.list = (form & kFormList) != 0;
+    P.out_bulk = (form & kFormBulk) != 0;
+    {
+        const int64_t cap = g_pipe_polls.load();
+        P.pipe_polls = cap < 0 ? kMaxPolls : (uint32_t)std::min<int64_t>(cap, kMaxPolls);
+    }
+    int dev = 0, smax = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    P.G = 4;
+    while (P.G > 1 && (int)leaf_tc_smem(nd, P.NP, P.G, true).total > smax) --P.G;
+    const size_t smem = leaf_tc_smem(nd, P.NP, P.G, true).total;   // the kernel's layout (mode 2) has the list rows
+    if ((int)smem > smax) {
+        set_error("the batched leaf kernel needs %zu bytes of shared memory", smem);
+        return CD_EUNSUPPORTED;
+    }
+    LeafBatch Bt;
+    Bt.jobs = static_cast<const LeafTcArgs *>(jobs);
+    Bt.tile_ref = tile_ref;
+    Bt.total = total;
+    CD_CUDA(cudaFuncSetAttribute(leaf_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t grid = std::min<int64_t>((total + P.G - 1) / P.G, sms());
+    LaunchScope ls(CD_K_LEAF, s, flops);
+    leaf_tc<2><<<(unsigned)grid, 128 * P.G, smem, s>>>(P, Bt);
+    CD_CHECK_LAUNCH();
+    return CD_OK;
+}
+
+double leaf_tc_job_flops(const void *job)
+{
+    LeafTcArgs P;
+    memcpy(&P, job, sizeof(P));
+    return 2.0 * (double)P.ntiles * 128.0 * kK * P.NP;
 }
 
 void set_leaf_tc_wait_polls(int64_t polls) { g_pipe_polls.store(polls < 0 ? -1 : polls); }

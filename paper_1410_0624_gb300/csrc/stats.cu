@@ -60,7 +60,10 @@ LaunchScope::LaunchScope(int kind, cudaStream_t s, double flops) : kind_(kind), 
     std::lock_guard<std::mutex> lk(g_mu);
     ++g_count[kind];
     g_flops[kind] += flops;
-    if (g_timing) {
+    // no timing events inside a stream capture (the graph would hold them and
+    // the runtime refuses timing events there)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (g_timing && cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
         a_ = take_event();
         b_ = take_event();
         cudaEventRecord(a_, s_);

@@ -103,6 +103,115 @@ def _check_oracle(nh, sh, ref_rows, geoms, precision, what):
         assert dsh <= satol, "%s box %d (%s): max shield error %.3g" % (what, b, SPECS[b], dsh)
 
 
+# boxes the persistent form serves: uniform trees of 32^3 and more, AMR trees
+# on a 32^3 base with two refined levels
+PSPECS = [("u", 5, 48), ("a", 128, 12), ("u", 6, 12), ("a", 128, 48), ("u", 5, 12), ("u", 6, 48)]
+
+
+def _pboxes(seed=0):
+    rng = np.random.default_rng(seed)
+    trees, geoms, rhos, srcs = [], [], [], []
+    g12, g48 = colden.precompute_geometry("healpix", 1), colden.precompute_geometry("healpix", 2)
+    for kind, size, nd in PSPECS:
+        sig = float(rng.uniform(1.0, 2.5))
+        if kind == "u":
+            rho = synth.lognormal_grf(1 << size, 30.0, sig, seed=int(rng.integers(1 << 30)))
+            trees.append(colden.build_tree_uniform(torch.from_numpy(rho).cuda(), BOX))
+            rhos.append(rho.reshape(-1))
+            srcs.append(("u", rho))
+        else:
+            fine = synth.lognormal_grf(size, 30.0, sig, seed=int(rng.integers(1 << 30)))
+            lv = synth.amr_leaves(fine, int(np.log2(size)) - 2, [60.0, 120.0])
+            trees.append(colden.build_tree_amr(lv["base"], lv["lmax"], BOX, lv["level"], lv["ijk"], lv["rho"]))
+            rhos.append(lv["rho"])
+            srcs.append(("a", lv))
+        geoms.append(g12 if nd == 12 else g48)
+    return trees, geoms, rhos, srcs
+
+
+def test_persistent_batch_matches_oracle_and_per_box():
+    """BF16 batch of boxes the persistent form serves: the graph holds a few
+    persistent launches (level-3 lists, one shell launch over every box,
+    level and tile, one leaf launch per direction set), the autotuner tried
+    both tile shapes and CTA counts, and every box matches the FP64 oracle at
+    the BF16 tolerance and the per-box evaluation within it; a replay after a
+    density update matches the oracle too."""
+    trees, geoms, rhos, srcs = _pboxes()
+    ref_rows = _oracle_rows(srcs, trees, geoms, np.random.default_rng(11))
+    rn, rs = _ref(trees, geoms, colden.BF16)
+    nh, sh = _outs(trees, geoms)
+    colden.debug_batch_form(1)
+    try:
+        batch = colden.Batch(trees, geoms, n_h=nh, shield=sh, precision=colden.BF16)
+    finally:
+        colden.debug_batch_form(-1)
+    info = batch.info()
+    assert info["persistent"], info
+    assert set(info["plan_ms"]) == {"half/1", "half/2", "full/1", "full/2"}, info
+    assert not info["ms_tried"], info
+    assert info["kernel_nodes"] <= 2 + 2 * len(geoms), info
+    for x in nh + sh:
+        x.fill_(-1.0)
+    for _ in range(2):          # two replays in a row (the counters are reset by the graph)
+        batch.run()
+    torch.cuda.synchronize()
+    colden.device_status()
+    _check_oracle(nh, sh, ref_rows, geoms, colden.BF16, "persistent replay")
+    for a, b in zip(nh, rn):
+        a, b = a.double().cpu(), b.double().cpu()
+        assert torch.max((a - b).abs() / b).item() <= 1e-2
+    for a, b in zip(sh, rs):
+        assert torch.max((a.cpu() - b).abs()).item() <= 5e-3
+    # a density update between replays is seen
+    rng = np.random.default_rng(6)
+    new = [(r * rng.uniform(0.5, 2.0, size=r.shape)).astype(np.float32) for r in rhos]
+    for t, r in zip(trees, new):
+        colden.tree_update(t, torch.from_numpy(r).cuda())
+    batch.run()
+    torch.cuda.synchronize()
+    src_new = []
+    for (kind, data), r in zip(srcs, new):
+        if kind == "u":
+            src_new.append(("u", r.reshape(data.shape)))
+        else:
+            d = dict(data)
+            d["rho"] = r
+            src_new.append(("a", d))
+    _check_oracle(nh, sh, _oracle_rows(src_new, trees, geoms, np.random.default_rng(12)), geoms, colden.BF16,
+                  "persistent replay after update")
+    colden.device_status()
+    batch.free()
+
+
+def test_batch_autotuner_keeps_the_fastest_form():
+    """Without a forced form the autotuner times the graph replay of every
+    persistent tile shape and every per-box fan-out and keeps the fastest;
+    the kept graph's results match per-box evaluation at the BF16 tolerance."""
+    trees, geoms, rhos, srcs = _pboxes(seed=3)
+    rn, rs = _ref(trees, geoms, colden.BF16)
+    nh, sh = _outs(trees, geoms)
+    batch = colden.Batch(trees, geoms, n_h=nh, shield=sh, precision=colden.BF16)
+    info = batch.info()
+    assert set(info["plan_ms"]) == {"half/1", "half/2", "full/1", "full/2"}, info
+    assert set(info["ms_tried"]) == {1, 2, 4}, info        # W <= number of boxes
+    best_plan, best_w = min(info["plan_ms"].values()), min(info["ms_tried"].values())
+    if info["persistent"]:
+        assert best_plan <= best_w, info
+    else:
+        assert best_w < best_plan and info["ms_tried"][info["width"]] == best_w, info
+    for x in nh + sh:
+        x.fill_(-1.0)
+    batch.run()
+    torch.cuda.synchronize()
+    colden.device_status()
+    for a, b in zip(nh, rn):
+        a, b = a.double().cpu(), b.double().cpu()
+        assert torch.max((a - b).abs() / b).item() <= 1e-2
+    for a, b in zip(sh, rs):
+        assert torch.max((a.cpu() - b).abs()).item() <= 5e-3
+    batch.free()
+
+
 @pytest.mark.parametrize("precision", [colden.FP32, colden.BF16])
 def test_batch_eager_and_graph_match_oracle_and_per_box(precision):
     trees, geoms, rhos, srcs = _boxes()
@@ -117,6 +226,8 @@ def test_batch_eager_and_graph_match_oracle_and_per_box(precision):
     nh2, sh2 = _outs(trees, geoms)
     batch = colden.Batch(trees, geoms, n_h=nh2, shield=sh2, precision=precision)
     info = batch.info()
+    # these boxes include small and shallow trees: every box's own kernels in the graph
+    assert not info["persistent"]
     assert info["width"] in (1, 2, 4, 8) and info["kernel_nodes"] > len(trees)
     for x in nh2 + sh2:
         x.fill_(-1.0)
