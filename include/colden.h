@@ -315,6 +315,43 @@ cd_status cd_geom_info(cd_geom geom, int *n_dir, double *dirs);
  * the n_dir x n_sub x 3 unit vectors (host), direction-major. */
 cd_status cd_geom_rays(cd_geom geom, int *n_sub, double *rays);
 
+/* Checkpoint images (no counterpart in the paper, which restarts from its
+ * simulation's own outputs).  An image is a flat little-endian byte string
+ * that ends in the FNV-1a 64-bit hash (cd_fnv1a64) of every byte before it.
+ *
+ * cd_tree_save: the mesh and its current densities, leaves in output order:
+ *   "CDTREE01" | int32 amr, base_level, max_level | float64 box_cm |
+ *   int64 n_leaf | int8 level[n] | int32 ijk[3 n] | float32 rho[n] | uint64 hash
+ * *size receives the image's size; with buf == NULL nothing else happens,
+ * else the image is written to buf (cap bytes; CD_EINVAL if too small).
+ * Synchronises `stream` (it reads the densities after the work on it).
+ * cd_tree_load builds the tree again (as cd_build_tree_uniform or
+ * cd_build_tree_amr, on `stream`).  An AMR tree loaded this way takes
+ * cd_tree_update densities in output order (the order it was saved in).
+ * CD_EINVAL for a damaged image (hash), a wrong magic or inconsistent sizes.
+ *
+ * cd_geom_save: how the direction set was made and what it holds:
+ *   "CDGEOM01" | int32 scheme, p0, p1, mode, n_dir, n_custom |
+ *   float64 custom[3 n_custom] (CD_DIRS_CUSTOM: the vectors as given) |
+ *   float64 dirs[3 n_dir] | uint64 dirs_hash | uint64 table_hash | uint64 hash
+ * (same size / buffer convention; synchronous).  cd_geom_load rebuilds the
+ * geometry with cd_precompute_geometry from the recorded construction and
+ * returns CD_EINVAL unless the rebuilt directions equal the saved ones bit for
+ * bit and the rebuilt tables have the saved table hash (an image from a
+ * library whose direction sets or tables differ is refused).
+ * cd_geom_hash: dirs_hash = FNV-1a of (int32 mode, int32 n_dir, dirs);
+ * table_hash = FNV-1a of int32 maxe followed by every table the evaluation
+ * reads (Kloc, the FP32 shell tables and counts, the BF16 operands) as stored
+ * on the device.  Either pointer may be NULL. */
+cd_status cd_tree_save(cd_tree tree, void *buf, size_t cap, size_t *size, void *stream);
+cd_status cd_tree_load(const void *buf, size_t size, void *stream, cd_tree *out);
+cd_status cd_geom_save(cd_geom geom, void *buf, size_t cap, size_t *size);
+cd_status cd_geom_load(const void *buf, size_t size, void *stream, cd_geom *out);
+cd_status cd_geom_hash(cd_geom geom, uint64_t *dirs_hash, uint64_t *table_hash);
+/* FNV-1a, 64 bits (Fowler, Noll, Vo): h = 14695981039346656037; for each
+ * byte b: h = (h ^ b) * 1099511628211 mod 2^64. */
+uint64_t cd_fnv1a64(const void *data, size_t n);
+
 /* Synchronises `stream` and reports whether any library kernel on the current
  * device gave up a bounded wait since the last call: CD_ETIMEOUT (flag
  * cleared, message in cd_last_error()) or CD_OK.  Kernels never trap; a wait

@@ -30,6 +30,7 @@ EXPORTS = (
     "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_column_density_noalloc", "cd_device_status",
     "cd_column_density_batch", "cd_batch_create", "cd_batch_run", "cd_batch_info", "cd_batch_plan", "cd_batch_free",
     "cd_debug_wait_polls", "cd_debug_batch_form", "cd_stats_flops",
+    "cd_tree_save", "cd_tree_load", "cd_geom_save", "cd_geom_load", "cd_geom_hash", "cd_fnv1a64",
     # include/colden_learned.h
     "cd_adam_default", "cd_net_num_params", "cd_raymarch", "cd_learned_features", "cd_learned_targets",
     "cd_net_create", "cd_net_fit_normaliser", "cd_net_forward", "cd_net_loss_grad", "cd_net_train_step",
@@ -94,6 +95,14 @@ def load(build_if_missing: bool = False):
     L.cd_debug_wait_polls.restype = None
     L.cd_debug_batch_form.argtypes = [I]
     L.cd_debug_batch_form.restype = None
+    SZ = ctypes.c_size_t
+    L.cd_tree_save.argtypes = [P, P, SZ, ctypes.POINTER(SZ), P]
+    L.cd_tree_load.argtypes = [P, SZ, P, ctypes.POINTER(P)]
+    L.cd_geom_save.argtypes = [P, P, SZ, ctypes.POINTER(SZ)]
+    L.cd_geom_load.argtypes = [P, SZ, P, ctypes.POINTER(P)]
+    L.cd_geom_hash.argtypes = [P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
+    L.cd_fnv1a64.argtypes = [P, SZ]
+    L.cd_fnv1a64.restype = ctypes.c_uint64
     L.cd_column_density_batch.argtypes = [I, P, P, ctypes.POINTER(Opts), P, P, P, P]
     L.cd_batch_create.argtypes = [I, P, P, ctypes.POINTER(Opts), P, P, P, P, ctypes.POINTER(P)]
     L.cd_batch_run.argtypes = [P, P]
@@ -130,7 +139,7 @@ def load(build_if_missing: bool = False):
     L.cd_net_free.argtypes = [P]
     L.cd_net_free.restype = None
     for name in EXPORTS:
-        if name not in _VOID:
+        if name not in _VOID and name != "cd_fnv1a64":   # the rest return cd_status
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -348,6 +357,70 @@ def stats_get(kind: int):
     n, ms = ctypes.c_int64(), ctypes.c_double()
     _check(load().cd_stats_get(int(kind), ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
+
+
+def tree_image(tree: Tree, stream=None) -> bytes:
+    """cd_tree_save: the tree's checkpoint image (mesh and current densities)."""
+    size = ctypes.c_size_t()
+    _check(load().cd_tree_save(tree.handle, None, 0, ctypes.byref(size), ctypes.c_void_p(_stream_ptr(stream))))
+    buf = ctypes.create_string_buffer(size.value)
+    _check(load().cd_tree_save(tree.handle, buf, size.value, ctypes.byref(size), ctypes.c_void_p(_stream_ptr(stream))))
+    return buf.raw
+
+
+def tree_from_image(image: bytes, stream=None) -> Tree:
+    """cd_tree_load."""
+    h = ctypes.c_void_p()
+    _check(load().cd_tree_load(image, len(image), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
+    return Tree(h.value)
+
+
+def geometry_image(geom: Geometry) -> bytes:
+    """cd_geom_save: the geometry's checkpoint image."""
+    size = ctypes.c_size_t()
+    _check(load().cd_geom_save(geom.handle, None, 0, ctypes.byref(size)))
+    buf = ctypes.create_string_buffer(size.value)
+    _check(load().cd_geom_save(geom.handle, buf, size.value, ctypes.byref(size)))
+    return buf.raw
+
+
+def geometry_from_image(image: bytes, stream=None) -> Geometry:
+    """cd_geom_load: rebuilds the geometry and checks its direction and table hashes."""
+    h = ctypes.c_void_p()
+    _check(load().cd_geom_load(image, len(image), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
+    return Geometry(h.value)
+
+
+def geometry_hash(geom: Geometry):
+    """cd_geom_hash: (hash of the direction set and mode, hash of the tables)."""
+    d, t = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().cd_geom_hash(geom.handle, ctypes.byref(d), ctypes.byref(t)))
+    return d.value, t.value
+
+
+def save_tree(tree: Tree, path: str, stream=None):
+    with open(path, "wb") as f:
+        f.write(tree_image(tree, stream))
+
+
+def load_tree(path: str, stream=None) -> Tree:
+    with open(path, "rb") as f:
+        return tree_from_image(f.read(), stream)
+
+
+def save_geometry(geom: Geometry, path: str):
+    with open(path, "wb") as f:
+        f.write(geometry_image(geom))
+
+
+def load_geometry(path: str, stream=None) -> Geometry:
+    with open(path, "rb") as f:
+        return geometry_from_image(f.read(), stream)
+
+
+def fnv1a64(data: bytes) -> int:
+    """cd_fnv1a64 (the checksum that ends every checkpoint image)."""
+    return load().cd_fnv1a64(data, len(data))
 
 
 def precompute_geometry(scheme="healpix", p0: int = 1, p1: int = 0, dirs=None, mode: int = MODE_PREC,

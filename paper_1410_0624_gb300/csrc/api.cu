@@ -184,6 +184,7 @@ const char *cd_last_error(void) { return g_err; }
 cd_status cd_build_tree_uniform(int leaf_level, double box_cm, const float *rho, int rho_on_device, void *stream,
                                 cd_tree *out)
 {
+    NvtxRange nvtx_range("colden:build_tree_uniform");
     if (!out) {
         set_error("out is NULL");
         return CD_EINVAL;
@@ -273,6 +274,7 @@ cd_status cd_build_tree_uniform(int leaf_level, double box_cm, const float *rho,
 cd_status cd_build_tree_amr(int base_level, int max_level, double box_cm, int64_t n_leaf, const int8_t *level,
                             const int32_t *ijk, const float *rho, int rho_on_device, void *stream, cd_tree *out)
 {
+    NvtxRange nvtx_range("colden:build_tree_amr");
     if (!out) {
         set_error("out is NULL");
         return CD_EINVAL;
@@ -308,6 +310,7 @@ cd_status cd_build_tree_amr(int base_level, int max_level, double box_cm, int64_
 
 cd_status cd_tree_update(cd_tree t, const float *rho, int rho_on_device, void *stream)
 {
+    NvtxRange nvtx_range("colden:tree_update");
     if (!t || !rho) {
         set_error("tree or rho is NULL");
         return CD_EINVAL;
@@ -346,6 +349,7 @@ cd_status cd_tree_update(cd_tree t, const float *rho, int rho_on_device, void *s
 cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs, int n_custom, int mode,
                                  void *stream, cd_geom *out)
 {
+    NvtxRange nvtx_range("colden:precompute_geometry");
     if (!out) {
         set_error("out is NULL");
         return CD_EINVAL;
@@ -368,6 +372,14 @@ cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs,
     cudaGetDevice(&g->dev);
     g->n_dir = nd;
     g->mode = mode;
+    g->scheme = scheme;
+    g->p0 = p0;
+    g->p1 = p1;
+    if (scheme == CD_DIRS_CUSTOM) {
+        g->n_custom = n_custom;
+        g->custom = new double[3 * (size_t)n_custom];
+        memcpy(g->custom, dirs, sizeof(double) * 3 * n_custom);
+    }
     g->dirs_host = new double[3 * nd];
     memcpy(g->dirs_host, buf, sizeof(double) * 3 * nd);
     static_assert(CD_CONE_RINGS * CD_CONE_AZ == CD_CONE_SUBRAYS, "sub-ray count of colden.h");
@@ -414,6 +426,7 @@ cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs,
 cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, float *n_h, float *a_v,
                             float *shield, void *stream)
 {
+    NvtxRange nvtx_range("colden:column_density");
     if (!tree || !geom) {
         set_error("tree or geometry is NULL");
         return CD_EINVAL;
@@ -627,6 +640,7 @@ void cd_geom_free(cd_geom g)
     if (g->wb) cudaFree(g->wb);
     if (g->rays_host != g->dirs_host) delete[] g->rays_host;
     delete[] g->dirs_host;
+    delete[] g->custom;
     delete g;
 }
 

@@ -454,6 +454,7 @@ extern "C" {
 cd_status cd_column_density_batch(int n, const cd_tree *trees, const cd_geom *geoms, const cd_opts *opts,
                                   float *const *n_h, float *const *a_v, float *const *shield, void *stream)
 {
+    NvtxRange nvtx_range("colden:column_density_batch");
     if (n < 0 || (n > 0 && (!trees || !geoms))) {
         set_error("bad batch arguments");
         return CD_EINVAL;
@@ -469,6 +470,7 @@ cd_status cd_column_density_batch(int n, const cd_tree *trees, const cd_geom *ge
 cd_status cd_batch_create(int n, const cd_tree *trees, const cd_geom *geoms, const cd_opts *opts, float *const *n_h,
                           float *const *a_v, float *const *shield, void *stream, cd_batch *out)
 {
+    NvtxRange nvtx_range("colden:batch_create");
     if (!out || n < 1 || !trees || !geoms) {
         set_error("bad batch arguments");
         return CD_EINVAL;
@@ -649,6 +651,7 @@ void cd_debug_batch_form(int form) { cd::g_batch_form.store(form < 0 ? -1 : form
 
 cd_status cd_batch_run(cd_batch b, void *stream)
 {
+    NvtxRange nvtx_range("colden:batch_run");
     if (!b) {
         set_error("batch is NULL");
         return CD_EINVAL;

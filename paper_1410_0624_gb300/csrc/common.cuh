@@ -164,6 +164,10 @@ struct cd_geom_s {
     int64_t uid = 0;                    // process-unique id (learned.cu caches per geometry)
     int n_dir = 0;
     int mode = 0;
+    // how the direction set was made (cd_geom_save records it): scheme, p0,
+    // p1 and, for CD_DIRS_CUSTOM, the caller's vectors as given
+    int scheme = 0, p0 = 0, p1 = 0, n_custom = 0;
+    double *custom = nullptr;
     double *dirs_host = nullptr;        // n_dir x 3
     double *dirs_dev = nullptr;
     // the rays the weights are averaged over: n_sub per direction, [nd][n_sub][3];
@@ -202,6 +206,18 @@ class LaunchScope {
     int kind_;
     cudaStream_t s_;
     cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
+// stats.cu: an NVTX range (nvtxRangePushA / nvtxRangePop) for the lifetime of
+// the scope; a no-op unless a tool (nsys, an NVTX injection library) is
+// attached.  Every LaunchScope also opens one named after its kernel kind
+// ("colden:shell", ...); the entry points open "colden:<entry point>".
+class NvtxRange {
+  public:
+    explicit NvtxRange(const char *name);
+    ~NvtxRange();
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 // learned.cu: frees the tree's LevelSums

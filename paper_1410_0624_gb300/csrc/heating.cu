@@ -78,6 +78,7 @@ using namespace cd;
 extern "C" cd_status cd_heating(cd_tree tree, const float *chi, const float *T, const float *n_e, double G0,
                                 float *g0_eff, float *gamma_uv, float *gamma_cr, void *stream)
 {
+    NvtxRange nvtx_range("colden:heating_entry");
     if (!tree || !chi) {
         set_error("tree or chi is NULL");
         return CD_EINVAL;

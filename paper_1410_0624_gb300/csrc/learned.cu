@@ -376,6 +376,7 @@ int64_t cd_net_num_params(int n_dir, int hidden)
 
 cd_status cd_raymarch(cd_tree tree, cd_geom geom, int64_t n, const int64_t *leaves, float *n_ray, void *stream)
 {
+    NvtxRange nvtx_range("colden:raymarch");
     cd_status st = check_tree_geom(tree, geom);
     if (st != CD_OK) return st;
     if (n < 0 || !n_ray || (!leaves && n > tree->n_leaf)) {
@@ -403,6 +404,7 @@ cd_status cd_raymarch(cd_tree tree, cd_geom geom, int64_t n, const int64_t *leav
 cd_status cd_learned_features(cd_tree tree, cd_geom geom, int64_t n, const int64_t *leaves, float *x, float *n_tree,
                               void *stream)
 {
+    NvtxRange nvtx_range("colden:learned_features");
     cd_status st = check_tree_geom(tree, geom);
     if (st != CD_OK) return st;
     if (geom->mode != CD_MODE_PREC) {
@@ -420,6 +422,7 @@ cd_status cd_learned_features(cd_tree tree, cd_geom geom, int64_t n, const int64
 
 cd_status cd_learned_targets(int64_t n, const float *n_ray, const float *n_tree, float *y, void *stream)
 {
+    NvtxRange nvtx_range("colden:learned_targets");
     if (n < 0 || (n > 0 && (!n_ray || !n_tree || !y))) {
         set_error("bad target arguments");
         return CD_EINVAL;
@@ -484,6 +487,7 @@ cd_status cd_net_fit_normaliser(cd_net net, int64_t n, const float *x, void *str
 
 cd_status cd_net_forward(cd_net net, int64_t n, const float *x, float *delta, void *stream)
 {
+    NvtxRange nvtx_range("colden:net_forward");
     cd_status st = check_net(net);
     if (st != CD_OK) return st;
     if (n < 0 || (n > 0 && (!x || !delta))) {
@@ -502,6 +506,7 @@ cd_status cd_net_forward(cd_net net, int64_t n, const float *x, float *delta, vo
 cd_status cd_net_loss_grad(cd_net net, int64_t B, const float *x, const float *y, const int64_t *rows, float *loss,
                            float *grad, void *stream)
 {
+    NvtxRange nvtx_range("colden:net_loss_grad");
     cd_status st = check_net(net);
     if (st != CD_OK) return st;
     if (B < 1 || B > kChunkRows * 4 || !x || !y) {
@@ -517,6 +522,7 @@ cd_status cd_net_loss_grad(cd_net net, int64_t B, const float *x, const float *y
 cd_status cd_net_train_step(cd_net net, int64_t B, const float *x, const float *y, const int64_t *rows,
                             const cd_adam *hp, float *loss, void *stream)
 {
+    NvtxRange nvtx_range("colden:net_train_step");
     cd_status st = cd_net_loss_grad(net, B, x, y, rows, loss, nullptr, stream);
     if (st != CD_OK) return st;
     cd_adam h;

@@ -5,6 +5,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace cd {
@@ -49,6 +51,13 @@ void drain()
 
 }  // namespace
 
+const char *const kKindRange[CD_K_COUNT] = {"colden:restrict", "colden:shell",    "colden:leaf",
+                                            "colden:other",    "colden:net",      "colden:features",
+                                            "colden:raymarch", "colden:learned",  "colden:heating"};
+
+NvtxRange::NvtxRange(const char *name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
+
 bool stats_timing()
 {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -57,6 +66,7 @@ bool stats_timing()
 
 LaunchScope::LaunchScope(int kind, cudaStream_t s, double flops) : kind_(kind), s_(s)
 {
+    nvtxRangePushA(kKindRange[kind]);
     std::lock_guard<std::mutex> lk(g_mu);
     ++g_count[kind];
     g_flops[kind] += flops;
@@ -72,10 +82,12 @@ LaunchScope::LaunchScope(int kind, cudaStream_t s, double flops) : kind_(kind), 
 
 LaunchScope::~LaunchScope()
 {
-    if (!a_) return;
-    cudaEventRecord(b_, s_);
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_pending.push_back({kind_, a_, b_});
+    if (a_) {
+        cudaEventRecord(b_, s_);
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_pending.push_back({kind_, a_, b_});
+    }
+    nvtxRangePop();
 }
 
 }  // namespace cd
