@@ -371,6 +371,27 @@ cd_status cd_device_status(void *stream);
  * Never set it outside tests: the outputs of capped launches are incomplete. */
 void cd_debug_wait_polls(int64_t polls);
 
+/* Bounds-checked build (no counterpart in the paper).  Built with
+ * -DCOLDEN_CHECKED (libcolden_checked.so, a test build), the kernels check the
+ * indices of their gathers and stores before each access; one that falls
+ * outside what it addresses is skipped and recorded (first failure wins) in
+ * a device error word, with no trap.  Sites:
+ *   11 FP32 shell kernel: stencil offset from the tables within the staged
+ *      density region;  12: output row;  13: far-shell prefix row
+ *   21 tensor-core shell kernel: brick index of an A-operand gather
+ *   31 tensor-core leaf kernel: a tile's octs (E, densities) and parents (S)
+ *   32 tensor-core leaf kernel: output row (N_H, A_V, screening factor)
+ *   41 FP32 leaf kernel: a batch's octs and parents
+ *   51 AMR list shell kernel: stencil offset within the stencil region
+ *    1 cd_debug_check_probe
+ * cd_checked_status synchronises the device and returns, in *site and
+ * *index, the first failure since the last call (0 and 0 when none), then
+ * clears it.  cd_debug_check_probe(i) reads element i of a 4-element device
+ * array through the check (i outside 0..3 must be recorded as site 1, not
+ * read).  Both return CD_EUNSUPPORTED from the normal library. */
+cd_status cd_checked_status(int *site, int64_t *index);
+cd_status cd_debug_check_probe(int64_t i, void *stream);
+
 /* Testing hook of the batch autotuner (no counterpart in the paper): form = 0
  * restricts later cd_batch_create calls to the per-box form, 1 to the
  * persistent form where the batch supports it (else the per-box form), < 0

@@ -31,6 +31,7 @@ EXPORTS = (
     "cd_column_density_batch", "cd_batch_create", "cd_batch_run", "cd_batch_info", "cd_batch_plan", "cd_batch_free",
     "cd_debug_wait_polls", "cd_debug_batch_form", "cd_stats_flops",
     "cd_tree_save", "cd_tree_load", "cd_geom_save", "cd_geom_load", "cd_geom_hash", "cd_fnv1a64",
+    "cd_checked_status", "cd_debug_check_probe",
     # include/colden_learned.h
     "cd_adam_default", "cd_net_num_params", "cd_raymarch", "cd_learned_features", "cd_learned_targets",
     "cd_net_create", "cd_net_fit_normaliser", "cd_net_forward", "cd_net_loss_grad", "cd_net_train_step",
@@ -66,16 +67,19 @@ def library_path() -> str:
 
 
 def load(build_if_missing: bool = False):
-    """Loads libcolden.so; raises if it is absent (no fallback exists)."""
+    """Loads libcolden.so (libcolden_checked.so, the bounds-checked test build,
+    when the environment sets COLDEN_CHECKED=1); raises if it is absent (no
+    fallback exists)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    checked = os.environ.get("COLDEN_CHECKED") == "1"
+    path = _build.LIB_CHECKED if checked else _build.LIB
     if not os.path.exists(path):
         if build_if_missing:
-            _build.build()
+            _build.build(checked=checked)
         else:
-            raise RuntimeError("libcolden.so is not built (run __graft_entry__.build())")
+            raise RuntimeError("%s is not built (run __graft_entry__.build())" % os.path.basename(path))
     L = ctypes.CDLL(path)
     P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
     L.cd_opts_default.argtypes = [ctypes.POINTER(Opts)]
@@ -101,6 +105,8 @@ def load(build_if_missing: bool = False):
     L.cd_geom_save.argtypes = [P, P, SZ, ctypes.POINTER(SZ)]
     L.cd_geom_load.argtypes = [P, SZ, P, ctypes.POINTER(P)]
     L.cd_geom_hash.argtypes = [P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
+    L.cd_checked_status.argtypes = [ctypes.POINTER(I), ctypes.POINTER(I64)]
+    L.cd_debug_check_probe.argtypes = [I64, P]
     L.cd_fnv1a64.argtypes = [P, SZ]
     L.cd_fnv1a64.restype = ctypes.c_uint64
     L.cd_column_density_batch.argtypes = [I, P, P, ctypes.POINTER(Opts), P, P, P, P]
@@ -332,6 +338,19 @@ def debug_wait_polls(polls: int):
     waits at `polls` polls (0: they give up at once); negative restores the
     default."""
     load().cd_debug_wait_polls(int(polls))
+
+
+def checked_status():
+    """cd_checked_status: (site, index) of the first out-of-bounds gather the
+    checked build recorded since the last call, (0, 0) when none."""
+    site, index = ctypes.c_int(), ctypes.c_int64()
+    _check(load().cd_checked_status(ctypes.byref(site), ctypes.byref(index)))
+    return site.value, index.value
+
+
+def debug_check_probe(i: int, stream=None):
+    """cd_debug_check_probe (checked build): a read of element i of a 4-element array through the check."""
+    _check(load().cd_debug_check_probe(int(i), ctypes.c_void_p(_stream_ptr(stream))))
 
 
 def debug_batch_form(form: int):

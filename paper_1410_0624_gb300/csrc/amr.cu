@@ -239,7 +239,8 @@ __device__ __forceinline__ void shell_list_body(const ShellListArgs &P, int64_t 
                 const int2 v = row[(size_t)q * nd];
                 const int a = v.x % R, b = (v.x / R) % R, c = v.x / (R * R);
                 const int64_t gx = ox + a, gy = oy + b, gz = oz + c;
-                if (gx >= 0 && gy >= 0 && gz >= 0 && gx < side && gy < side && gz < side)
+                if (gx >= 0 && gy >= 0 && gz >= 0 && gx < side && gy < side && gz < side &&
+                    in_bounds(v.x, R * R * R, kCheckListLevel))
                     part = fmaf(rho[(gz * side + gy) * side + gx], __int_as_float(v.y), part);
             }
             acc = fmaf(P.dx[t], part, acc);
@@ -951,6 +952,7 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
             b.a_v = a_v;
             b.shield = shield;
             b.oleaf = B.oleaf;
+            b.n_rows = t->n_leaf;
             cd_status st = launch_leaf_tc(b, s_leaf);
             if (st == CD_OK) continue;
             if (st != CD_EUNSUPPORTED) return st;

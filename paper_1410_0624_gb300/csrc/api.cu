@@ -14,6 +14,7 @@
 // runs on the tree's high-priority side stream; step 3 waits for both
 // (SideFork).
 #include <atomic>
+#include <vector>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -162,6 +163,27 @@ cd_status SideFork::join()
 cudaStream_t SideFork::side(int i) const { return serial_ ? s_ : t_->side[i]; }
 
 SideFork::~SideFork() { join(); }
+
+#ifdef COLDEN_CHECKED
+// every translation unit's check-word reader (registered at load time)
+static std::vector<CheckReader> &check_readers()
+{
+    static std::vector<CheckReader> v;
+    return v;
+}
+
+int register_check_reader(CheckReader r)
+{
+    check_readers().push_back(r);
+    return 1;
+}
+
+// cd_debug_check_probe: reads a[i] of a 4-element array through the check
+__global__ void check_probe(const float *a, int64_t i, float *out)
+{
+    *out = in_bounds(i, 4, kCheckProbe) ? a[i] : -1.f;
+}
+#endif
 
 }  // namespace cd
 
@@ -531,6 +553,65 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
 }
 
 void cd_debug_wait_polls(int64_t polls) { set_leaf_tc_wait_polls(polls); }
+
+cd_status cd_checked_status(int *site, int64_t *index)
+{
+#ifndef COLDEN_CHECKED
+    (void)site;
+    (void)index;
+    set_error("this library was built without COLDEN_CHECKED");
+    return CD_EUNSUPPORTED;
+#else
+    CD_CUDA(cudaDeviceSynchronize());
+    int s0 = 0;
+    int64_t i0 = 0;
+    for (CheckReader r : check_readers()) {
+        CheckWord w = {};
+        if (!r(&w)) {
+            set_error("reading a check word failed: %s", cudaGetErrorString(cudaGetLastError()));
+            return CD_ECUDA;
+        }
+        if (w.site && !s0) {
+            s0 = w.site;
+            i0 = w.index;
+        }
+    }
+    if (site) *site = s0;
+    if (index) *index = i0;
+    return CD_OK;
+#endif
+}
+
+cd_status cd_debug_check_probe(int64_t i, void *stream)
+{
+#ifndef COLDEN_CHECKED
+    (void)i;
+    (void)stream;
+    set_error("this library was built without COLDEN_CHECKED");
+    return CD_EUNSUPPORTED;
+#else
+    cudaStream_t s = (cudaStream_t)stream;
+    float *buf = nullptr;
+    if (cudaMallocAsync(&buf, 5 * sizeof(float), s) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cannot allocate the probe buffer");
+        return CD_ENOMEM;
+    }
+    CD_CUDA(cudaMemsetAsync(buf, 0, 5 * sizeof(float), s));
+    {
+        LaunchScope ls(CD_K_OTHER, s);
+        check_probe<<<1, 1, 0, s>>>(buf, i, buf + 4);
+    }
+    const cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(buf, s);
+    if (e != cudaSuccess) {
+        set_error("probe launch failed: %s", cudaGetErrorString(e));
+        return CD_ECUDA;
+    }
+    CD_CUDA(cudaStreamSynchronize(s));
+    return CD_OK;
+#endif
+}
 
 cd_status cd_device_status(void *stream)
 {

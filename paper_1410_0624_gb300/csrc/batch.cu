@@ -265,6 +265,7 @@ cd_status plan_build(cd_batch_s &b, int full, int ctas, Plan &P)
         lb.n_h = b.n_h[i];
         lb.a_v = b.a_v[i];
         lb.shield = b.shield[i];
+        lb.n_rows = t->n_leaf;
         if (!t->amr) {
             oct_job(L - 1, t->ws.E, nullptr, nullptr, nullptr);
             lb.n_oct = t->n_oct;

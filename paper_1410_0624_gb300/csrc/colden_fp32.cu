@@ -68,7 +68,9 @@ __global__ void __launch_bounds__(kExtThreads) shell_sum_fp32(ExtArgs P)
         const int j = p / nd, d = p - j * nd;
         const uint64_t m = first + (uint64_t)j;
         const uint32_t cx = compact3((uint64_t)j), cy = compact3((uint64_t)j >> 1), cz = compact3((uint64_t)j >> 2);
-        float acc = P.a.prefix_in ? P.a.prefix_in[(m >> 3) * nd + d] : 0.f;
+        float acc = P.a.prefix_in && in_bounds((long long)(m >> 3), 1ll << (3 * (k - 1)), kCheckFp32Prefix)
+                        ? P.a.prefix_in[(m >> 3) * nd + d]
+                        : 0.f;
 #pragma unroll
         for (int t = 1; t <= 3; ++t) {
             if (!(P.a.tmask & (1 << (t - 1)))) continue;
@@ -83,11 +85,12 @@ __global__ void __launch_bounds__(kExtThreads) shell_sum_fp32(ExtArgs P)
             float part = 0.f;
             for (int e = 0; e < n; ++e) {
                 const int2 v = row[(size_t)e * nd];
-                part = fmaf(s_rho[anchor + v.x], __int_as_float(v.y), part);
+                if (in_bounds(anchor + v.x - region_base(t), R * R * R, kCheckFp32Region))
+                    part = fmaf(s_rho[anchor + v.x], __int_as_float(v.y), part);
             }
             acc = fmaf(P.a.dx[t], part, acc);
         }
-        P.a.out[m * nd + d] = acc;
+        if (in_bounds((long long)m, 1ll << (3 * k), kCheckFp32Out)) P.a.out[m * nd + d] = acc;
     }
 }
 

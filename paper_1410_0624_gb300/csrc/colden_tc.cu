@@ -374,7 +374,8 @@ __global__ void __maxnreg__(64) shell_sum_tc(TcArgs P0, TcBatch Bt)
                 for (int b = 0; b < kChunkBricks; ++b) {
                     const int nq = nq0 + b;                           // uniform
                     const int64_t off = ((int64_t)((nq / 9) * n + (nq / 3) % 3) * n + nq % 3) * 8;
-                    const bool in = nq < 27 && ((mk >> nq) & 1u);
+                    const bool in = nq < 27 && ((mk >> nq) & 1u) &&
+                                    in_bounds((cor - P.brick[t + 1]) / 8 + off / 8, (long long)n * n * n, kCheckTcBrick);
                     cp_async16_ca(dst + b * kALbo, in ? cor + off : P.brick[1], in ? 16u : 0u);
                 }
                 cp_async_arrive(&full[s]);

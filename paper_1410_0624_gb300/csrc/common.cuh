@@ -19,6 +19,54 @@ namespace cd {
 
 void set_error(const char *fmt, ...);
 
+// ---- bounds-checked builds (COLDEN_CHECKED) ---------------------------------
+// Built with -DCOLDEN_CHECKED (libcolden_checked.so), the gathers of the shell
+// and leaf kernels test each index against the extent of what they read or
+// write: in_bounds(i, n, site) is true for 0 <= i < n; otherwise it records
+// (site, i) in this translation unit's check word (the first failure wins),
+// returns false and the caller skips the access (or issues an empty copy).
+// Nothing traps.  cd_checked_status collects and clears every unit's word.
+// In the normal build in_bounds is the constant true and the checks vanish.
+#ifdef COLDEN_CHECKED
+struct CheckWord {
+    int site;
+    int pad;
+    long long index;
+};
+using CheckReader = bool (*)(CheckWord *);
+int register_check_reader(CheckReader r);   // api.cu
+namespace {
+__device__ CheckWord g_check_word;
+__device__ __noinline__ bool check_fail(long long i, int site)
+{
+    if (atomicCAS(&g_check_word.site, 0, site) == 0) *(volatile long long *)&g_check_word.index = i;
+    return false;
+}
+__device__ __forceinline__ bool in_bounds(long long i, long long n, int site)
+{
+    return (i >= 0 && i < n) ? true : check_fail(i, site);
+}
+bool read_check_word(CheckWord *w)
+{
+    const CheckWord zero = {};
+    return cudaMemcpyFromSymbol(w, g_check_word, sizeof(CheckWord)) == cudaSuccess &&
+           cudaMemcpyToSymbol(g_check_word, &zero, sizeof(CheckWord)) == cudaSuccess;
+}
+const int g_check_registered = register_check_reader(read_check_word);
+}  // namespace
+#else
+__device__ __forceinline__ constexpr bool in_bounds(long long, long long, int) { return true; }
+#endif
+// check sites (cd_checked_status reports the code)
+enum {
+    kCheckProbe = 1,
+    kCheckFp32Region = 11, kCheckFp32Out = 12, kCheckFp32Prefix = 13,
+    kCheckTcBrick = 21,
+    kCheckLeafTcIn = 31, kCheckLeafTcOut = 32,
+    kCheckLeafIn = 41,
+    kCheckListLevel = 51,
+};
+
 // Shared-memory staging of the shell kernels: the density region read by
 // table t is a cube of side kRegionSide[t] level-(k-t+1) cells (6 + 2 x the
 // ancestors per axis of one CTA) starting at kRegionBase[t].
@@ -311,6 +359,7 @@ struct LeafLaunch {
     // of oct o (-1: refined); rho_leaf then holds 8 densities per oct (in list
     // order), E already includes the parent prefix and Sp is NULL
     const int32_t *oleaf;
+    int64_t n_rows;           // list mode: rows of n_h / a_v / shield (the tree's leaves; bounds checks)
 };
 cd_status launch_leaf(const LeafLaunch &a, cudaStream_t s);
 

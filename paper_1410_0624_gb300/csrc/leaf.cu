@@ -105,6 +105,12 @@ __global__ void __launch_bounds__(384, 2) leaf_tma(LeafTmaArgs P)
         const uint32_t eb = P.a.E ? (uint32_t)nb * nd * 4 : 0u;
         const int64_t p0 = o0 >> 3;
         const uint32_t pb = P.a.Sp ? (uint32_t)(((o0 + nb - 1) >> 3) - p0 + 1) * nd * 4 : 0u;
+        // checked builds: a batch outside the octs (or their parents) copies nothing
+        if (!(in_bounds(o0, n_oct, kCheckLeafIn) && in_bounds(o0 + nb - 1, n_oct, kCheckLeafIn) &&
+              (!P.a.Sp || in_bounds((o0 + nb - 1) >> 3, (n_oct + 7) / 8, kCheckLeafIn)))) {
+            mbar_expect_tx(&bar[st], 0);
+            return;
+        }
         mbar_expect_tx(&bar[st], eb + pb + (uint32_t)nb * 32);
         if (P.a.E) bulk_g2s(Eb + st * B * nd, P.a.E + o0 * nd, eb, &bar[st]);
         if (P.a.Sp) bulk_g2s(Pb + st * prows * nd, P.a.Sp + p0 * nd, pb, &bar[st]);

@@ -123,6 +123,13 @@ __device__ __forceinline__ void prefetch(const LeafTcArgs &P, const LeafTcSmem &
 {
     const int nd = P.a.nd;
     const uint32_t nb = (uint32_t)tile_octs(P, tile, list);
+    // checked builds: a tile outside its job's octs (or parents) copies nothing
+    const int64_t o0 = tile * 16, n_oct = P.a.n_oct;
+    if (!(in_bounds(o0, n_oct, kCheckLeafTcIn) && in_bounds(o0 + nb - 1, n_oct, kCheckLeafTcIn) &&
+          (!P.a.Sp || in_bounds(tile * 2 + 1, n_oct / 8, kCheckLeafTcIn)))) {
+        mbar_expect_tx(bar, 0);
+        return;
+    }
     const uint32_t be = nb * nd * 4, bp = P.a.Sp ? 2u * nd * 4 : 0u, br = nb * 32, bl = list ? nb * 32 : 0u;
     mbar_expect_tx(bar, be + bp + br + bl);
     bulk_g2s(st + S.st_e, P.a.E + tile * 16 * nd, be, bar);
@@ -379,7 +386,7 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P0, LeafBatch Bt)
         {
             // output row of this leaf: Morton position, or the list's row (-1: none)
             const int64_t m = lst ? ((i >> 3) < nb ? (int64_t)sL[i] : -1) : tile * 128 + i;
-            const bool ok = m >= 0;
+            const bool ok = m >= 0 && in_bounds(m, lst ? P.a.n_rows : 8 * P.a.n_oct, kCheckLeafTcOut);
             const int64_t mr = ok ? m : 0;
             const float *Ei = reinterpret_cast<const float *>(st + S.st_e) + (i >> 3) * nd;
             const float *Pi = reinterpret_cast<const float *>(st + S.st_p) + (i >> 6) * nd;
@@ -414,14 +421,14 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P0, LeafBatch Bt)
         fence_proxy_async_smem();
         tc_fence_before();
         named_barrier(bid, 128);
-        if (P0.out_bulk && !lst && i == 0) {
+        if (P0.out_bulk && !lst && i == 0 && in_bounds(tile * 128 + 127, 8 * P.a.n_oct, kCheckLeafTcOut)) {
             bulk_s2g(P.a.n_h + tile * 128 * nd, sO, (uint32_t)(128 * nd * 4));
             bulk_commit();
         }
         if (lst && P0.out_bulk && i < nb) {
             // oct i's children: one copy when their rows are consecutive, else one per leaf row
             const int r0 = sL[8 * i];
-            bool run = r0 >= 0;
+            bool run = r0 >= 0 && in_bounds(r0 + 7, P.a.n_rows, kCheckLeafTcOut);
 #pragma unroll
             for (int t = 1; t < 8; ++t) run = run && sL[8 * i + t] == r0 + t;
             if (run) {
@@ -429,7 +436,8 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P0, LeafBatch Bt)
             } else {
                 for (int t = 0; t < 8; ++t) {
                     const int r = sL[8 * i + t];
-                    if (r >= 0) bulk_s2g(P.a.n_h + (int64_t)r * nd, sO + (size_t)(8 * i + t) * nd, (uint32_t)(nd * 4));
+                    if (r >= 0 && in_bounds(r, P.a.n_rows, kCheckLeafTcOut))
+                        bulk_s2g(P.a.n_h + (int64_t)r * nd, sO + (size_t)(8 * i + t) * nd, (uint32_t)(nd * 4));
                 }
             }
             bulk_commit();

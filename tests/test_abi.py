@@ -63,3 +63,9 @@ def test_no_oracle_in_product_path():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "liboracle" not in src, f
+
+
+def test_checked_entry_points_refuse_in_the_normal_build(lib):
+    site, index = ctypes.c_int(), ctypes.c_int64()
+    assert lib.cd_checked_status(ctypes.byref(site), ctypes.byref(index)) == colden.CD_EUNSUPPORTED
+    assert lib.cd_debug_check_probe(ctypes.c_int64(9), None) == colden.CD_EUNSUPPORTED
