@@ -197,6 +197,25 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts, flo
 cd_status cd_column_density_batch(int n, const cd_tree *trees, const cd_geom *geoms, const cd_opts *opts,
                                   float *const *n_h, float *const *a_v, float *const *shield, void *stream);
 
+/* cd_column_density for a caller whose data live in HOST memory: rho (or
+ * NULL to keep the tree's densities) is uploaded and applied as by
+ * cd_tree_update (same layout and order; not validated, as on the device
+ * path), then the evaluation runs and n_h, a_v and shield (host buffers of
+ * the sizes above, any may be NULL) receive the results.  On a uniform tree of
+ * 128 or more octs the leaf stage runs in 8 Morton chunks of whole 16-oct
+ * tiles and each chunk's rows are copied to the host on an internal copy
+ * stream while the next chunk is computed; otherwise the copies follow the
+ * evaluation.  Device staging (densities, outputs) is owned by the tree,
+ * allocated by the first call that needs it and kept until cd_tree_free, so
+ * that first call must not run while `stream` is capturing.  Asynchronous
+ * like cd_column_density: the host buffers are complete once `stream` has
+ * completed the call's work (e.g. cudaStreamSynchronize).  Page-locked host
+ * memory (cudaHostAlloc / cudaHostRegister) keeps the copies asynchronous;
+ * pageable memory works but the runtime may stage it.
+ * Errors: as cd_column_density, CD_ENOMEM for the staging buffers. */
+cd_status cd_column_density_host(cd_tree tree, cd_geom geom, const cd_opts *opts, const float *rho, float *n_h,
+                                 float *a_v, float *shield, void *stream);
+
 /* A batch captured once into a single CUDA graph.  cd_batch_create evaluates
  * the batch once eagerly (allocating every box's scratch), then autotunes it:
  * each candidate form is captured into a graph and its replay timed, and the

@@ -31,7 +31,7 @@ EXPORTS = (
     "cd_column_density_batch", "cd_batch_create", "cd_batch_run", "cd_batch_info", "cd_batch_plan", "cd_batch_free",
     "cd_debug_wait_polls", "cd_debug_batch_form", "cd_stats_flops",
     "cd_tree_save", "cd_tree_load", "cd_geom_save", "cd_geom_load", "cd_geom_hash", "cd_fnv1a64",
-    "cd_checked_status", "cd_debug_check_probe",
+    "cd_checked_status", "cd_debug_check_probe", "cd_column_density_host",
     # include/colden_learned.h
     "cd_adam_default", "cd_net_num_params", "cd_raymarch", "cd_learned_features", "cd_learned_targets",
     "cd_net_create", "cd_net_fit_normaliser", "cd_net_forward", "cd_net_loss_grad", "cd_net_train_step",
@@ -105,6 +105,7 @@ def load(build_if_missing: bool = False):
     L.cd_geom_save.argtypes = [P, P, SZ, ctypes.POINTER(SZ)]
     L.cd_geom_load.argtypes = [P, SZ, P, ctypes.POINTER(P)]
     L.cd_geom_hash.argtypes = [P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
+    L.cd_column_density_host.argtypes = [P, P, ctypes.POINTER(Opts), P, P, P, P, P]
     L.cd_checked_status.argtypes = [ctypes.POINTER(I), ctypes.POINTER(I64)]
     L.cd_debug_check_probe.argtypes = [I64, P]
     L.cd_fnv1a64.argtypes = [P, SZ]
@@ -472,6 +473,41 @@ def column_density(tree: Tree, geom: Geometry, n_h=None, a_v=None, shield=None, 
     ptrs = _outputs(tree, geom, n_h, a_v, shield)
     _check(load().cd_column_density(tree.handle, geom.handle, ctypes.byref(o), *ptrs,
                                     ctypes.c_void_p(_stream_ptr(stream))))
+    return n_h, a_v, shield
+
+
+def _hptr(x, numel, name):
+    """Host pointer of a contiguous float32 CPU tensor or numpy array (or None)."""
+    if x is None:
+        return None
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous():
+            raise ValueError("%s must be a contiguous float32 CPU tensor" % name)
+        n, ptr = x.numel(), x.data_ptr()
+    else:
+        if not isinstance(x, np.ndarray) or x.dtype != np.float32 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("%s must be a C-contiguous float32 numpy array" % name)
+        n, ptr = x.size, x.ctypes.data
+    if n < numel:
+        raise ValueError("%s holds %d floats, %d needed" % (name, n, numel))
+    return ptr
+
+
+def column_density_host(tree: Tree, geom: Geometry, rho=None, n_h=None, a_v=None, shield=None,
+                        precision: int = FP32, av_per_nh: float = 1.0 / 1.87e21, shield_k: float = 2.5,
+                        stream=None):
+    """cd_column_density_host: densities from and results to HOST memory (CPU
+    tensors, pinned for asynchronous copies, or numpy arrays).  rho (or
+    None): as for tree_update; n_h / a_v: n_leaf * n_dir floats, shield:
+    n_leaf.  The host buffers are complete once `stream` is synchronised."""
+    o = opts_default()
+    o.precision, o.av_per_nh, o.shield_k = int(precision), float(av_per_nh), float(shield_k)
+    nd = tree.n_leaf * geom.n_dir
+    ptrs = [_hptr(rho, tree.n_leaf, "rho"), _hptr(n_h, nd, "n_h"), _hptr(a_v, nd, "a_v"),
+            _hptr(shield, tree.n_leaf, "shield")]
+    _check(load().cd_column_density_host(tree.handle, geom.handle, ctypes.byref(o),
+                                         *[ctypes.c_void_p(p) for p in ptrs], ctypes.c_void_p(_stream_ptr(stream))))
     return n_h, a_v, shield
 
 

@@ -13,6 +13,7 @@
 // only the densities, so it runs on a side stream of the tree while step 1
 // runs on the tree's high-priority side stream; step 3 waits for both
 // (SideFork).
+#include <algorithm>
 #include <atomic>
 #include <vector>
 #include <stdarg.h>
@@ -163,6 +164,48 @@ cd_status SideFork::join()
 cudaStream_t SideFork::side(int i) const { return serial_ ? s_ : t_->side[i]; }
 
 SideFork::~SideFork() { join(); }
+
+void free_host_io(cd_tree t)
+{
+    cd_tree_s::HostIO &h = t->hio;
+    for (float *p : {h.rho, h.nh, h.av, h.sh})
+        if (p) cudaFree(p);
+    if (h.copy) cudaStreamDestroy(h.copy);
+    for (cudaEvent_t e : h.ev)
+        if (e) cudaEventDestroy(e);
+    h = cd_tree_s::HostIO();
+}
+
+// the staging buffers cd_column_density_host needs (kept by the tree, grown on demand)
+cd_status ensure_host_io(cd_tree t, int64_t nh_elems, bool rho, bool nh, bool av, bool sh)
+{
+    cd_tree_s::HostIO &h = t->hio;
+    if (h.nh_elems < nh_elems) {
+        for (float **p : {&h.nh, &h.av}) {
+            if (*p) cudaFree(*p);
+            *p = nullptr;
+        }
+        h.nh_elems = nh_elems;
+    }
+    bool ok = true;
+    if (!h.copy) {
+        ok = cudaStreamCreateWithFlags(&h.copy, cudaStreamNonBlocking) == cudaSuccess;
+        for (cudaEvent_t &e : h.ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    }
+    auto take = [&](float *&p, bool want, int64_t n) {
+        if (ok && want && !p) ok = cudaMalloc(&p, sizeof(float) * n) == cudaSuccess;
+    };
+    take(h.rho, rho, t->n_leaf);
+    take(h.nh, nh, nh_elems);
+    take(h.av, av, nh_elems);
+    take(h.sh, sh, t->n_leaf);
+    if (!ok) {
+        cudaGetLastError();
+        set_error("cannot allocate the host-output staging buffers");
+        return CD_ENOMEM;
+    }
+    return CD_OK;
+}
 
 #ifdef COLDEN_CHECKED
 // every translation unit's check-word reader (registered at load time)
@@ -445,10 +488,20 @@ cd_status cd_precompute_geometry(int scheme, int p0, int p1, const double *dirs,
     return CD_OK;
 }
 
-cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, float *n_h, float *a_v,
-                            float *shield, void *stream)
+// cd_column_density_host: the leaf stage of a uniform tree runs in Morton
+// chunks and each chunk's rows go to the host on the copy stream while the
+// next chunk is computed
+constexpr int kHostChunks = 8;
+struct LeafSink {
+    float *h_nh, *h_av, *h_sh;     // host destinations (NULL: not wanted)
+    cudaStream_t copy;
+    cudaEvent_t *ev;               // kHostChunks + 1
+    bool used;                     // the leaf stage copied its rows out itself
+};
+
+static cd_status evaluate(cd_tree tree, cd_geom geom, const cd_opts *opts_in, float *n_h, float *a_v, float *shield,
+                          void *stream, LeafSink *sink)
 {
-    NvtxRange nvtx_range("colden:column_density");
     if (!tree || !geom) {
         set_error("tree or geometry is NULL");
         return CD_EINVAL;
@@ -545,11 +598,81 @@ cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, 
     b.n_h = n_h;
     b.a_v = a_v;
     b.shield = shield;
-    if (bf16) {
-        st = launch_leaf_tc(b, s);
-        if (st != CD_EUNSUPPORTED) return st;
+    auto leaf = [&](const LeafLaunch &x) {
+        if (bf16) {
+            const cd_status r = launch_leaf_tc(x, s);
+            if (r != CD_EUNSUPPORTED) return r;
+        }
+        return launch_leaf(x, s);
+    };
+    if (!sink || tree->n_oct < 16 * kHostChunks) return leaf(b);
+    // chunks of whole 16-oct tiles (whole parents too), each copied out once written
+    const int64_t per = (tree->n_oct / kHostChunks + 15) & ~(int64_t)15;
+    int c = 0;
+    for (int64_t o0 = 0; o0 < tree->n_oct; o0 += per, ++c) {
+        const int64_t no = std::min(per, tree->n_oct - o0), r0 = 8 * o0, nr = 8 * no;
+        LeafLaunch x = b;
+        x.n_oct = no;
+        x.rho_leaf += r0;
+        x.E += o0 * nd;
+        if (x.Sp) x.Sp += (o0 / 8) * nd;
+        if (x.n_h) x.n_h += r0 * nd;
+        if (x.a_v) x.a_v += r0 * nd;
+        if (x.shield) x.shield += r0;
+        if ((st = leaf(x)) != CD_OK) return st;
+        CD_CUDA(cudaEventRecord(sink->ev[c], s));
+        CD_CUDA(cudaStreamWaitEvent(sink->copy, sink->ev[c], 0));
+        if (sink->h_nh)
+            CD_CUDA(cudaMemcpyAsync(sink->h_nh + r0 * nd, x.n_h, sizeof(float) * nr * nd, cudaMemcpyDeviceToHost,
+                                    sink->copy));
+        if (sink->h_av)
+            CD_CUDA(cudaMemcpyAsync(sink->h_av + r0 * nd, x.a_v, sizeof(float) * nr * nd, cudaMemcpyDeviceToHost,
+                                    sink->copy));
+        if (sink->h_sh)
+            CD_CUDA(cudaMemcpyAsync(sink->h_sh + r0, x.shield, sizeof(float) * nr, cudaMemcpyDeviceToHost,
+                                    sink->copy));
     }
-    return launch_leaf(b, s);
+    CD_CUDA(cudaEventRecord(sink->ev[kHostChunks], sink->copy));
+    CD_CUDA(cudaStreamWaitEvent(s, sink->ev[kHostChunks], 0));
+    sink->used = true;
+    return CD_OK;
+}
+
+cd_status cd_column_density(cd_tree tree, cd_geom geom, const cd_opts *opts_in, float *n_h, float *a_v,
+                            float *shield, void *stream)
+{
+    NvtxRange nvtx_range("colden:column_density");
+    return evaluate(tree, geom, opts_in, n_h, a_v, shield, stream, nullptr);
+}
+
+cd_status cd_column_density_host(cd_tree tree, cd_geom geom, const cd_opts *opts, const float *rho, float *n_h,
+                                 float *a_v, float *shield, void *stream)
+{
+    NvtxRange nvtx_range("colden:column_density_host");
+    if (!tree || !geom) {
+        set_error("tree or geometry is NULL");
+        return CD_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = tree->n_leaf, nd = geom->n_dir;
+    cd_tree_s::HostIO &h = tree->hio;
+    cd_status st = ensure_host_io(tree, N * nd, rho != nullptr, n_h != nullptr, a_v != nullptr, shield != nullptr);
+    if (st != CD_OK) return st;
+    if (rho) {
+        CD_CUDA(cudaMemcpyAsync(h.rho, rho, sizeof(float) * N, cudaMemcpyHostToDevice, s));
+        if ((st = cd_tree_update(tree, h.rho, 1, stream)) != CD_OK) return st;
+    }
+    if (!n_h && !a_v && !shield) return CD_OK;
+    LeafSink sink = {n_h, a_v, shield, h.copy, h.ev, false};
+    if ((st = evaluate(tree, geom, opts, n_h ? h.nh : nullptr, a_v ? h.av : nullptr, shield ? h.sh : nullptr, stream,
+                       &sink)) != CD_OK)
+        return st;
+    if (!sink.used) {
+        if (n_h) CD_CUDA(cudaMemcpyAsync(n_h, h.nh, sizeof(float) * N * nd, cudaMemcpyDeviceToHost, s));
+        if (a_v) CD_CUDA(cudaMemcpyAsync(a_v, h.av, sizeof(float) * N * nd, cudaMemcpyDeviceToHost, s));
+        if (shield) CD_CUDA(cudaMemcpyAsync(shield, h.sh, sizeof(float) * N, cudaMemcpyDeviceToHost, s));
+    }
+    return CD_OK;
 }
 
 void cd_debug_wait_polls(int64_t polls) { set_leaf_tc_wait_polls(polls); }
@@ -686,6 +809,7 @@ void cd_tree_free(cd_tree t)
     cudaDeviceSynchronize();
     free_workspace(t);
     free_side_streams(t);
+    free_host_io(t);
     free_level_sums(t);
     free_tc_lists(t);
     for (int l = 0; l <= CD_MAXL; ++l) {

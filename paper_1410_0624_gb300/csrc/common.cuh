@@ -202,6 +202,14 @@ struct cd_tree_s {
     // joined back into the caller's stream before the call returns
     cudaStream_t side[2] = {};
     cudaEvent_t ev_fork = nullptr, ev_done[2] = {};
+    // cd_column_density_host: device staging of the host densities and
+    // outputs, the copy stream and one event per leaf chunk (api.cu)
+    struct HostIO {
+        float *rho = nullptr, *nh = nullptr, *av = nullptr, *sh = nullptr;
+        int64_t nh_elems = 0;                 // n_h / a_v staging size (n_leaf x n_dir)
+        cudaStream_t copy = nullptr;
+        cudaEvent_t ev[9] = {};
+    } hio;
     cudaEvent_t ev_S[CD_MAXL + 1] = {}, ev_E[CD_MAXL + 1] = {};
     // live cd_batch objects whose graph holds this tree's scratch pointers:
     // while it is non-zero an evaluation must not reallocate the scratch
