@@ -325,7 +325,6 @@ __global__ void __maxnreg__(64) shell_sum_tc(TcArgs P0, TcBatch Bt)
             int job;
             int64_t tile;
             const TcArgs P = job_of(g, job, tile);
-            const int nchunk = P.c1 - P.c0;
             int64_t gb;
             int cls, h;
             int4 tt;
@@ -358,27 +357,40 @@ __global__ void __maxnreg__(64) shell_sum_tc(TcArgs P0, TcBatch Bt)
                     mm |= ((mx >> (nq % 3)) & (my >> ((nq / 3) % 3)) & (mz >> (nq / 9)) & 1u) << nq;
                 mask[t] = valid ? mm : 0u;
             }
-            for (int j = 0; j < nchunk; ++j, ++q) {
+            // the 15 chunks unrolled: chunk j is table t = j / 5, neighbours
+            // 6 (j % 5) .. + 5, so every neighbour offset is a constant
+            // (dz, dy, dx) scaled by the level's side 2^e (a uniform shift);
+            // chunks outside [c0, c1) are skipped
+            const int e0 = P.k - 1;
+#pragma unroll
+            for (int j = 0; j < kChunks; ++j) {
+                if (j < P.c0 || j >= P.c1) continue;
                 const int s = q % kStages;
                 bool ok = true;
                 if (lane == 0) ok = wait_bar(&empty[s], ((q / kStages) & 1) ^ 1);
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (!ok) { fault = true; break; }
-                const int kb0 = (P.c0 + j) * kChunkBricks;           // uniform
-                const int t = kb0 / kBricksPerTable, nq0 = kb0 - t * kBricksPerTable;
-                const int n = 1 << (P.k - 1 - t);
-                const __nv_bfloat16 *cor = t == 0 ? corner[0] : t == 1 ? corner[1] : corner[2];
-                const uint32_t mk = t == 0 ? mask[0] : t == 1 ? mask[1] : mask[2];
+                constexpr int kPerTable = kBricksPerTable / kChunkBricks;
+                const int t = j / kPerTable, nq0 = (j % kPerTable) * kChunkBricks;
+                const int e = e0 - t;                                 // level side n = 2^e
+                const __nv_bfloat16 *cor = corner[t];
+                const uint32_t mk = mask[t];
                 unsigned char *dst = dst_row + s * kAStageBytes;
 #pragma unroll
                 for (int b = 0; b < kChunkBricks; ++b) {
-                    const int nq = nq0 + b;                           // uniform
-                    const int64_t off = ((int64_t)((nq / 9) * n + (nq / 3) % 3) * n + nq % 3) * 8;
-                    const bool in = nq < 27 && ((mk >> nq) & 1u) &&
-                                    in_bounds((cor - P.brick[t + 1]) / 8 + off / 8, (long long)n * n * n, kCheckTcBrick);
+                    const int nq = nq0 + b;
+                    if (nq >= 27) {                                    // the zero bricks of the table
+                        cp_async16_ca(dst + b * kALbo, P.brick[1], 0u);
+                        continue;
+                    }
+                    const int64_t off = ((int64_t)(nq / 9) << (2 * e + 3)) + ((int64_t)((nq / 3) % 3) << (e + 3)) +
+                                        (int64_t)((nq % 3) << 3);
+                    const bool in = ((mk >> nq) & 1u) &&
+                                    in_bounds((cor - P.brick[t + 1]) / 8 + off / 8, 1ll << (3 * e), kCheckTcBrick);
                     cp_async16_ca(dst + b * kALbo, in ? cor + off : P.brick[1], in ? 16u : 0u);
                 }
                 cp_async_arrive(&full[s]);
+                ++q;
             }
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
