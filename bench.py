@@ -726,9 +726,10 @@ def run_batch(args):
     return 0
 
 
-def _learned_dataset(colden, synth, geom, L, seed, n_rows, x_out, y_out):
+def _learned_dataset(colden, synth, geom, L, seed, n_rows, x_out, y_out, nt_out=None, nr_out=None):
     """Rows of one seeded training field: network inputs and ray-marched
-    targets of a random leaf subset, written into x_out / y_out."""
+    targets of a random leaf subset, written into x_out / y_out (and the
+    plain and ray-marched columns into nt_out / nr_out when given)."""
     import torch
     rho = synth.lognormal_grf_torch(1 << L, 30.0, 2.0, seed, device="cuda").contiguous()
     tree = colden.build_tree_uniform(rho, 10 * synth.PC_CM)
@@ -736,8 +737,8 @@ def _learned_dataset(colden, synth, geom, L, seed, n_rows, x_out, y_out):
     g.manual_seed(seed)
     rows = torch.randperm(tree.n_leaf, generator=g)[:n_rows].cuda()
     nd = geom.n_dir
-    nt = torch.empty((len(rows), nd), device="cuda")
-    nr = torch.empty_like(nt)
+    nt = torch.empty((len(rows), nd), device="cuda") if nt_out is None else nt_out
+    nr = torch.empty_like(nt) if nr_out is None else nr_out
     colden.learned_features(tree, geom, x_out, nt, leaves=rows)
     colden.raymarch(tree, geom, nr, leaves=rows)
     colden.learned_targets(nr, nt, y_out)
@@ -760,9 +761,13 @@ def _ray_scores(n_h, sh, nd, rows, n_ray):
 
 def run_learned(args):
     """Learned correction: the network trained on 16 seeded 128^3 fields
-    (1M leaves each, ray-marched targets), evaluated on a 512^3 field of the
-    same recipe (seed 200).  One step = restriction + the BF16 learned form
-    (per-level sums, per-oct layer 1, fused per-leaf network, N_H + shield)."""
+    (1M leaves each, ray-marched targets) plus --matched-fields fields at the
+    evaluation resolution (other seeds), its training stop chosen on a
+    held-out field at that resolution, evaluated on a 512^3 field of the same
+    recipe (seed 200).  A network trained on the 128^3 fields alone is
+    scored beside it (its per-level inputs do not transfer across
+    resolution).  One step = restriction + the BF16 learned form (per-level
+    sums, per-oct layer 1, fused per-leaf network, N_H + shield)."""
     import torch
     from paper_1410_0624_gb300 import colden, synth
     rank, world, local = _rank()
@@ -772,22 +777,51 @@ def run_learned(args):
     nd = geom.n_dir
     H = 128
     # ---- training set and training (one-off, timed apart) ----
-    n_fields, rows_per = 16, args.train_rows
+    # 16 seeded 128^3 fields, then resolution-matched fields at the evaluation
+    # level (seeds 300+) and a held-out validation field there (seed 400)
+    n_fields, rows_per, n_match = 16, args.train_rows, args.matched_fields
     t0 = time.time()
-    x = torch.empty((n_fields * rows_per, 8 * nd + 1), device="cuda")
-    y = torch.empty((n_fields * rows_per, nd), device="cuda")
-    for i in range(n_fields):
-        _learned_dataset(colden, synth, geom, 7, 100 + i, rows_per, x[i * rows_per:(i + 1) * rows_per],
-                         y[i * rows_per:(i + 1) * rows_per])
+    n_rows = (n_fields + n_match) * rows_per
+    # rows drawn in proportion to the squared mean ray-marched A_V: the fit follows the A_V error
+    wrow = torch.empty(n_rows, dtype=torch.float64, device="cuda")
+    x = torch.empty((n_rows, 8 * nd + 1), device="cuda")
+    y = torch.empty((n_rows, nd), device="cuda")
+    for i in range(n_fields + n_match):
+        lev, seed = (7, 100 + i) if i < n_fields else (args.eval_level, 300 + i - n_fields)
+        nr_i = torch.empty((rows_per, nd), device="cuda")
+        _learned_dataset(colden, synth, geom, lev, seed, rows_per, x[i * rows_per:(i + 1) * rows_per],
+                         y[i * rows_per:(i + 1) * rows_per], nr_out=nr_i)
+        wrow[i * rows_per:(i + 1) * rows_per] = (nr_i.double() / 1.87e21).mean(1) ** 2
+        del nr_i
+    n_val = min(rows_per, 200_000)
+    xv = torch.empty((n_val, 8 * nd + 1), device="cuda")
+    yv = torch.empty((n_val, nd), device="cuda")
+    ntv = torch.empty((n_val, nd), device="cuda")
+    nrv = torch.empty((n_val, nd), device="cuda")
+    _learned_dataset(colden, synth, geom, args.eval_level, 400, n_val, xv, yv, ntv, nrv)
     torch.cuda.synchronize()
     gen_s = time.time() - t0
+    # the 128^3-only network (scored on the evaluation field for comparison)
+    net128 = colden.Net(nd, H, synth.mlp_init(nd, H, 12, out_scale=0.1))
+    net128.fit_normaliser(x[:n_fields * rows_per])
+    colden.train(net128, x[:n_fields * rows_per], y[:n_fields * rows_per], steps=args.train_steps, batch=8192,
+                 lr=2e-3, lr_final=1e-4, seed=3)
     net = colden.Net(nd, H, synth.mlp_init(nd, H, 12, out_scale=0.1))
     t0 = time.time()
     net.fit_normaliser(x)
-    losses = colden.train(net, x, y, steps=args.train_steps, batch=8192, lr=2e-3, lr_final=1e-4, seed=3)
+    dv = torch.empty_like(yv)
+
+    def val_dav(nn):
+        # training stop: mean |A_V| error on the held-out field at the evaluation resolution
+        nn.forward(xv, dv)
+        return float(((ntv.double() * torch.exp(dv.double()) - nrv.double()).abs() / 1.87e21).mean())
+
+    losses = colden.train(net, x, y, steps=args.train_steps, batch=8192, lr=2e-3, lr_final=1e-4, seed=3,
+                          val=val_dav, eval_every=250, row_weights=wrow)
     torch.cuda.synchronize()
     train_s = time.time() - t0
-    del x, y
+    best_step, best_val = min(net.val_history, key=lambda h: h[1])
+    del x, y, xv, yv, ntv, nrv, dv
     torch.cuda.empty_cache()
 
     # ---- evaluation field ----
@@ -837,6 +871,20 @@ def run_learned(args):
     torch.cuda.synchronize()
     forms["bf16_learned"] = {"ms_per_step": ms, "value": units / (ms / 1e3),
                              "vs_ray_marcher": _ray_scores(n_h, sh, nd, rows, n_ray)}
+    # the 128^3-only network on the same leaves (FP32 forward on the sampled leaves' inputs)
+    xs = torch.empty((len(rows), 8 * nd + 1), device="cuda")
+    nts = torch.empty((len(rows), nd), device="cuda")
+    colden.learned_features(tree, geom, xs, nts, leaves=rows)
+    ds = torch.empty_like(nts)
+    net128.forward(xs, ds)
+    torch.cuda.synchronize()
+    n128 = nts.double() * torch.exp(ds.double())
+    forms["learned_128_only"] = {
+        "vs_ray_marcher": {"a_v_abs_mean": float(((n128 - n_ray.double()).abs() / 1.87e21).mean()),
+                           "ln_err_mse": float(((n128 / n_ray.double()).log() ** 2).mean()),
+                           "leaves": int(len(rows))},
+        "note": "network trained on the 16 128^3 fields alone (no resolution-matched rows), FP32 forward"}
+    del xs, nts, ds, n128
     for name, prec, learned, k in (("bf16_plain", "bf16", False, args.steps), ("fp32_plain", "fp32", False, args.steps),
                                    ("fp32_learned", "fp32", True, 1)):
         if args.no_compare and name != "bf16_plain":
@@ -880,11 +928,18 @@ def run_learned(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": "learned correction (48 dirs x 8 slots + ln n -> 2 x 128 GELU -> 48) trained on "
-                                   "16 seeded 128^3 fields, evaluated on a %d^3 uniform field (10 pc, k^-11/3 "
-                                   "log-normal, mean 30, sigma_ln 2, seed 200), N_H + shield out" % (1 << L),
+                                   "16 seeded 128^3 fields + %d fields at %d^3 (other seeds), evaluated on a %d^3 "
+                                   "uniform field (10 pc, k^-11/3 log-normal, mean 30, sigma_ln 2, seed 200), "
+                                   "N_H + shield out" % (n_match, 1 << L, 1 << L),
                        "precision": "bf16", "l2": "512 MB buffer written between timed steps; N_H output %.1f GB"
                                                   % (4 * units / 1e9),
                        "training": {"fields": n_fields, "rows_per_field": rows_per, "steps": args.train_steps,
+                                    "matched_fields": n_match, "matched_level": args.eval_level,
+                                    "validation": "mean |A_V| error on a held-out field at level %d (seed 400), "
+                                                  "%d leaves, every 250 steps" % (args.eval_level, n_val),
+                                    "stop_step": int(best_step), "val_a_v_abs_mean": float(best_val),
+                                    "row_sampling": "with replacement, probability proportional to the squared "
+                                                    "mean ray-marched A_V of the leaf",
                                     "batch": 8192, "data_s": gen_s, "train_s": train_s,
                                     "loss_first": float(losses[:20].mean()), "loss_last": float(losses[-200:].mean())}},
             "gpu_launches": int(launches), "kernels": kern, "roofline": roof, "forms": forms,
@@ -916,10 +971,12 @@ def _learned_oracle_checks(colden, synth, tree, geom, rho, box, L, cpu_seconds):
     T = oracle.Tree.uniform(rho.cpu().numpy(), box)
     rho_np = rho.reshape(-1).cpu().numpy().astype(np.float64)
     n_side = 1 << L
+    dirs = oracle.dirs_healpix(2)          # the oracle's own direction set (48 HEALPix pixel centres)
+    assert dirs.shape[0] == nd
 
     def oracle_rows(m):
         ijk = np.stack([_compact_np(m), _compact_np(m >> 1), _compact_np(m >> 2)], axis=1)
-        _, pl = T.column_density(geom.dirs, np.full(len(m), L), ijk, per_level=L)
+        _, pl = T.column_density(dirs, np.full(len(m), L), ijk, per_level=L)
         slots = ol.slots_from_levels(pl)
         nv = rho_np[(ijk[:, 2] * n_side + ijk[:, 1]) * n_side + ijk[:, 0]]
         return slots, nv
@@ -998,6 +1055,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=3000, help="learned: Adam steps")
     ap.add_argument("--ray-leaves", type=int, default=100_000, help="learned: leaves scored against the ray-marcher")
     ap.add_argument("--eval-level", type=int, default=9, help="learned: leaf level of the evaluation field")
+    ap.add_argument("--matched-fields", type=int, default=4,
+                    help="learned: training fields at the evaluation resolution (seeds 300+)")
     ap.add_argument("--boxes", type=int, default=64)
     ap.add_argument("--amr-level", type=int, default=10,
                     help="amr: finest level of the mesh (base three levels coarser); 9 is a small case for profiling")

@@ -760,10 +760,21 @@ class Net:
 
 
 def train(net: Net, x, y, steps: int, batch: int = 4096, lr: float = 1e-3, seed: int = 0, lr_final: float = None,
-          stream=None):
+          val=None, eval_every: int = 250, row_weights=None, stream=None):
     """Adam training loop over the rows of (x, y) (CUDA tensors): a seeded
     permutation per epoch, minibatches of `batch` rows, optional cosine decay
-    of the step size to lr_final.  Returns the per-step loss (host array).
+    of the step size to lr_final.  With val = (x_val, y_val), the loss on
+    those rows (cd_net_loss_grad, no update) is taken every `eval_every`
+    steps and at the end, and the network is left in the state of the lowest
+    one (the training stop chosen on held-out rows, e.g. of a field at the
+    resolution the network will serve); val may instead be a function of
+    the network returning the score to minimise (e.g. the mean |A_V| error
+    on held-out leaves).  net.val_history then lists (step, score).
+    With row_weights (one non-negative weight per row), each epoch draws its
+    rows with replacement with probabilities proportional to the weights
+    instead of a permutation, which weights the loss by them in expectation
+    (e.g. by the squared column, so that the fit follows the absolute A_V
+    error rather than the log error alone).  Returns the per-step training loss (host array).
     Orchestration only: every step is cd_net_train_step."""
     import math
     import torch
@@ -771,14 +782,44 @@ def train(net: Net, x, y, steps: int, batch: int = 4096, lr: float = 1e-3, seed:
     g = torch.Generator(device="cpu")
     g.manual_seed(seed)
     loss = torch.zeros(steps, device=x.device, dtype=torch.float32)
+    vbuf = torch.zeros(1, device=x.device, dtype=torch.float32)
+    best, best_state, hist = None, None, []
+
+    def check(step):
+        nonlocal best, best_state
+        if callable(val):
+            v = float(val(net))
+        else:
+            net.loss_grad(val[0], val[1], vbuf, stream=stream)
+            v = float(vbuf.item())
+        hist.append((step, v))
+        if best is None or v < best:
+            best, best_state = v, net.state()
+
+    cdf = None if row_weights is None else torch.cumsum(row_weights.detach().double().cpu(), 0)
+
+    def epoch():
+        if cdf is None:
+            return torch.randperm(n, generator=g)
+        # n draws with replacement by inverse transform of the weights' cumulative sum
+        u = torch.rand(n, generator=g, dtype=torch.float64) * cdf[-1]
+        return torch.searchsorted(cdf, u, right=True).clamp_(max=n - 1)
+
     perm = None
     pos = n
     for it in range(steps):
+        if val is not None and it > 0 and it % eval_every == 0:
+            check(it)
         if pos + batch > n:
-            perm = torch.randperm(n, generator=g).to(device=x.device, dtype=torch.int64)
+            perm = epoch().to(device=x.device, dtype=torch.int64)
             pos = 0
         rows = perm[pos:pos + min(batch, n)]
         pos += batch
         cur = lr if lr_final is None else lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * it / steps))
         net.train_step(x, y, rows=rows, lr=cur, loss=loss[it:it + 1], stream=stream)
+    if val is not None:
+        check(steps)
+        if best_state is not None and hist[-1][1] > best:
+            net.load_state(best_state)
+        net.val_history = hist
     return loss.cpu().numpy()
