@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P0, LeafBatch Bt)
     __shared__ LeafTcArgs s_job[kMode == 2 ? 4 : 1][3];
     __shared__ int s_job_id[kMode == 2 ? 4 : 1][3];
     __shared__ int s_tile[kMode == 2 ? 4 : 1][3];
+    __shared__ int s_run[4][4];                  // list tiles: per group and warp, rows form one run
     // [0 .. G) group MMAs, [G + 2 g + stage] input stages
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S.bar);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 3 * G);
@@ -418,6 +419,14 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P0, LeafBatch Bt)
             }
             if ((fm & kFormShield) && ok) *shp = acc / (float)nd;
         }
+        // list tiles: do the tile's leaf rows form one run (row of leaf i = row of leaf 0 + i)?
+        // then one bulk copy sends the tile, as for Morton tiles (octs whose children are all
+        // leaves lie next to each other in the depth-first order)
+        if (lst && P0.out_bulk) {
+            const bool in_run = (i >> 3) >= nb || sL[i] == sL[0] + i;
+            const bool all = __all_sync(0xffffffffu, in_run);
+            if ((i & 31) == 0) s_run[g][quarter] = all ? 1 : 0;
+        }
         fence_proxy_async_smem();
         tc_fence_before();
         named_barrier(bid, 128);
@@ -425,7 +434,13 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P0, LeafBatch Bt)
             bulk_s2g(P.a.n_h + tile * 128 * nd, sO, (uint32_t)(128 * nd * 4));
             bulk_commit();
         }
-        if (lst && P0.out_bulk && i < nb) {
+        const bool tile_run = lst && P0.out_bulk && sL[0] >= 0 && s_run[g][0] && s_run[g][1] && s_run[g][2] &&
+                              s_run[g][3] && in_bounds(sL[0] + 8 * nb - 1, P.a.n_rows, kCheckLeafTcOut);
+        if (tile_run && i == 0) {
+            bulk_s2g(P.a.n_h + (int64_t)sL[0] * nd, sO, (uint32_t)(8 * nb * nd * 4));
+            bulk_commit();
+        }
+        if (lst && P0.out_bulk && i < nb && !tile_run) {
             // oct i's children: one copy when their rows are consecutive, else one per leaf row
             const int r0 = sL[8 * i];
             bool run = r0 >= 0 && in_bounds(r0 + 7, P.a.n_rows, kCheckLeafTcOut);
