@@ -1,5 +1,5 @@
-"""Edge cases of the path: the degenerate all-zero field and the largest tree
-the API accepts.
+"""Edge cases of the path: the degenerate all-zero field, the largest uniform
+tree and the deepest AMR tree the API accepts.
 
 A box with no gas has no column in any direction (Eq. N_discret sums
 densities times path lengths): N_H and A_V are exactly zero and the screening
@@ -76,5 +76,56 @@ def test_largest_tree_1024cube_sampled():
         rel = np.abs(got - ref) / ref
         assert rel.max() <= rtol, (precision, rel.max())
         assert np.max(np.abs(sh[rows].double().cpu().numpy() - oracle.shield(ref))) <= satol
+    t.free()
+    g.free()
+
+
+def _cascade(base, lmax, point, seed):
+    """Leaves of a tree refined cell by cell around one point: at every level
+    from base to lmax - 1 the cell containing `point` (fractions of the box)
+    is split, every other cell of the level is a leaf; densities i.i.d.
+    log-normal."""
+    levels, ijks = [], []
+    for l in range(base, lmax + 1):
+        n = 1 << l
+        here = [int(p * n) for p in point]
+        if l == base:
+            cells = [(i, j, k) for k in range(n) for j in range(n) for i in range(n)]
+        else:
+            up = [2 * c for c in prev]
+            cells = [(up[0] + (o & 1), up[1] + ((o >> 1) & 1), up[2] + (o >> 2)) for o in range(8)]
+        for c in cells:
+            if l < lmax and list(c) == here:
+                continue
+            levels.append(l)
+            ijks.append(c)
+        prev = here
+    rng = np.random.default_rng(seed)
+    rho = np.exp(rng.normal(np.log(10.0), 1.5, size=len(levels))).astype(np.float32)
+    return np.array(levels, np.int8), np.array(ijks, np.int32), rho
+
+
+@pytest.mark.parametrize("precision", [colden.FP32, colden.BF16])
+def test_deepest_amr_tree_all_leaves(precision):
+    """The deepest AMR tree the API accepts (max_level 11, a 2048^3-effective
+    finest cell) refined around one point from an 8^3 base: every leaf against
+    the oracle."""
+    base, lmax, box = 3, 11, 10 * PC
+    lvl, ijk, rho = _cascade(base, lmax, (0.31, 0.62, 0.47), seed=21)
+    t = colden.build_tree_amr(base, lmax, box, lvl, ijk, rho)
+    assert t.max_level == lmax and t.n_leaf == len(lvl)
+    g = colden.precompute_geometry("healpix", 2)
+    nd = g.n_dir
+    n_h = torch.full((t.n_leaf * nd,), -1.0, device="cuda")
+    sh = torch.full((t.n_leaf,), -1.0, device="cuda")
+    colden.column_density(t, g, n_h=n_h, shield=sh, precision=precision)
+    torch.cuda.synchronize()
+    colden.device_status()
+    olv, oijk = t.leaves()
+    ref = oracle.Tree.amr(base, lmax, box, lvl, ijk, rho).column_density(oracle.dirs_healpix(2), olv, oijk)
+    rtol, satol = (1e-5, 1e-5) if precision == colden.FP32 else (1e-2, 5e-3)
+    rel = np.abs(n_h.view(-1, nd).double().cpu().numpy() - ref) / ref
+    assert rel.max() <= rtol, rel.max()
+    assert np.max(np.abs(sh.double().cpu().numpy() - oracle.shield(ref))) <= satol
     t.free()
     g.free()
