@@ -20,7 +20,12 @@ per-direction log correction toward the exactly ray-traced column:
     z2 = W2 a1 + b2, a2 = gelu(z2)
     delta = W3 a2 + b3                              (one value per direction)
     N_learned[d] = N_tree[d] * exp(delta[d]),  N_tree[d] = sum_s c[s, d]
-                   (N_tree itself where delta[d] is not finite)
+                   (N_tree itself where delta[d] is not finite, or lies
+                   outside the trusted range [lo, hi]: by default the whole
+                   line; after training, the range of the targets the
+                   network was fitted to, widened by a margin, so that a
+                   finite but untrained correction falls back to the plain
+                   method)
 
 Training minimises the mean squared error of delta against
 y = ln(N_ray / N_tree) with Adam (Kingma & Ba 2015, Algorithm 1).  GELU is the
@@ -184,9 +189,22 @@ def adam(p: np.ndarray, g: np.ndarray, m: np.ndarray, v: np.ndarray, t: int, lr:
     return p - lr * mhat / (np.sqrt(vhat) + eps), m, v
 
 
-def apply(n_tree: np.ndarray, delta: np.ndarray) -> np.ndarray:
-    """N_learned = N_tree exp(delta); the plain method where delta is not finite."""
+def apply(n_tree: np.ndarray, delta: np.ndarray, lo: float = -math.inf, hi: float = math.inf) -> np.ndarray:
+    """N_learned = N_tree exp(delta); the plain method where delta is not
+    finite or lies outside the closed range [lo, hi] (lo > hi: everywhere)."""
     with np.errstate(over="ignore", invalid="ignore"):
         out = n_tree * np.exp(delta)
-    return np.where(np.isfinite(delta), out, n_tree)
+        keep = np.isfinite(delta) & (delta >= lo) & (delta <= hi)
+    return np.where(keep, out, n_tree)
+
+
+def delta_range(y: np.ndarray, margin: float):
+    """The trusted range of a network trained on targets y: [min y - margin,
+    max y + margin] over the finite entries ((+inf, -inf), an empty range,
+    when there are none)."""
+    f = np.asarray(y, dtype=np.float64).reshape(-1)
+    f = f[np.isfinite(f)]
+    if f.size == 0:
+        return math.inf, -math.inf
+    return float(f.min()) - margin, float(f.max()) + margin
 

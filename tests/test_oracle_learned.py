@@ -129,6 +129,58 @@ def test_apply_falls_back_where_delta_is_not_finite():
     assert np.allclose(ol.apply(n, d), [[1.0, 4.0, 3.0, 4.0]], rtol=1e-15)
 
 
+def test_apply_range_limits():
+    """Infinite range: the unguarded form; a closed range keeps its end
+    points and falls back outside; an empty range (lo > hi) is the plain
+    method everywhere."""
+    n = np.array([[1.0, 2.0, 3.0, 4.0, 5.0]])
+    d = np.array([[-1.0, -0.5, 0.25, 0.5, 2.0]])
+    assert np.array_equal(ol.apply(n, d, -math.inf, math.inf), ol.apply(n, d))
+    got = ol.apply(n, d, -0.5, 0.5)
+    assert np.allclose(got, [[1.0, 2.0 * math.exp(-0.5), 3.0 * math.exp(0.25), 4.0 * math.exp(0.5), 5.0]],
+                       rtol=1e-15)
+    assert np.array_equal(ol.apply(n, d, 1.0, -1.0), n)
+    assert np.array_equal(ol.apply(n, np.array([[np.nan, np.inf, -np.inf, 0.0, 0.0]]), -10, 10),
+                          [[1.0, 2.0, 3.0, 4.0, 5.0]])
+
+
+def test_delta_range_of_targets():
+    y = np.array([0.3, -1.25, np.nan, 2.5, np.inf, -np.inf, 0.0])
+    assert ol.delta_range(y, 0.5) == (-1.75, 3.0)
+    assert ol.delta_range(y, 0.0) == (-1.25, 2.5)
+    lo, hi = ol.delta_range(np.array([np.nan]), 1.0)
+    assert lo > hi
+
+
+def test_range_falls_back_to_the_plain_method():
+    """Where delta leaves the trusted range the learned column is the plain
+    tree method's column (the slot sum of the per-level oracle, checked here
+    against the C oracle's own total); inside it, the corrected column.  A
+    64^3 box of random densities and a seeded network whose biases put every
+    even direction's delta near 3 and every odd one's near 0."""
+    rng = np.random.default_rng(11)
+    L, box = 6, 10 * PC
+    rho = rng.lognormal(1.0, 1.5, size=(1 << L,) * 3)
+    T = oracle.Tree.uniform(rho, box)
+    dirs = oracle.dirs_healpix(1)
+    ijk = rng.integers(0, 1 << L, size=(40, 3)).astype(np.int32)
+    lv = np.full(40, L, dtype=np.int8)
+    tot, pl = T.column_density(dirs, lv, ijk, per_level=L)
+    slots = ol.slots_from_levels(pl)
+    nd, H = dirs.shape[0], 16
+    p = ol.unpack(rng.normal(scale=0.05, size=ol.n_params(nd, H)), nd, H)
+    p["b3"][:] = np.where(np.arange(nd) % 2 == 0, 3.0, 0.0)
+    x = ol.features(slots, rho[ijk[:, 2], ijk[:, 1], ijk[:, 0]])
+    mu, sinv = ol.normaliser(x)
+    delta, _ = ol.forward(p, mu, sinv, x)
+    out_of_range = np.abs(delta) > 1.0
+    assert np.array_equal(out_of_range, np.broadcast_to(np.arange(nd) % 2 == 0, delta.shape))
+    assert np.allclose(ol.apply(ol.tree_total(slots), delta, 1.0, -1.0), tot, rtol=1e-13)
+    out = ol.apply(ol.tree_total(slots), delta, -1.0, 1.0)
+    assert np.allclose(out[out_of_range], tot[out_of_range], rtol=1e-13)
+    assert np.allclose(out[~out_of_range], (tot * np.exp(delta))[~out_of_range], rtol=1e-13)
+
+
 def test_normaliser_moments():
     x = np.array([[1.0, 5.0, 7.0], [2.0, 5.0, 7.0 + 1e-4], [3.0, 5.0, 7.0], [4.0, 5.0, 7.0 + 1e-4]])
     mu, sinv = ol.normaliser(x)
