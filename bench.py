@@ -821,6 +821,8 @@ def run_learned(args):
     torch.cuda.synchronize()
     train_s = time.time() - t0
     best_step, best_val = min(net.val_history, key=lambda h: h[1])
+    # outside the targets' range (widened by the margin) the plain column is kept
+    d_lo, d_hi = net.fit_delta_range(y, args.delta_margin)
     del x, y, xv, yv, ntv, nrv, dv
     torch.cuda.empty_cache()
 
@@ -938,6 +940,7 @@ def run_learned(args):
                                     "validation": "mean |A_V| error on a held-out field at level %d (seed 400), "
                                                   "%d leaves, every 250 steps" % (args.eval_level, n_val),
                                     "stop_step": int(best_step), "val_a_v_abs_mean": float(best_val),
+                                    "delta_range": [d_lo, d_hi], "delta_margin": args.delta_margin,
                                     "row_sampling": "with replacement, probability proportional to the squared "
                                                     "mean ray-marched A_V of the leaf",
                                     "batch": 8192, "data_s": gen_s, "train_s": train_s,
@@ -1055,6 +1058,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=3000, help="learned: Adam steps")
     ap.add_argument("--ray-leaves", type=int, default=100_000, help="learned: leaves scored against the ray-marcher")
     ap.add_argument("--eval-level", type=int, default=9, help="learned: leaf level of the evaluation field")
+    ap.add_argument("--delta-margin", type=float, default=0.5,
+                    help="learned: trusted delta range = training targets' range widened by this (ln units)")
     ap.add_argument("--matched-fields", type=int, default=4,
                     help="learned: training fields at the evaluation resolution (seeds 300+)")
     ap.add_argument("--boxes", type=int, default=64)

@@ -19,7 +19,9 @@
  *   delta    W3 gelu(W2 gelu(W1 u + b1) + b2) + b3       (n_dir values)
  *            gelu(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))
  *   N        N_tree[d] exp(delta[d]),  N_tree[d] = sum_s c[s][d] (the plain
- *            method's column); N_tree[d] itself where delta[d] is not finite.
+ *            method's column); N_tree[d] itself where delta[d] is not finite
+ *            or lies outside the network's trusted range [lo, hi]
+ *            (cd_net_set_delta_range; the whole line by default).
  *
  * Training minimises the mean over rows and directions of
  * (delta - y)^2 with y = ln(N_ray / N_tree), N_ray from cd_raymarch, by Adam
@@ -129,6 +131,25 @@ cd_status cd_net_get_state(cd_net net, float *params, float *mu, float *sinv, fl
                            int64_t *step);
 cd_status cd_net_set_state(cd_net net, const float *params, const float *mu, const float *sinv,
                            const float *adam_m, const float *adam_v, int64_t step);
+
+/* The trusted range of the correction: where delta[d] lies outside the
+ * closed range [lo, hi] (or is not finite) the learned form returns the plain
+ * column N_tree[d], so that a finite correction the network was never trained
+ * to make falls back to the tree method.  lo > hi makes the range empty (the
+ * plain method everywhere).  A new network's range is [-inf, +inf].  The
+ * bounds are kept in FP32; the BF16 form compares delta log2(e) with the
+ * bounds times log2(e), so a delta within a rounding of an end point may be
+ * decided either way.  Not part of cd_net_get_state / cd_net_set_state.
+ * Errors: CD_EINVAL (NULL handle, a NaN end). */
+cd_status cd_net_set_delta_range(cd_net net, double lo, double hi);
+cd_status cd_net_get_delta_range(cd_net net, double *lo, double *hi);
+
+/* Sets the trusted range to [min y - margin, max y + margin] over the finite
+ * entries of the n training targets y (device [n], e.g. from
+ * cd_learned_targets); an empty range when none is finite.  Synchronises the
+ * stream.  Errors: CD_EINVAL (n < 1, NULL y, margin negative or not finite),
+ * CD_ENOMEM, CD_ECUDA. */
+cd_status cd_net_fit_delta_range(cd_net net, int64_t n, const float *y, double margin, void *stream);
 
 /* The network's direction count, hidden width and parameter count (any
  * pointer may be NULL); CD_EINVAL for a NULL handle. */

@@ -35,7 +35,8 @@ EXPORTS = (
     # include/colden_learned.h
     "cd_adam_default", "cd_net_num_params", "cd_raymarch", "cd_learned_features", "cd_learned_targets",
     "cd_net_create", "cd_net_fit_normaliser", "cd_net_forward", "cd_net_loss_grad", "cd_net_train_step",
-    "cd_net_get_state", "cd_net_set_state", "cd_net_info", "cd_net_free",
+    "cd_net_get_state", "cd_net_set_state", "cd_net_info", "cd_net_free", "cd_net_set_delta_range",
+    "cd_net_get_delta_range", "cd_net_fit_delta_range",
 )
 _VOID = ("cd_opts_default", "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_stats_reset", "cd_batch_free",
          "cd_adam_default", "cd_net_free", "cd_net_num_params", "cd_debug_wait_polls", "cd_debug_batch_form")
@@ -143,6 +144,9 @@ def load(build_if_missing: bool = False):
     L.cd_net_get_state.argtypes = [P, P, P, P, P, P, ctypes.POINTER(I64)]
     L.cd_net_set_state.argtypes = [P, P, P, P, P, P, I64]
     L.cd_net_info.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I64)]
+    L.cd_net_set_delta_range.argtypes = [P, ctypes.c_double, ctypes.c_double]
+    L.cd_net_get_delta_range.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.cd_net_fit_delta_range.argtypes = [P, I64, P, ctypes.c_double, P]
     L.cd_net_free.argtypes = [P]
     L.cd_net_free.restype = None
     for name in EXPORTS:
@@ -719,8 +723,24 @@ class Net:
         _check(load().cd_net_train_step(self._h, B, _dptr(x), _dptr(y), _iptr(rows), ctypes.byref(hp),
                                         _dptr(loss), ctypes.c_void_p(_stream_ptr(stream))))
 
+    def set_delta_range(self, lo: float, hi: float):
+        """Trusted range of delta: outside [lo, hi] the plain column is kept."""
+        _check(load().cd_net_set_delta_range(self._h, float(lo), float(hi)))
+
+    def delta_range(self):
+        lo, hi = ctypes.c_double(), ctypes.c_double()
+        _check(load().cd_net_get_delta_range(self._h, ctypes.byref(lo), ctypes.byref(hi)))
+        return lo.value, hi.value
+
+    def fit_delta_range(self, y, margin: float, stream=None):
+        """Trusted range = the finite targets' range widened by margin."""
+        _check(load().cd_net_fit_delta_range(self._h, y.numel(), _dptr(y), float(margin),
+                                             ctypes.c_void_p(_stream_ptr(stream))))
+        return self.delta_range()
+
     def state(self) -> dict:
-        """Checkpoint of the whole state (host numpy arrays)."""
+        """Checkpoint of the whole state (host numpy arrays), with the
+        trusted delta range."""
         P, I = self.n_params, self.n_in
         out = {k: np.zeros(n, dtype=np.float32) for k, n in
                (("params", P), ("mu", I), ("sinv", I), ("adam_m", P), ("adam_v", P))}
@@ -729,6 +749,7 @@ class Net:
         _check(load().cd_net_get_state(self._h, c(out["params"]), c(out["mu"]), c(out["sinv"]), c(out["adam_m"]),
                                        c(out["adam_v"]), ctypes.byref(step)))
         out["step"] = step.value
+        out["delta_range"] = np.array(self.delta_range())
         return out
 
     def load_state(self, st: dict):
@@ -736,6 +757,8 @@ class Net:
         c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
         _check(load().cd_net_set_state(self._h, c(arr["params"]), c(arr["mu"]), c(arr["sinv"]), c(arr["adam_m"]),
                                        c(arr["adam_v"]), int(st.get("step", 0))))
+        if "delta_range" in st:
+            self.set_delta_range(*[float(v) for v in np.asarray(st["delta_range"]).reshape(2)])
 
     def save(self, path: str):
         np.savez(path, n_dir=self.n_dir, hidden=self.hidden, **self.state())

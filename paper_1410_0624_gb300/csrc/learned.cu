@@ -155,10 +155,41 @@ __global__ void targets(int64_t n, const float *__restrict__ n_ray, const float 
         y[i] = logf(n_ray[i] / n_tree[i]);
 }
 
-// N = N_tree exp(delta) (N_tree where delta is not finite), A_V and the
-// shield; one warp per leaf, the shield summed by a fixed butterfly.
+// per-block minimum and maximum of the finite entries of y (+inf / -inf
+// where a block saw none)
+__global__ void __launch_bounds__(256) finite_range(int64_t n, const float *__restrict__ y, float *__restrict__ part)
+{
+    __shared__ float smin[256], smax[256];
+    float lo = INFINITY, hi = -INFINITY;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = y[i];
+        if (isfinite(v)) {
+            lo = fminf(lo, v);
+            hi = fmaxf(hi, v);
+        }
+    }
+    smin[threadIdx.x] = lo;
+    smax[threadIdx.x] = hi;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            smin[threadIdx.x] = fminf(smin[threadIdx.x], smin[threadIdx.x + w]);
+            smax[threadIdx.x] = fmaxf(smax[threadIdx.x], smax[threadIdx.x + w]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = smin[0];
+        part[2 * blockIdx.x + 1] = smax[0];
+    }
+}
+
+// N = N_tree exp(delta) (N_tree where delta is not finite or outside
+// [dlo, dhi]), A_V and the shield; one warp per leaf, the shield summed by a
+// fixed butterfly.
 __global__ void __launch_bounds__(kThreads) learned_combine(int64_t n, int nd, const float *__restrict__ n_tree,
-                                                            const float *__restrict__ delta, float av_per_nh,
+                                                            const float *__restrict__ delta, float dlo, float dhi,
+                                                            float av_per_nh,
                                                             float shield_k, float *__restrict__ n_h,
                                                             float *__restrict__ a_v, float *__restrict__ shield)
 {
@@ -169,7 +200,7 @@ __global__ void __launch_bounds__(kThreads) learned_combine(int64_t n, int nd, c
         for (int d = lane; d < nd; d += 32) {
             const int64_t o = r * nd + d;
             const float dl = delta[o], nt = n_tree[o];
-            const float N = isfinite(dl) ? nt * expf(dl) : nt;
+            const float N = isfinite(dl) && dl >= dlo && dl <= dhi ? nt * expf(dl) : nt;
             const float av = N * av_per_nh;
             if (n_h) n_h[o] = N;
             if (a_v) a_v[o] = av;
@@ -346,7 +377,7 @@ cd_status column_density_learned(cd_tree t, cd_geom g, const cd_opts &o, float *
         if ((st = mlp_forward(net, cn, lv.x, nullptr, lv.delta, s)) != CD_OK) return st;
         LaunchScope ls(CD_K_FEATURES, s);
         learned_combine<<<grid_for(cn * 32, kThreads), kThreads, 0, s>>>(
-            cn, nd, lv.n_tree, lv.delta, (float)o.av_per_nh, (float)o.shield_k, n_h ? n_h + c0 * nd : nullptr,
+            cn, nd, lv.n_tree, lv.delta, net->dlo, net->dhi, (float)o.av_per_nh, (float)o.shield_k, n_h ? n_h + c0 * nd : nullptr,
             a_v ? a_v + c0 * nd : nullptr, shield ? shield + c0 : nullptr);
         CD_CHECK_LAUNCH();
     }
@@ -565,6 +596,65 @@ cd_status cd_net_set_state(cd_net net, const float *params, const float *mu, con
     CD_CUDA(cudaDeviceSynchronize());   // the pageable uploads have landed
     net->step = step;
     net->version += 1;
+    return CD_OK;
+}
+
+cd_status cd_net_set_delta_range(cd_net net, double lo, double hi)
+{
+    cd_status st = check_net(net);
+    if (st != CD_OK) return st;
+    if (std::isnan(lo) || std::isnan(hi)) {
+        set_error("the delta range has a NaN end");
+        return CD_EINVAL;
+    }
+    net->dlo = (float)lo;
+    net->dhi = (float)hi;
+    return CD_OK;
+}
+
+cd_status cd_net_get_delta_range(cd_net net, double *lo, double *hi)
+{
+    cd_status st = check_net(net);
+    if (st != CD_OK) return st;
+    if (lo) *lo = net->dlo;
+    if (hi) *hi = net->dhi;
+    return CD_OK;
+}
+
+cd_status cd_net_fit_delta_range(cd_net net, int64_t n, const float *y, double margin, void *stream)
+{
+    cd_status st = check_net(net);
+    if (st != CD_OK) return st;
+    if (n < 1 || !y || !(margin >= 0.0) || std::isinf(margin)) {
+        set_error("the delta range needs n >= 1 targets and a finite margin >= 0");
+        return CD_EINVAL;
+    }
+    constexpr int kBlocks = 256;
+    float *part = nullptr;
+    if (alloc(&part, 2 * kBlocks) != CD_OK) return CD_ENOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    float h[2 * kBlocks];
+    finite_range<<<kBlocks, 256, 0, s>>>(n, y, part);
+    const bool ok = cudaGetLastError() == cudaSuccess &&
+                    cudaMemcpyAsync(h, part, sizeof(h), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                    cudaStreamSynchronize(s) == cudaSuccess;
+    cudaFree(part);
+    if (!ok) {
+        set_error("delta range reduction failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return CD_ECUDA;
+    }
+    float lo = INFINITY, hi = -INFINITY;
+    for (int b = 0; b < kBlocks; ++b) {
+        lo = std::min(lo, h[2 * b]);
+        hi = std::max(hi, h[2 * b + 1]);
+    }
+    if (lo > hi) {   // no finite target: an empty range, the plain method everywhere
+        net->dlo = INFINITY;
+        net->dhi = -INFINITY;
+    } else {
+        net->dlo = (float)((double)lo - margin);
+        net->dhi = (float)((double)hi + margin);
+    }
     return CD_OK;
 }
 

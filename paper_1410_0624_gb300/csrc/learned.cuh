@@ -53,6 +53,9 @@ struct cd_net_s {
     float *m = nullptr, *v = nullptr;   // Adam moments
     float *grad = nullptr;    // [total]
     int64_t step = 0;
+    // trusted range of delta (cd_net_set_delta_range): outside it, or where
+    // delta is not finite, the learned form returns the plain column
+    float dlo = -INFINITY, dhi = INFINITY;
     int dev = 0;
     cd::Activations act;
     // BF16 operands of the tensor-core inference (mlp_tc.cu), rebuilt when

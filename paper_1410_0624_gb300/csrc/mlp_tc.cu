@@ -484,6 +484,7 @@ struct CellArgs {
     const unsigned char *tc;
     int64_t n_leaf, ntiles;
     float dx_leaf, av_per_nh, c2;    // c2 = -shield_k av_per_nh log2(e)
+    float dlo2, dhi2;                // trusted delta range x log2(e)
     const float *rho_leaf;           // Morton
     const float *kloc;               // [8][8][nd]
     const __nv_bfloat16 *h;          // layer-1 blocks
@@ -789,7 +790,7 @@ __global__ void __launch_bounds__(kCellThreads, 1) learned_cell_tc(CellArgs A)
                     for (int q = 0; q < 4; ++q) {
                         const float dl = __uint_as_float(v[j4 + q]);
                         const float nt = __uint_as_float(w[j4 + q]) + ev[q];
-                        N[q] = isfinite(dl) ? nt * fast_exp2(dl) : nt;
+                        N[q] = isfinite(dl) && dl >= A.dlo2 && dl <= A.dhi2 ? nt * fast_exp2(dl) : nt;
                         acc += fast_exp2(A.c2 * N[q]);
                     }
                     *reinterpret_cast<float4 *>(nrow + c + j4) = make_float4(N[0], N[1], N[2], N[3]);
@@ -951,6 +952,8 @@ cd_status column_density_learned_tc(cd_tree t, cd_geom g, const cd_opts &o, floa
         A.dx_leaf = (float)(t->box_cm / (double)((int64_t)1 << t->L));
         A.av_per_nh = (float)o.av_per_nh;
         A.c2 = (float)(-o.shield_k * o.av_per_nh * 1.4426950408889634);
+        A.dlo2 = (float)((double)net->dlo * 1.4426950408889634);
+        A.dhi2 = (float)((double)net->dhi * 1.4426950408889634);
         A.rho_leaf = t->rho_leaf;
         A.kloc = g->kloc;
         A.h = ts->h;

@@ -16,6 +16,8 @@ Tolerances.
   * Learned N = N_tree exp(delta): relative error = error of N_tree + absolute
     error of delta: held to 1e-4 relative; shield to 2e-5 absolute.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -330,6 +332,80 @@ def test_learned_bf16_column_density_matches_oracle(L, k, dset):
     assert np.all(np.isfinite(got))
     assert rel.max() < 1.5e-2 and rel.mean() < 3e-3
     assert np.max(np.abs(gsh - wsh)) < 2e-3
+
+
+@pytest.mark.parametrize("L,k,precision", [(5, 600, colden.FP32), (5, 600, colden.BF16), (7, 300, colden.BF16)])
+def test_learned_trusted_range_falls_back_to_the_plain_column(L, k, precision):
+    """A network whose biases put every even direction's delta near 3 and
+    every odd one's near 0, with the trusted range [-1, 1]: the even
+    directions return the plain tree column, the odd ones the corrected
+    column, as the oracle chain with the same range (no delta lies within
+    0.5 of an end point, so both sides take the same decisions)."""
+    rho, tree, geom, T = _setup(L, 300 + L)
+    nd, H = geom.n_dir, 128
+    p = synth.mlp_init(nd, H, 300 + L, out_scale=0.05)
+    p[-nd:] = np.where(np.arange(nd) % 2 == 0, 3.0, 0.0)
+    net = colden.Net(nd, H, p)
+    assert net.delta_range() == (-math.inf, math.inf)
+    rho_m = rho.reshape(-1).cpu().numpy().astype(np.float64)
+    ms = _sample(tree.n_leaf, 2000, 301 + L)
+    ij = _ijk_of(ms)
+    mu, sinv = ol.normaliser(ol.features(_oracle_slots(T, L, geom.dirs, ms),
+                                         rho_m[(ij[:, 2] * (1 << L) + ij[:, 1]) * (1 << L) + ij[:, 0]]))
+    st = net.state()
+    st["mu"], st["sinv"] = mu.astype(np.float32), sinv.astype(np.float32)
+    net.load_state(st)
+    net.set_delta_range(-1.0, 1.0)
+    assert net.delta_range() == (-1.0, 1.0)
+    n_h = torch.full((tree.n_leaf * nd,), -1.0, device="cuda")
+    sh = torch.full((tree.n_leaf,), -1.0, device="cuda")
+    colden.column_density(tree, geom, n_h=n_h, shield=sh, net=net, precision=precision)
+    torch.cuda.synchronize()
+    colden.device_status()
+    m = _sample(tree.n_leaf, k, 302 + L)
+    slots = _oracle_slots(T, L, geom.dirs, m)
+    ij = _ijk_of(m)
+    nv = rho_m[(ij[:, 2] * (1 << L) + ij[:, 1]) * (1 << L) + ij[:, 0]]
+    delta, _ = ol.forward(ol.unpack(p.astype(np.float64), nd, H), mu.astype(np.float32).astype(np.float64),
+                          sinv.astype(np.float32).astype(np.float64), ol.features(slots, nv))
+    even = np.arange(nd) % 2 == 0
+    assert np.all(np.abs(delta[:, even]) > 1.5) and np.all(np.abs(delta[:, ~even]) < 0.5)
+    plain = ol.tree_total(slots)
+    want = ol.apply(plain, delta, -1.0, 1.0)
+    assert np.array_equal(want[:, even], plain[:, even])
+    got = n_h.reshape(-1, nd)[torch.from_numpy(m).cuda()].cpu().numpy().astype(np.float64)
+    rel = np.abs(got - want) / want
+    tol = 1e-4 if precision == colden.FP32 else 1.5e-2
+    assert rel.max() < tol, rel.max()
+    # without the range, the even directions would be ~e^3 larger
+    assert np.all(got[:, even] < 2.0 * plain[:, even])
+    got_sh = sh[torch.from_numpy(m).cuda()].cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got_sh - oracle.shield(want))) < (2e-5 if precision == colden.FP32 else 2e-3)
+    # an empty range: the plain column everywhere
+    net.set_delta_range(1.0, -1.0)
+    colden.column_density(tree, geom, n_h=n_h, net=net, precision=precision)
+    got = n_h.reshape(-1, nd)[torch.from_numpy(m).cuda()].cpu().numpy().astype(np.float64)
+    assert (np.abs(got - plain) / plain).max() < tol
+
+
+def test_fit_delta_range_and_checkpoint(tmp_path):
+    """The fitted range is the finite targets' range widened by the margin
+    (FP32 ends), it survives save / load, and a NaN end is refused."""
+    net, _ = _net(12, 16, seed=5)
+    y_np = np.random.default_rng(5).normal(size=10007).astype(np.float32)
+    y_np[[3, 77, 5000]] = [np.nan, np.inf, -np.inf]
+    lo, hi = net.fit_delta_range(torch.from_numpy(y_np).cuda(), 0.25)
+    wlo, whi = ol.delta_range(y_np.astype(np.float64), 0.25)
+    assert lo == float(np.float32(wlo)) and hi == float(np.float32(whi))
+    path = str(tmp_path / "net.npz")
+    net.save(path)
+    assert colden.Net.load(path).delta_range() == (lo, hi)
+    lo, hi = net.fit_delta_range(torch.full((5,), float("nan"), device="cuda"), 0.0)
+    assert lo > hi
+    with pytest.raises(colden.ColdenError):
+        net.set_delta_range(float("nan"), 1.0)
+    with pytest.raises(colden.ColdenError):
+        net.fit_delta_range(torch.zeros(3, device="cuda"), -1.0)
 
 
 def test_learned_bf16_unaligned_outputs_match_aligned():
