@@ -361,11 +361,22 @@ def run_ours(args):
         return _errors(n_h.reshape(-1, nd)[rows].double().cpu().numpy(), sh[rows].double().cpu().numpy(), ref)
 
     # ---- the headline form: warm-up, timed steps with clocks sampled ----
+    # A step is the density update + evaluation captured once as a CUDA graph
+    # (cd_eval_graph) and replayed; --eager times the same calls one by one.
     step = make_step(args.precision)
     for _ in range(args.warmup):
         flush.zero_()
         step()
     torch.cuda.synchronize()
+    graph = None
+    if not args.eager:
+        graph = colden.EvalGraph(tree, geom, rho=rho, n_h=n_h, shield=sh, precision=forms[args.precision],
+                                 stream=stream)
+        for _ in range(args.warmup):
+            flush.zero_()
+            graph.launch(stream)
+        torch.cuda.synchronize()
+    timed = step if graph is None else (lambda: graph.launch(stream))
     clocks = ClockSampler(local)
     colden.stats_reset(timing=False)
     if dist:
@@ -373,11 +384,12 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
-    ms = _time_steps(step, flush, stream, args.steps)
+    ms = _time_steps(timed, flush, stream, args.steps)
     clk = clocks.stop()
     launches = sum(colden.stats_get(k)[0] for k in range(len(colden.KERNEL_KINDS)))
     if dist:
         dist.barrier()
+    ms_eager = _time_steps(step, flush, stream, args.steps) if graph is not None else ms
     ms = max_ranks(ms)
     value = n_leaf * nd * world / (ms / 1e3)
     kern = _kernel_breakdown(colden, step, flush, args.steps)
@@ -462,7 +474,11 @@ def run_ours(args):
                            "geometry_build_ms": geom_ms,
                            "l2": "512 MB buffer written between timed steps; N_H output (%.2f GB) > L2"
                                  % (4 * n_leaf * nd / 1e9),
-                           "parallelism": "replicas" if world > 1 else "single"},
+                           "parallelism": "replicas" if world > 1 else "single",
+                           "launch": "eager calls" if graph is None else
+                                     "update + evaluation captured once as a CUDA graph (cd_eval_graph), "
+                                     "one graph launch per step",
+                           "eager_ms_per_step": ms_eager},
                 "gpu_launches": int(launches),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic, "kernel": dom, "kernel_ms": dom_ms,
@@ -517,13 +533,22 @@ def run_amr(args):
         flush.zero_()
         step()
     torch.cuda.synchronize()
+    graph = None
+    if not args.eager:
+        graph = colden.EvalGraph(tree, geom, rho=rho, n_h=n_h, shield=sh, precision=prec, stream=stream)
+        for _ in range(args.warmup):
+            flush.zero_()
+            graph.launch(stream)
+        torch.cuda.synchronize()
+    timed = step if graph is None else (lambda: graph.launch(stream))
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
     colden.stats_reset(timing=False)
-    ms = _time_steps(step, flush, stream, args.steps)
+    ms = _time_steps(timed, flush, stream, args.steps)
     clk = clocks.stop()
     launches = sum(colden.stats_get(k)[0] for k in range(len(colden.KERNEL_KINDS)))
+    ms_eager = _time_steps(step, flush, stream, args.steps) if graph is not None else ms
     kern = _kernel_breakdown(colden, step, flush, args.steps)
     units = tree.n_leaf * nd
     peak, peak_kind = _peaks()
@@ -576,7 +601,11 @@ def run_amr(args):
                                    "(mean 30, sigma_ln 2, seed 2), 48 HEALPix dirs, N_H + shield out",
                        "leaves": int(tree.n_leaf), "leaves_per_level": np.bincount(lv["level"])[lb:].tolist(),
                        "refined_octs": int(tree.n_oct), "precision": args.precision, "build_s": build_s,
-                       "l2": "512 MB buffer written between timed steps"},
+                       "l2": "512 MB buffer written between timed steps",
+                       "launch": "eager calls" if graph is None else
+                                 "update + evaluation captured once as a CUDA graph (cd_eval_graph), "
+                                 "one graph launch per step",
+                       "eager_ms_per_step": ms_eager},
             "gpu_launches": int(launches), "kernels": kern,
             "roofline": {"bound": "hbm", "achieved": bpu * units / (dom_ms / 1e3) / 1e9, "peak": peak,
                          "unit": "GB/s", "frac": bpu * units / (dom_ms / 1e3) / 1e9 / peak, "traffic": None,
@@ -1058,6 +1087,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=3000, help="learned: Adam steps")
     ap.add_argument("--ray-leaves", type=int, default=100_000, help="learned: leaves scored against the ray-marcher")
     ap.add_argument("--eval-level", type=int, default=9, help="learned: leaf level of the evaluation field")
+    ap.add_argument("--eager", action="store_true",
+                    help="uniform / amr: time the update and evaluation as eager calls instead of a captured graph")
     ap.add_argument("--delta-margin", type=float, default=0.5,
                     help="learned: trusted delta range = training targets' range widened by this (ln units)")
     ap.add_argument("--matched-fields", type=int, default=4,

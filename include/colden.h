@@ -216,6 +216,43 @@ cd_status cd_column_density_batch(int n, const cd_tree *trees, const cd_geom *ge
 cd_status cd_column_density_host(cd_tree tree, cd_geom geom, const cd_opts *opts, const float *rho, float *n_h,
                                  float *a_v, float *shield, void *stream);
 
+/* One evaluation step captured once as a CUDA graph and replayed by one
+ * launch (csrc/graph.cu).  cd_eval_graph_create runs the step once eagerly on
+ * `stream` (allocating every buffer the library allocates on first use) and
+ * synchronises it, then captures on a private stream: cd_tree_update(tree,
+ * rho, device) when rho is not NULL, then cd_column_density(tree, geom, opts,
+ * n_h, a_v, shield), with the evaluation's fork and join over the tree's side
+ * streams.  cd_eval_graph_launch enqueues the whole step on `stream` as one
+ * graph launch: the same kernels with the same arguments, so the outputs are
+ * bitwise those of the eager calls on the densities that rho holds at the
+ * time of the launch (without rho, on the tree's current densities).
+ *   rho      device [n_leaf] in the tree's output order, or NULL; read by
+ *            every launch, caller-owned, must stay allocated
+ *   n_h, a_v, shield   as cd_column_density; caller-owned, must stay allocated
+ * The graph holds the device pointers of the tree, the geometry and the
+ * network as they were at capture.  Every free of library-owned device memory
+ * (a tree, geometry, network or batch freed; a tree's workspace reallocated by
+ * an evaluation with another direction count; a network's scratch grown) makes
+ * every later launch of every graph return CD_EINVAL without launching
+ * anything, as does a change of the network's parameters (training,
+ * cd_net_set_state) or trusted range; create the graph again.  A learned
+ * graph (opts->net) must hold the update (rho != NULL), because the learned
+ * form reuses its per-level sums while the host records them as current.
+ * Launches add the recorded kernels to cd_stats_get's counts (not their
+ * times); the capture itself counts nothing.  Creation must not happen while
+ * `stream` is capturing.
+ * Errors: CD_EINVAL (NULL handles or out, another current device, a learned
+ * graph without rho), the errors of the eager step, CD_ECUDA when the capture
+ * or the instantiation fails. */
+typedef struct cd_eval_graph_s *cd_eval_graph;
+cd_status cd_eval_graph_create(cd_tree tree, cd_geom geom, const cd_opts *opts, const float *rho, float *n_h,
+                               float *a_v, float *shield, void *stream, cd_eval_graph *out);
+cd_status cd_eval_graph_launch(cd_eval_graph graph, void *stream);
+/* Kernels one launch runs (any pointer may be NULL). */
+cd_status cd_eval_graph_info(cd_eval_graph graph, int64_t *kernels);
+/* Synchronises the device, then frees the graph; NULL is ignored. */
+void cd_eval_graph_free(cd_eval_graph graph);
+
 /* A batch captured once into a single CUDA graph.  cd_batch_create evaluates
  * the batch once eagerly (allocating every box's scratch), then autotunes it:
  * each candidate form is captured into a graph and its replay timed, and the

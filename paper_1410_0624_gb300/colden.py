@@ -32,6 +32,7 @@ EXPORTS = (
     "cd_debug_wait_polls", "cd_debug_batch_form", "cd_stats_flops",
     "cd_tree_save", "cd_tree_load", "cd_geom_save", "cd_geom_load", "cd_geom_hash", "cd_fnv1a64",
     "cd_checked_status", "cd_debug_check_probe", "cd_column_density_host",
+    "cd_eval_graph_create", "cd_eval_graph_launch", "cd_eval_graph_info", "cd_eval_graph_free",
     # include/colden_learned.h
     "cd_adam_default", "cd_net_num_params", "cd_raymarch", "cd_learned_features", "cd_learned_targets",
     "cd_net_create", "cd_net_fit_normaliser", "cd_net_forward", "cd_net_loss_grad", "cd_net_train_step",
@@ -39,6 +40,7 @@ EXPORTS = (
     "cd_net_get_delta_range", "cd_net_fit_delta_range",
 )
 _VOID = ("cd_opts_default", "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_stats_reset", "cd_batch_free",
+         "cd_eval_graph_free",
          "cd_adam_default", "cd_net_free", "cd_net_num_params", "cd_debug_wait_polls", "cd_debug_batch_form")
 K_RESTRICT, K_SHELL, K_LEAF, K_OTHER, K_NET, K_FEATURES, K_RAYMARCH, K_LEARNED, K_HEATING = range(9)
 KERNEL_KINDS = ("restrict", "shell", "leaf", "other", "net", "features", "raymarch", "learned", "heating")
@@ -116,6 +118,11 @@ def load(build_if_missing: bool = False):
     L.cd_batch_run.argtypes = [P, P]
     L.cd_batch_info.argtypes = [P, ctypes.POINTER(I), P, ctypes.POINTER(I64)]
     L.cd_batch_plan.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), P]
+    L.cd_eval_graph_create.argtypes = [P, P, ctypes.POINTER(Opts), P, P, P, P, P, ctypes.POINTER(P)]
+    L.cd_eval_graph_launch.argtypes = [P, P]
+    L.cd_eval_graph_info.argtypes = [P, ctypes.POINTER(I64)]
+    L.cd_eval_graph_free.argtypes = [P]
+    L.cd_eval_graph_free.restype = None
     L.cd_batch_free.argtypes = [P]
     L.cd_batch_free.restype = None
     L.cd_tree_info.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I64)]
@@ -586,6 +593,45 @@ def column_density_batch(trees, geoms, n_h=None, a_v=None, shield=None, precisio
     _check(load().cd_column_density_batch(n, _ptr_array(trees, lambda t: t.handle.value),
                                           _ptr_array(geoms, lambda g: g.handle.value), ctypes.byref(o),
                                           *outs, ctypes.c_void_p(_stream_ptr(stream))))
+
+
+class EvalGraph:
+    """cd_eval_graph: one step (the update from the device buffer rho, if
+    given, then the evaluation into n_h / a_v / shield) captured once as a
+    CUDA graph; launch() replays it (see include/colden.h)."""
+
+    def __init__(self, tree: Tree, geom: Geometry, rho=None, n_h=None, a_v=None, shield=None,
+                 precision: int = FP32, av_per_nh: float = 1.0 / 1.87e21, shield_k: float = 2.5, net=None,
+                 stream=None):
+        self._keep = (tree, geom, rho, n_h, a_v, shield, net)
+        o = opts_default()
+        o.net = net.handle.value if net is not None else None
+        o.precision, o.av_per_nh, o.shield_k = int(precision), float(av_per_nh), float(shield_k)
+        outs = _outputs(tree, geom, n_h, a_v, shield)
+        r = _dptr(rho, tree.n_leaf, tree.device, "rho")
+        h = ctypes.c_void_p()
+        _check(load().cd_eval_graph_create(tree.handle, geom.handle, ctypes.byref(o), r, *outs,
+                                           ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(load().cd_eval_graph_launch(self._h, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def kernels(self) -> int:
+        n = ctypes.c_int64()
+        _check(load().cd_eval_graph_info(self._h, ctypes.byref(n)))
+        return n.value
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().cd_eval_graph_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 class Batch:

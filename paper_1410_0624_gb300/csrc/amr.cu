@@ -644,9 +644,9 @@ void free_tc_lists(cd_tree t)
 {
     for (int k = 0; k <= CD_MAXL; ++k)
         for (TcList *L : {&t->tc_ref[k], &t->tc_oct[k]}) {
-            if (L->key) cudaFree(L->key);
-            if (L->out) cudaFree(L->out);
-            if (L->tiles) cudaFree(L->tiles);
+            if (L->key) cd::lib_free(L->key);
+            if (L->out) cd::lib_free(L->out);
+            if (L->tiles) cd::lib_free(L->tiles);
             *L = TcList();
         }
 }
@@ -772,10 +772,10 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
         const cd_status pin = check_workspace_pinned(t, nd);
         if (pin != CD_OK) return pin;
         for (int k = 0; k <= CD_MAXL; ++k) {
-            if (t->ws.S[k]) cudaFree(t->ws.S[k]);
+            if (t->ws.S[k]) cd::lib_free(t->ws.S[k]);
             t->ws.S[k] = nullptr;
         }
-        if (t->ws.E) cudaFree(t->ws.E);
+        if (t->ws.E) cd::lib_free(t->ws.E);
         t->ws.E = nullptr;
         t->ws.ndir = 0;
         for (int k = 3; k <= L - 2; ++k)

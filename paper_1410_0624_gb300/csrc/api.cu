@@ -38,10 +38,10 @@ void set_error(const char *fmt, ...)
 static void free_workspace(cd_tree t)
 {
     for (int l = 0; l <= CD_MAXL; ++l) {
-        if (t->ws.S[l]) cudaFree(t->ws.S[l]);
+        if (t->ws.S[l]) cd::lib_free(t->ws.S[l]);
         t->ws.S[l] = nullptr;
     }
-    if (t->ws.E) cudaFree(t->ws.E);
+    if (t->ws.E) cd::lib_free(t->ws.E);
     t->ws.E = nullptr;
     t->ws.ndir = 0;
 }
@@ -169,7 +169,7 @@ void free_host_io(cd_tree t)
 {
     cd_tree_s::HostIO &h = t->hio;
     for (float *p : {h.rho, h.nh, h.av, h.sh})
-        if (p) cudaFree(p);
+        if (p) cd::lib_free(p);
     if (h.copy) cudaStreamDestroy(h.copy);
     for (cudaEvent_t e : h.ev)
         if (e) cudaEventDestroy(e);
@@ -182,7 +182,7 @@ cd_status ensure_host_io(cd_tree t, int64_t nh_elems, bool rho, bool nh, bool av
     cd_tree_s::HostIO &h = t->hio;
     if (h.nh_elems < nh_elems) {
         for (float **p : {&h.nh, &h.av}) {
-            if (*p) cudaFree(*p);
+            if (*p) cd::lib_free(*p);
             *p = nullptr;
         }
         h.nh_elems = nh_elems;
@@ -287,7 +287,7 @@ cd_status cd_build_tree_uniform(int leaf_level, double box_cm, const float *rho,
     cd_status st = CD_OK;
     float *staging = nullptr;
     auto fail = [&](cd_status code) {
-        if (staging) cudaFree(staging);
+        if (staging) cd::lib_free(staging);
         cd_tree_free(t);
         return code;
     };
@@ -329,7 +329,7 @@ cd_status cd_build_tree_uniform(int leaf_level, double box_cm, const float *rho,
             set_error("tree build failed: %s", cudaGetErrorString(cudaGetLastError()));
             return fail(CD_ECUDA);
         }
-        cudaFree(staging);
+        cd::lib_free(staging);
         staging = nullptr;
     }
     *out = t;
@@ -813,18 +813,18 @@ void cd_tree_free(cd_tree t)
     free_level_sums(t);
     free_tc_lists(t);
     for (int l = 0; l <= CD_MAXL; ++l) {
-        if (t->rho_lvl[l]) cudaFree(t->rho_lvl[l]);
-        if (t->rho_brick[l]) cudaFree(t->rho_brick[l]);
+        if (t->rho_lvl[l]) cd::lib_free(t->rho_lvl[l]);
+        if (t->rho_brick[l]) cd::lib_free(t->rho_brick[l]);
     }
-    if (t->rho_leaf) cudaFree(t->rho_leaf);
+    if (t->rho_leaf) cd::lib_free(t->rho_leaf);
     for (int l = 0; l <= CD_MAXL; ++l) {
-        if (t->ref_key[l]) cudaFree(t->ref_key[l]);
-        if (t->ref_parent[l]) cudaFree(t->ref_parent[l]);
+        if (t->ref_key[l]) cd::lib_free(t->ref_key[l]);
+        if (t->ref_parent[l]) cd::lib_free(t->ref_parent[l]);
     }
     for (void *p : {(void *)t->deep_key, (void *)t->deep_paint, (void *)t->oct_key, (void *)t->oct_parent,
                     (void *)t->oct_leaf, (void *)t->oct_rho8,
                     (void *)t->leaf_key, (void *)t->leaf_lvl, (void *)t->leaf_src})
-        if (p) cudaFree(p);
+        if (p) cd::lib_free(p);
     delete[] t->leaf_level_h;
     delete[] t->leaf_ijk_h;
     delete[] t->leaf_src_h;
@@ -835,14 +835,14 @@ void cd_geom_free(cd_geom g)
 {
     if (!g) return;
     cudaDeviceSynchronize();
-    if (g->rays_dev && g->rays_dev != g->dirs_dev) cudaFree(g->rays_dev);
-    if (g->dirs_dev) cudaFree(g->dirs_dev);
+    if (g->rays_dev && g->rays_dev != g->dirs_dev) cd::lib_free(g->rays_dev);
+    if (g->dirs_dev) cd::lib_free(g->dirs_dev);
     for (int t = 0; t < 4; ++t) {
-        if (g->tab[t]) cudaFree(g->tab[t]);
-        if (g->cmax[t]) cudaFree(g->cmax[t]);
+        if (g->tab[t]) cd::lib_free(g->tab[t]);
+        if (g->cmax[t]) cd::lib_free(g->cmax[t]);
     }
-    if (g->kloc) cudaFree(g->kloc);
-    if (g->wb) cudaFree(g->wb);
+    if (g->kloc) cd::lib_free(g->kloc);
+    if (g->wb) cd::lib_free(g->wb);
     if (g->rays_host != g->dirs_host) delete[] g->rays_host;
     delete[] g->dirs_host;
     delete[] g->custom;

@@ -131,7 +131,7 @@ cd_status enqueue(cd_batch_s &b, int W, cudaStream_t s)
 void plan_free(Plan &P)
 {
     for (void *p : P.allocs)
-        if (p) cudaFree(p);
+        if (p) cd::lib_free(p);
     P = Plan();
 }
 
@@ -432,7 +432,7 @@ cd_status tune_form(cudaStream_t s, F &&enq, Tuned &out)
 void destroy(cd_batch_s *b)
 {
     plan_free(b->plan);
-    if (b->keys512) cudaFree(b->keys512);
+    if (b->keys512) cd::lib_free(b->keys512);
     if (b->pinned)
         for (size_t i = 0; i < b->trees.size(); ++i)
             if (std::find(b->trees.begin(), b->trees.begin() + i, b->trees[i]) == b->trees.begin() + i)

@@ -281,6 +281,15 @@ void free_level_sums(cd_tree t);
 
 // stats.cu: per-launch timing is on (cd_stats_reset(1))
 bool stats_timing();
+// Frees library-owned device memory and advances a process-wide count, so
+// that a captured evaluation graph (cd_eval_graph) refuses to replay once a
+// buffer it may reference has been freed or reallocated.
+cudaError_t lib_free(void *p);
+int64_t free_generation();
+// launch counters and flops by kind (CD_K_COUNT entries): a copy, and adding
+// sign x counts (a graph replay adds what its capture recorded)
+void stats_snapshot(int64_t *count, double *flops);
+void stats_add(const int64_t *count, const double *flops, int sign = 1);
 
 // api.cu: the side streams of a tree.  Fork makes both side streams wait for
 // the work enqueued on s so far; join() (or the destructor, on an early

@@ -323,15 +323,15 @@ void free_level_sums(cd_tree t)
 {
     LevelSums &lv = t->lv;
     for (int k = 0; k <= CD_MAXL; ++k) {
-        if (lv.C[k]) cudaFree(lv.C[k]);
+        if (lv.C[k]) cd::lib_free(lv.C[k]);
         lv.C[k] = nullptr;
     }
     for (int i = 0; i < 4; ++i) {
-        if (lv.Et[i]) cudaFree(lv.Et[i]);
+        if (lv.Et[i]) cd::lib_free(lv.Et[i]);
         lv.Et[i] = nullptr;
     }
     for (float **p : {&lv.x, &lv.n_tree, &lv.delta}) {
-        if (*p) cudaFree(*p);
+        if (*p) cd::lib_free(*p);
         *p = nullptr;
     }
     lv.rows = 0;
@@ -362,7 +362,7 @@ cd_status column_density_learned(cd_tree t, cd_geom g, const cd_opts &o, float *
     const int64_t chunk = std::min<int64_t>(kChunkRows, t->n_leaf);
     if (lv.rows < chunk) {
         for (float **p : {&lv.x, &lv.n_tree, &lv.delta}) {
-            if (*p) cudaFree(*p);
+            if (*p) cd::lib_free(*p);
             *p = nullptr;
         }
         lv.rows = 0;
@@ -638,7 +638,7 @@ cd_status cd_net_fit_delta_range(cd_net net, int64_t n, const float *y, double m
     const bool ok = cudaGetLastError() == cudaSuccess &&
                     cudaMemcpyAsync(h, part, sizeof(h), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
                     cudaStreamSynchronize(s) == cudaSuccess;
-    cudaFree(part);
+    cd::lib_free(part);
     if (!ok) {
         set_error("delta range reduction failed: %s", cudaGetErrorString(cudaGetLastError()));
         return CD_ECUDA;
@@ -674,7 +674,7 @@ void cd_net_free(cd_net net)
     cudaDeviceSynchronize();
     for (float *p : {net->p, net->m, net->v, net->grad, net->mu, net->sinv, net->act.U, net->act.Z1, net->act.A1,
                      net->act.Z2, net->act.A2, net->act.D, net->act.G, net->act.part, net->act.red})
-        if (p) cudaFree(p);
+        if (p) cd::lib_free(p);
     net_free_tc(net);
     delete net;
 }

@@ -295,7 +295,7 @@ template <typename T>
 cd_status grow(T **p, size_t *cap, size_t need)
 {
     if (*cap >= need) return CD_OK;
-    if (*p) cudaFree(*p);
+    if (*p) cd::lib_free(*p);
     *p = nullptr;
     *cap = 0;
     if (cudaMalloc(p, need * sizeof(T)) != cudaSuccess) {
@@ -335,7 +335,7 @@ cd_status net_reserve(cd_net net, int64_t rows)
     Activations &a = net->act;
     if (a.cap >= rows) return CD_OK;
     for (float *p : {a.U, a.Z1, a.A1, a.Z2, a.A2, a.D, a.G})
-        if (p) cudaFree(p);
+        if (p) cd::lib_free(p);
     a.U = a.Z1 = a.A1 = a.Z2 = a.A2 = a.D = a.G = nullptr;
     a.cap = 0;
     const NetLayout &L = net->lay;

@@ -913,8 +913,8 @@ cd_status column_density_learned_tc(cd_tree t, cd_geom g, const cd_opts &o, floa
     const TcLayout &T = ts->lay;
     const int64_t n_blocks = (t->n_oct + 15) / 16;
     if (ts->cap < t->n_oct) {
-        if (ts->h) cudaFree(ts->h);
-        if (ts->ext) cudaFree(ts->ext);
+        if (ts->h) cd::lib_free(ts->h);
+        if (ts->ext) cd::lib_free(ts->ext);
         ts->h = nullptr;
         ts->ext = nullptr;
         ts->cap = 0;
@@ -988,9 +988,9 @@ void net_free_tc(cd_net net)
 {
     TcState *st = static_cast<TcState *>(net->tc);
     if (!st) return;
-    if (st->buf) cudaFree(st->buf);
-    if (st->h) cudaFree(st->h);
-    if (st->ext) cudaFree(st->ext);
+    if (st->buf) cd::lib_free(st->buf);
+    if (st->h) cd::lib_free(st->h);
+    if (st->ext) cd::lib_free(st->ext);
     delete st;
     net->tc = nullptr;
 }

@@ -2,6 +2,7 @@
 // (cd_stats_reset / cd_stats_get).  Every kernel launch of the library goes
 // through a LaunchScope, so the counters are the library's own claim of how
 // many kernels it ran.
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -57,6 +58,34 @@ const char *const kKindRange[CD_K_COUNT] = {"colden:restrict", "colden:shell",  
 
 NvtxRange::NvtxRange(const char *name) { nvtxRangePushA(name); }
 NvtxRange::~NvtxRange() { nvtxRangePop(); }
+
+static std::atomic<int64_t> g_free_gen{0};
+
+cudaError_t lib_free(void *p)
+{
+    g_free_gen.fetch_add(1);
+    return cudaFree(p);
+}
+
+int64_t free_generation() { return g_free_gen.load(); }
+
+void stats_snapshot(int64_t *count, double *flops)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (int k = 0; k < CD_K_COUNT; ++k) {
+        count[k] = g_count[k];
+        flops[k] = g_flops[k];
+    }
+}
+
+void stats_add(const int64_t *count, const double *flops, int sign)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (int k = 0; k < CD_K_COUNT; ++k) {
+        g_count[k] += sign * count[k];
+        g_flops[k] += sign * flops[k];
+    }
+}
 
 bool stats_timing()
 {
