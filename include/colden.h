@@ -226,8 +226,9 @@ cd_status cd_column_density_host(cd_tree tree, cd_geom geom, const cd_opts *opts
  * graph launch: the same kernels with the same arguments, so the outputs are
  * bitwise those of the eager calls on the densities that rho holds at the
  * time of the launch (without rho, on the tree's current densities).
- *   rho      device [n_leaf] in the tree's output order, or NULL; read by
- *            every launch, caller-owned, must stay allocated
+ *   rho      device [n_leaf] in cd_tree_update's layout (a uniform tree's
+ *            [z][y][x] grid, an AMR tree's original leaf order), or NULL;
+ *            read by every launch, caller-owned, must stay allocated
  *   n_h, a_v, shield   as cd_column_density; caller-owned, must stay allocated
  * The graph holds the device pointers of the tree, the geometry and the
  * network as they were at capture.  Every free of library-owned device memory
