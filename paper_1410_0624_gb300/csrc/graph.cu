@@ -57,6 +57,12 @@ cd_status cd_eval_graph_create(cd_tree tree, cd_geom geom, const cd_opts *opts, 
         return CD_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CD_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) {
+        set_error("the stream is capturing: the graph's eager first step cannot run inside a capture");
+        return CD_EINVAL;
+    }
     // one eager step first: every buffer that the library allocates on first
     // use exists before the capture (no allocation may happen inside it)
     cd_status st = CD_OK;

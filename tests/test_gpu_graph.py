@@ -181,3 +181,69 @@ def test_graph_is_refused_after_a_free_and_can_be_recreated():
     g.free()
     torch.cuda.synchronize()
     colden.device_status()
+
+
+@pytest.mark.parametrize("mode,precision", [(colden.MODE_CONE, colden.BF16), (colden.MODE_INSITU, colden.FP32)])
+def test_graph_of_the_cone_and_insitu_forms(mode, precision):
+    L = 6
+    rho0 = _uniform_field(L, 9)
+    tree = colden.build_tree_uniform(rho0.reshape((1 << L,) * 3), 10 * PC)
+    geom = colden.precompute_geometry("healpix", 1, mode=mode)
+    buf = rho0.clone()
+    n_h, a_v, sh = _outs(tree, geom)
+    g = colden.EvalGraph(tree, geom, rho=buf, n_h=n_h, a_v=a_v, shield=sh, precision=precision)
+    new = _uniform_field(L, 10)
+    buf.copy_(new)
+    g.launch()
+    torch.cuda.synchronize()
+    got = (n_h.clone(), a_v.clone(), sh.clone())
+    want = _eager(tree, geom, new, precision)
+    for x, y in zip(got, want):
+        assert torch.equal(x, y)
+
+
+def test_graph_captured_while_per_launch_timing_is_on():
+    """With per-launch timing on the evaluation runs in order on one stream;
+    its capture holds no timing events and replays match the eager step."""
+    L = 6
+    rho0 = _uniform_field(L, 11)
+    tree = colden.build_tree_uniform(rho0.reshape((1 << L,) * 3), 10 * PC)
+    geom = colden.precompute_geometry("healpix", 2)
+    buf = rho0.clone()
+    n_h, a_v, sh = _outs(tree, geom)
+    colden.stats_reset(timing=True)
+    try:
+        g = colden.EvalGraph(tree, geom, rho=buf, n_h=n_h, shield=sh, precision=colden.BF16)
+        new = _uniform_field(L, 12)
+        buf.copy_(new)
+        g.launch()
+        torch.cuda.synchronize()
+        assert colden.stats_get(colden.K_LEAF)[0] >= 2      # the eager first step and the replay
+    finally:
+        colden.stats_reset(timing=False)
+    got = (n_h.clone(), sh.clone())
+    want = _eager(tree, geom, new, colden.BF16)
+    assert torch.equal(got[0], want[0]) and torch.equal(got[1], want[2])
+
+
+def test_graph_creation_on_a_capturing_stream_is_refused():
+    L = 5
+    rho0 = _uniform_field(L, 13)
+    tree = colden.build_tree_uniform(rho0.reshape((1 << L,) * 3), 10 * PC)
+    geom = colden.precompute_geometry("healpix", 1)
+    n_h, a_v, sh = _outs(tree, geom)
+    colden.column_density(tree, geom, n_h=n_h, precision=colden.FP32)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    outer = torch.cuda.CUDAGraph()
+    err = None
+    with torch.cuda.graph(outer, stream=s):
+        try:
+            colden.EvalGraph(tree, geom, n_h=n_h, precision=colden.FP32, stream=torch.cuda.current_stream())
+        except colden.ColdenError as e:
+            err = e
+        colden.column_density(tree, geom, n_h=n_h, precision=colden.FP32, stream=torch.cuda.current_stream())
+    assert err is not None and "capturing" in str(err)
+    outer.replay()
+    torch.cuda.synchronize()
+    colden.device_status()
