@@ -162,9 +162,11 @@ __global__ void fill_deep(const uint64_t *__restrict__ keys, const int8_t *__res
     }
 }
 
-// Sibling densities of every oct: child o at level k+1 from the dense array,
-// or from the leaves when k+1 is the finest level.  One launch over the octs
-// of every level (they are stored level by level, oct_begin[k] .. oct_begin[k+1]).
+// Sibling densities of every oct: a leaf child's own density (its row in the
+// output order: an oct whose children are all leaves reads 8 consecutive
+// values), a refined child's volume mean from the dense array of level k+1.
+// One launch over the octs of every level (they are stored level by level,
+// oct_begin[k] .. oct_begin[k+1]).
 struct Rho8Args {
     const uint64_t *okey;
     const int32_t *oleaf;
@@ -184,15 +186,18 @@ __global__ void gather_rho8(const __grid_constant__ Rho8Args A)
         int k = 0;
         while (k + 1 < A.nlev && i >= A.begin[k + 1]) ++k;
         const float *dense_k1 = A.dense[k];
+        const int32_t row = A.oleaf[e];
         float v;
-        if (dense_k1) {
+        if (row >= 0) {
+            v = A.rho_leaf[row];
+        } else if (dense_k1) {
             const int64_t side = (int64_t)1 << (k + 1);
             const uint64_t m = A.okey[i];
             const int64_t x = 2 * (int64_t)compact3(m) + (o & 1), y = 2 * (int64_t)compact3(m >> 1) + ((o >> 1) & 1),
                           z = 2 * (int64_t)compact3(m >> 2) + ((o >> 2) & 1);
             v = dense_k1[(z * side + y) * side + x];
         } else {
-            v = A.rho_leaf[A.oleaf[e]];
+            v = 0.f;   // not reached: the finest octs' children are all leaves
         }
         A.rho8[e] = v;
     }
