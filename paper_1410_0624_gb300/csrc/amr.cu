@@ -633,6 +633,43 @@ cd_status build_amr(cd_tree t, int base, int lmax, int64_t n, const int8_t *leve
         if (!up((void **)&t->deep_paint, paint.data(), paint.size())) return st;
         t->sparse_finest = 1;
     }
+    // the read part of level lm = lf-1 when it lies above the base level:
+    // level-(lm-1) cells around the parents of the octs of level lm and around
+    // the grandparents of the octs of level lf
+    if (t->sparse_finest && lmax - 2 > base) {
+        const int lm = lmax - 2;
+        const int64_t ps = (int64_t)1 << (lm - 1);
+        std::vector<uint64_t> mid;
+        auto around = [&](uint64_t a) {
+            const int64_t ax = compact3(a), ay = compact3(a >> 1), az = compact3(a >> 2);
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int64_t x = ax + dx, y = ay + dy, z = az + dz;
+                        if (x < 0 || y < 0 || z < 0 || x >= ps || y >= ps || z >= ps) continue;
+                        mid.push_back(morton3((uint32_t)x, (uint32_t)y, (uint32_t)z));
+                    }
+        };
+        for (uint64_t o : oct[lm]) around(o >> 3);
+        for (uint64_t o : oct[lm + 1]) around(o >> 6);
+        std::sort(mid.begin(), mid.end());
+        mid.erase(std::unique(mid.begin(), mid.end()), mid.end());
+        std::vector<int8_t> paint(mid.size());
+        for (size_t j = 0; j < mid.size(); ++j)
+            paint[j] = std::binary_search(ref[lm - 1].begin(), ref[lm - 1].end(), mid[j]) ? 0 : 1;
+        t->n_mid = (int64_t)mid.size();
+        if (!up((void **)&t->mid_key, mid.data(), mid.size() * 8)) return st;
+        if (!up((void **)&t->mid_paint, paint.data(), paint.size())) return st;
+        const size_t cells = (size_t)1 << (3 * lm);
+        // (memsets are ordered on the legacy stream only: finished here, before any
+        // stream writes the painted part)
+        if (cudaMemset(t->rho_lvl[lm], 0xff, cells * 4) != cudaSuccess ||
+            cudaMemset(t->rho_brick[lm], 0xff, cells * 2) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+            set_error("AMR tree initialisation failed");
+            return CD_ECUDA;
+        }
+        t->sparse_mid = 1;
+    }
     // tensor-core lists of the levels the BF16 contraction serves (receiving level >= 4)
     for (int k = 4; k <= lmax - 1; ++k) {
         if (k <= lmax - 2 && (st = build_tc_list(ref[k], t->ref_parent[k], t->tc_ref[k])) != CD_OK) return st;
@@ -673,8 +710,8 @@ cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s)
     for (int l = t->base; l <= lf; ++l) {
         if (l == t->base) {
             // done above
-        } else if (t->sparse_finest && l == lf) {
-            // no prolongation into the finest dense level: fill_deep paints the part that is read
+        } else if ((t->sparse_finest && l == lf) || (t->sparse_mid && l == lf - 1)) {
+            // no prolongation into the finest dense levels: fill_deep paints the part that is read
         } else if (l >= 2) {
             LaunchScope ls(CD_K_RESTRICT, s);
             prolong4<<<grid_for((int64_t)1 << (3 * l - 2), 256, 152 * 64), 256, 0, s>>>(t->rho_lvl[l - 1], l,
@@ -708,7 +745,27 @@ cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s)
                                                                          t->rho_lvl[lf], t->rho_lvl[lf - 1]);
             CD_CHECK_LAUNCH();
         }
-        if ((st = restrict_dense(t, lf - 1, s)) != CD_OK) return st;
+        if (t->sparse_mid) {
+            // level lf-2 complete (its refined cells from lf-1), restricted from
+            // there; then the read part of lf-1 and its bricks
+            if (t->n_ref[lf - 2]) {
+                LaunchScope ls(CD_K_RESTRICT, s);
+                fill_refined<<<grid_for(t->n_ref[lf - 2], 256), 256, 0, s>>>(t->ref_key[lf - 2], t->n_ref[lf - 2],
+                                                                             lf - 2, t->rho_lvl[lf - 1],
+                                                                             t->rho_lvl[lf - 2]);
+                CD_CHECK_LAUNCH();
+            }
+            if ((st = restrict_dense(t, lf - 2, s)) != CD_OK) return st;
+            if (t->n_mid) {
+                LaunchScope ls(CD_K_RESTRICT, s);
+                fill_deep<<<grid_for(t->n_mid, 256), 256, 0, s>>>(t->mid_key, t->mid_paint, t->n_mid, lf - 1,
+                                                                  t->rho_lvl[lf - 2], t->rho_lvl[lf - 1],
+                                                                  t->rho_brick[lf - 1]);
+                CD_CHECK_LAUNCH();
+            }
+        } else if ((st = restrict_dense(t, lf - 1, s)) != CD_OK) {
+            return st;
+        }
         if (t->n_deep) {
             LaunchScope ls(CD_K_RESTRICT, s);
             fill_deep<<<grid_for(t->n_deep, 256), 256, 0, s>>>(t->deep_key, t->deep_paint, t->n_deep, lf,

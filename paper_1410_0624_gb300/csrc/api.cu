@@ -821,7 +821,8 @@ void cd_tree_free(cd_tree t)
         if (t->ref_key[l]) cd::lib_free(t->ref_key[l]);
         if (t->ref_parent[l]) cd::lib_free(t->ref_parent[l]);
     }
-    for (void *p : {(void *)t->deep_key, (void *)t->deep_paint, (void *)t->oct_key, (void *)t->oct_parent,
+    for (void *p : {(void *)t->deep_key, (void *)t->deep_paint, (void *)t->mid_key, (void *)t->mid_paint,
+                    (void *)t->oct_key, (void *)t->oct_parent,
                     (void *)t->oct_leaf, (void *)t->oct_rho8,
                     (void *)t->leaf_key, (void *)t->leaf_lvl, (void *)t->leaf_src})
         if (p) cd::lib_free(p);

@@ -190,6 +190,16 @@ struct cd_tree_s {
     int64_t n_deep = 0;
     uint64_t *deep_key = nullptr;         // (device) those level-(lf-1) cells, sorted Morton keys
     int8_t *deep_paint = nullptr;         // (device) 1: not refined, its children take its value
+    // The level below it, lm = lf-1, likewise when lm > base: leaves, refined
+    // cells, and the children of the level-(lm-1) cells around the parents of
+    // the octs of level lm and the grandparents of the octs of level lf (the
+    // stencils of their shells, in-situ walks and of the deep cells' parents);
+    // the rest of level lm holds NaN from the build on, so that a read outside
+    // the painted part cannot pass unnoticed
+    int sparse_mid = 0;
+    int64_t n_mid = 0;
+    uint64_t *mid_key = nullptr;          // (device) those level-(lm-1) cells, sorted Morton keys
+    int8_t *mid_paint = nullptr;          // (device) 1: not refined, its children take its value
     uint64_t *leaf_key = nullptr;         // (device) output order: Morton key at the leaf's level
     int8_t *leaf_lvl = nullptr;           // (device) output order: level
     int64_t *leaf_src = nullptr;          // (device) output order: index in the caller's leaf arrays

@@ -194,3 +194,46 @@ def test_amr_bf16_1024_effective_sampled():
     got = n_h.reshape(-1, nd)[torch.from_numpy(sel).cuda()].double().cpu().numpy()
     assert np.max(np.abs(got - ref) / ref) <= BF16_RTOL
     assert np.max(np.abs(sh[torch.from_numpy(sel).cuda()].double().cpu().numpy() - oracle.shield(ref))) <= BF16_SHIELD_ATOL
+
+
+def _mesh3():
+    """Three refined levels above a 16^3 base (128^3 effective): the two
+    finest dense levels are filled only where read (the rest of the level
+    below the finest holds NaN), so any read outside the painted part would
+    show as a non-finite column."""
+    fine = synth.lognormal_grf(128, 30.0, 2.0, seed=23)
+    lv = synth.amr_leaves(fine, 4, [35.0, 55.0, 80.0])
+    assert len(np.unique(lv["level"])) == 4
+    return lv
+
+
+@pytest.mark.parametrize("precision,mode", [(colden.FP32, "prec"), (colden.BF16, "prec"), (colden.FP32, "insitu"),
+                                            (colden.FP32, "cone")])
+def test_amr_three_refined_levels_all_leaves(precision, mode):
+    lv = _mesh3()
+    box = 10 * PC
+    tree = colden.build_tree_amr(lv["base"], lv["lmax"], box, lv["level"], lv["ijk"], lv["rho"])
+    gmode = {"prec": colden.MODE_PREC, "insitu": colden.MODE_INSITU, "cone": colden.MODE_CONE}[mode]
+    geom = colden.precompute_geometry("healpix", 1, mode=gmode)
+    nd = geom.n_dir
+    n_h, a_v, sh = _run(tree, geom, precision=precision)
+    assert np.all(np.isfinite(n_h)) and np.all(np.isfinite(sh))
+    olv, oijk = tree.leaves()
+    T = oracle.Tree.amr(lv["base"], lv["lmax"], box, lv["level"], lv["ijk"], lv["rho"])
+    if mode == "cone":
+        sel = np.sort(np.random.default_rng(5).choice(tree.n_leaf, 400, replace=False))
+        ref = T.column_density_cone(geom.dirs, olv[sel], oijk[sel])
+        got = n_h.reshape(-1, nd)[sel]
+    else:
+        ref = T.column_density(geom.dirs, olv, oijk, mode=oracle.MODE_INSITU if mode == "insitu" else oracle.MODE_PREC)
+        got = n_h.reshape(-1, nd)
+    tol = RTOL if precision == colden.FP32 or mode == "insitu" else BF16_RTOL
+    assert np.max(np.abs(got - ref) / ref) <= tol
+    # an update to new densities gives the rebuilt tree's columns bit for bit
+    r2 = (lv["rho"] * np.random.default_rng(6).uniform(0.5, 2.0, size=len(lv["rho"]))).astype(np.float32)
+    colden.tree_update(tree, torch.from_numpy(r2).cuda())
+    a = _run(tree, geom, precision=precision)
+    b = _run(colden.build_tree_amr(lv["base"], lv["lmax"], box, lv["level"], lv["ijk"], r2), geom,
+             precision=precision)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
