@@ -428,6 +428,15 @@ cd_status cd_device_status(void *stream);
  * Never set it outside tests: the outputs of capped launches are incomplete. */
 void cd_debug_wait_polls(int64_t polls);
 
+/* Testing hook (no counterpart in the paper).  On AMR trees the BF16 leaf
+ * kernel adds each oct's far-shell prefix row (S of the parent level, §3.3)
+ * itself: a tile of 16 consecutive octs stages its parents' rows, which form
+ * one contiguous span of S, with one copy when the span is at most `rows`
+ * rows (16 by default, the staging capacity), else one row per oct.  rows = 0
+ * forces the per-oct form everywhere; the results do not change.  rows < 0 or
+ * > 16 restores the default.  Process-wide; applies to later launches. */
+void cd_debug_leaf_span(int rows);
+
 /* Bounds-checked build (no counterpart in the paper).  Built with
  * -DCOLDEN_CHECKED (libcolden_checked.so, a test build), the kernels check the
  * indices of their gathers and stores before each access; one that falls

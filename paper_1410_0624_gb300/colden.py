@@ -29,7 +29,7 @@ EXPORTS = (
     "cd_stats_get", "cd_heating",
     "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_column_density_noalloc", "cd_device_status",
     "cd_column_density_batch", "cd_batch_create", "cd_batch_run", "cd_batch_info", "cd_batch_plan", "cd_batch_free",
-    "cd_debug_wait_polls", "cd_debug_batch_form", "cd_stats_flops",
+    "cd_debug_wait_polls", "cd_debug_batch_form", "cd_stats_flops", "cd_debug_leaf_span",
     "cd_tree_save", "cd_tree_load", "cd_geom_save", "cd_geom_load", "cd_geom_hash", "cd_fnv1a64",
     "cd_checked_status", "cd_debug_check_probe", "cd_column_density_host",
     "cd_eval_graph_create", "cd_eval_graph_launch", "cd_eval_graph_info", "cd_eval_graph_free",
@@ -40,7 +40,7 @@ EXPORTS = (
     "cd_net_get_delta_range", "cd_net_fit_delta_range",
 )
 _VOID = ("cd_opts_default", "cd_tree_free", "cd_geom_free", "cd_last_error", "cd_stats_reset", "cd_batch_free",
-         "cd_eval_graph_free",
+         "cd_eval_graph_free", "cd_debug_leaf_span",
          "cd_adam_default", "cd_net_free", "cd_net_num_params", "cd_debug_wait_polls", "cd_debug_batch_form")
 K_RESTRICT, K_SHELL, K_LEAF, K_OTHER, K_NET, K_FEATURES, K_RAYMARCH, K_LEARNED, K_HEATING = range(9)
 KERNEL_KINDS = ("restrict", "shell", "leaf", "other", "net", "features", "raymarch", "learned", "heating")
@@ -101,6 +101,7 @@ def load(build_if_missing: bool = False):
     L.cd_debug_wait_polls.argtypes = [I64]
     L.cd_debug_wait_polls.restype = None
     L.cd_debug_batch_form.argtypes = [I]
+    L.cd_debug_leaf_span.argtypes = [I]
     L.cd_debug_batch_form.restype = None
     SZ = ctypes.c_size_t
     L.cd_tree_save.argtypes = [P, P, SZ, ctypes.POINTER(SZ), P]
@@ -370,6 +371,12 @@ def debug_batch_form(form: int):
     form, 1 = the persistent form where supported, negative = the autotuner
     chooses."""
     load().cd_debug_batch_form(int(form))
+
+
+def debug_leaf_span(rows: int):
+    """cd_debug_leaf_span (tests only): the widest parent span an AMR list
+    tile stages as one copy; 0 forces one row per oct, negative restores 16."""
+    load().cd_debug_leaf_span(int(rows))
 
 
 def stats_reset(timing: bool = False):

@@ -992,14 +992,9 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
         if (have_E[k]) CD_CUDA(cudaStreamWaitEvent(s_leaf, t->ev_E[k], 0));
         if (B.Sp && have_S[k - 1]) CD_CUDA(cudaStreamWaitEvent(s_leaf, t->ev_S[k - 1], 0));
         if (tc) {
-            // BF16: the parent prefix goes into E first, then the tensor-core leaf
-            // kernel takes the level's octs in tiles of 16 (csrc/leaf_tc.cu)
+            // BF16: the tensor-core leaf kernel takes the level's octs in tiles of
+            // 16 (csrc/leaf_tc.cu) and adds each oct's parent prefix row itself
             float *Ek = t->ws.E + t->oct_begin[k] * nd;
-            if (B.Sp) {
-                cd_status st = launch_add_parent_list(Ek, B.Sp, B.oparent, nd, no, s_leaf);
-                if (st != CD_OK) return st;
-                B.Sp = nullptr;
-            }
             LeafLaunch b = {};
             b.n_oct = no;
             b.nd = nd;
@@ -1008,7 +1003,9 @@ cd_status column_density_amr(cd_tree t, cd_geom g, const cd_opts &opts, float *n
             b.shield_k = (float)opts.shield_k;
             b.rho_leaf = B.rho8;
             b.E = Ek;
-            b.Sp = nullptr;
+            b.Sp = B.Sp;
+            b.oparent = B.Sp ? B.oparent : nullptr;
+            b.n_sp = B.Sp ? t->n_ref[k - 1] : 0;
             b.kloc = g->kloc;
             b.n_h = n_h;
             b.a_v = a_v;

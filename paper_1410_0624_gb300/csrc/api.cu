@@ -677,6 +677,8 @@ cd_status cd_column_density_host(cd_tree tree, cd_geom geom, const cd_opts *opts
 
 void cd_debug_wait_polls(int64_t polls) { set_leaf_tc_wait_polls(polls); }
 
+void cd_debug_leaf_span(int rows) { set_leaf_tc_span_max(rows); }
+
 cd_status cd_checked_status(int *site, int64_t *index)
 {
 #ifndef COLDEN_CHECKED

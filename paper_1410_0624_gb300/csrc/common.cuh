@@ -384,9 +384,13 @@ struct LeafLaunch {
     float *n_h, *a_v, *shield;
     // AMR list mode (leaf_tc only): oleaf[8 o + t] is the output row of child t
     // of oct o (-1: refined); rho_leaf then holds 8 densities per oct (in list
-    // order), E already includes the parent prefix and Sp is NULL
+    // order).  The parent prefix is either already in E (Sp NULL) or row
+    // oparent[o] of Sp (n_sp rows); oparent is non-decreasing along the list,
+    // so a tile's parent rows are one contiguous span of Sp
     const int32_t *oleaf;
     int64_t n_rows;           // list mode: rows of n_h / a_v / shield (the tree's leaves; bounds checks)
+    const int32_t *oparent;   // list mode with Sp: [n_oct] parent row of each oct
+    int64_t n_sp;             // list mode with Sp: rows of Sp
 };
 cd_status launch_leaf(const LeafLaunch &a, cudaStream_t s);
 
@@ -410,6 +414,8 @@ cd_status launch_leaf_tc_batch(const void *jobs, const int2 *tile_ref, int64_t t
                                int form, double flops, cudaStream_t s);
 // cd_debug_wait_polls: poll limit of the BF16 leaf kernel's pipeline waits (< 0: default)
 void set_leaf_tc_wait_polls(int64_t polls);
+// cd_debug_leaf_span: widest parent span a list tile stages as one copy (< 0: default 16)
+void set_leaf_tc_span_max(int rows);
 
 // colden_tc.cu: BF16 tensor-core shell contraction for receiving levels >= 4
 bool tc_supported(int nd);

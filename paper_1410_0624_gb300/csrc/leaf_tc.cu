@@ -34,6 +34,10 @@ constexpr int kK = 64;                  // 8 octant blocks x 8 siblings
 static __device__ int g_leaftc_fault;
 // cd_debug_wait_polls: < 0 = the default limit
 static std::atomic<int64_t> g_pipe_polls{-1};
+// cd_debug_leaf_span: list tiles stage their parents' prefix rows as one span
+// of up to this many rows (else one row per oct)
+constexpr int kSpanRows = 16;
+static std::atomic<int> g_span_max{kSpanRows};
 
 __host__ __device__ constexpr size_t align128(size_t v) { return (v + 127) & ~(size_t)127; }
 __host__ __device__ constexpr int round16(int v) { return (v + 15) & ~15; }
@@ -53,6 +57,7 @@ struct LeafTcArgs {
     uint32_t pipe_polls;       // poll limit of the pipeline waits (cd_debug_wait_polls); the exit
                                // waits for the CTA's own copies and products keep kMaxPolls
     int form;                  // kForm* bits; batched: the same for every job of the launch
+    int span_max;              // list tiles with Sp: the widest parent span staged as one copy (<= 16)
 };
 
 // what a leaf row reads and writes: the parent prefix, staged rows (bulk
@@ -81,7 +86,7 @@ __host__ __device__ inline LeafTcSmem leaf_tc_smem(int nd, int NP, int G, bool l
     S.out = align128((size_t)128 * kK * 2);
     S.st_e = 0;
     S.st_p = align128((size_t)16 * nd * 4);
-    S.st_r = S.st_p + align128((size_t)2 * nd * 4);
+    S.st_r = S.st_p + align128((size_t)(list ? 16 : 2) * nd * 4);   // list tiles: up to 16 parent rows
     S.st_l = S.st_r + 128 * 4;                     // list mode: the 16 octs' leaf rows
     S.stage_bytes = align128(S.st_l + (list ? 128 * 4 : 0));
     S.stage = S.out + align128((size_t)128 * nd * 4);
@@ -117,25 +122,45 @@ __device__ __forceinline__ int tile_octs(const LeafTcArgs &P, int64_t tile, bool
 }
 
 // a tile's inputs: E rows of its 16 octs, Sp rows of their 2 parents, 128
-// densities (list mode: no Sp, plus the octs' 128 leaf rows)
-__device__ __forceinline__ void prefetch(const LeafTcArgs &P, const LeafTcSmem &S, int64_t tile, unsigned char *st,
-                                         uint64_t *bar, bool list)
+// densities (list mode: plus the octs' 128 leaf rows, and with Sp the parent
+// rows of the tile's octs: the span pf .. pl in one copy when it is at most
+// 16 rows, else one row per oct; returns the first staged row, or -1 for the
+// per-oct layout)
+__device__ __forceinline__ int prefetch(const LeafTcArgs &P, const LeafTcSmem &S, int64_t tile, unsigned char *st,
+                                        uint64_t *bar, bool list, int pf = 0, int pl = 0)
 {
     const int nd = P.a.nd;
     const uint32_t nb = (uint32_t)tile_octs(P, tile, list);
+    const bool lsp = list && P.a.Sp;
+    const bool per_oct = lsp && pl - pf >= P.span_max;
     // checked builds: a tile outside its job's octs (or parents) copies nothing
     const int64_t o0 = tile * 16, n_oct = P.a.n_oct;
-    if (!(in_bounds(o0, n_oct, kCheckLeafTcIn) && in_bounds(o0 + nb - 1, n_oct, kCheckLeafTcIn) &&
-          (!P.a.Sp || in_bounds(tile * 2 + 1, n_oct / 8, kCheckLeafTcIn)))) {
+    bool sp_ok = true;
+    if (lsp && !per_oct)
+        sp_ok = pf <= pl && in_bounds(pf, P.a.n_sp, kCheckLeafTcIn) && in_bounds(pl, P.a.n_sp, kCheckLeafTcIn);
+    else if (P.a.Sp && !list)
+        sp_ok = in_bounds(tile * 2 + 1, n_oct / 8, kCheckLeafTcIn);
+    if (!(in_bounds(o0, n_oct, kCheckLeafTcIn) && in_bounds(o0 + nb - 1, n_oct, kCheckLeafTcIn) && sp_ok)) {
         mbar_expect_tx(bar, 0);
-        return;
+        return pf;
     }
-    const uint32_t be = nb * nd * 4, bp = P.a.Sp ? 2u * nd * 4 : 0u, br = nb * 32, bl = list ? nb * 32 : 0u;
+    const uint32_t bp = !P.a.Sp ? 0u : !list ? 2u * nd * 4 : per_oct ? nb * nd * 4 : (uint32_t)(pl - pf + 1) * nd * 4;
+    const uint32_t be = nb * nd * 4, br = nb * 32, bl = list ? nb * 32 : 0u;
     mbar_expect_tx(bar, be + bp + br + bl);
     bulk_g2s(st + S.st_e, P.a.E + tile * 16 * nd, be, bar);
-    if (P.a.Sp) bulk_g2s(st + S.st_p, P.a.Sp + tile * 2 * nd, bp, bar);
+    if (per_oct) {
+        // a span with parents that have no octs of this level in it: row by row
+        for (uint32_t o = 0; o < nb; ++o) {
+            int r = __ldg(P.a.oparent + o0 + o);
+            if (!in_bounds(r, P.a.n_sp, kCheckLeafTcIn)) r = 0;
+            bulk_g2s(st + S.st_p + (size_t)o * nd * 4, P.a.Sp + (int64_t)r * nd, nd * 4, bar);
+        }
+    } else if (P.a.Sp) {
+        bulk_g2s(st + S.st_p, P.a.Sp + (list ? (int64_t)pf : tile * 2) * nd, bp, bar);
+    }
     bulk_g2s(st + S.st_r, P.a.rho_leaf + tile * 128, br, bar);
     if (list) bulk_g2s(st + S.st_l, P.a.oleaf + tile * 128, bl, bar);
+    return per_oct ? -1 : pf;
 }
 
 // Leaf jobs of many boxes (cd_batch) walked by one persistent launch: global
@@ -293,6 +318,17 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P0, LeafBatch Bt)
         }
         s_tile[g][sl] = ref.y;
     };
+    // list tiles with a parent prefix: thread 0 reads the span of parent rows of
+    // a tile one tile before its prefetch, so that the loads' latency hides
+    // behind the current tile; s_pf holds each stage's first staged row
+    const bool lsp = kMode == 1 && P0.a.Sp != nullptr;
+    __shared__ int s_pf[4][2];
+    int pf_next = 0, pl_next = 0;
+    auto span = [&](int64_t t, int &pf, int &pl) {
+        const int nb = tile_octs(P0, t, true);
+        pf = __ldg(P0.a.oparent + t * 16);
+        pl = __ldg(P0.a.oparent + t * 16 + nb - 1);
+    };
     if (i == 0 && first < total) {
         if (kMode == 2) {
             for (int sl = 0; sl < 3; ++sl) s_job_id[g][sl] = -1;
@@ -303,7 +339,12 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P0, LeafBatch Bt)
             int64_t lt;
             bool lst;
             const LeafTcArgs J = job_of(first, lt, lst);
-            prefetch(J, S, lt, Gb + S.stage, &bar[G + 2 * g], lst);
+            int pf = 0, pl = 0;
+            if (lsp) {
+                span(lt, pf, pl);
+                if (first + stride < total) span(first + stride, pf_next, pl_next);
+            }
+            s_pf[g][0] = prefetch(J, S, lt, Gb + S.stage, &bar[G + 2 * g], lst, pf, pl);
         }
         pending[0] = true;
     }
@@ -327,7 +368,10 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P0, LeafBatch Bt)
                     int64_t lt;
                     bool ln;
                     const LeafTcArgs J = job_of(gt + stride, lt, ln);
-                    prefetch(J, S, lt, Gb + S.stage + (stg ^ 1) * S.stage_bytes, &bar[G + 2 * g + (stg ^ 1)], ln);
+                    const int pf = pf_next, pl = pl_next;
+                    if (lsp && gt + 2 * stride < total) span(gt + 2 * stride, pf_next, pl_next);
+                    s_pf[g][stg ^ 1] = prefetch(J, S, lt, Gb + S.stage + (stg ^ 1) * S.stage_bytes,
+                                                &bar[G + 2 * g + (stg ^ 1)], ln, pf, pl);
                 }
                 pending[stg ^ 1] = true;
             }
@@ -349,6 +393,8 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P0, LeafBatch Bt)
         lst = kMode == 2 ? P0.list != 0 : kList;
         tile = kMode == 2 ? (int64_t)s_tile[g][slot] : gt;
         const float *sR = reinterpret_cast<const float *>(st + S.st_r);
+        // list tiles with a parent prefix: this row's parent row (its load overlaps the product)
+        const int par = lsp && (i >> 3) < tile_octs(P, tile, true) ? __ldg(P0.a.oparent + tile * 16 + (i >> 3)) : 0;
         // ---- A row: the oct's densities in block t ----
         {
             const float4 r0 = *reinterpret_cast<const float4 *>(sR + (i & ~7));
@@ -390,7 +436,14 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P0, LeafBatch Bt)
             const bool ok = m >= 0 && in_bounds(m, lst ? P.a.n_rows : 8 * P.a.n_oct, kCheckLeafTcOut);
             const int64_t mr = ok ? m : 0;
             const float *Ei = reinterpret_cast<const float *>(st + S.st_e) + (i >> 3) * nd;
-            const float *Pi = reinterpret_cast<const float *>(st + S.st_p) + (i >> 6) * nd;
+            // the row's parent row among the staged ones: uniform tiles hold 2 parents;
+            // list tiles the span from s_pf (at most 16 rows), or one row per oct (-1)
+            int prow = i >> 6;
+            if (lsp) {
+                const int f = s_pf[g][stg];
+                prow = f < 0 ? (i >> 3) : min(max(par - f, 0), 15);
+            }
+            const float *Pi = reinterpret_cast<const float *>(st + S.st_p) + prow * nd;
             float *orow = sO + (size_t)i * nd;
             const float c2 = P.c2, avk = P.a.av_per_nh;
             // the output form is a launch constant (kernel parameter): pick the
@@ -496,7 +549,7 @@ cd_status launch_leaf_tc(const LeafLaunch &a, cudaStream_t s)
     if (nd % 4 != 0 || nd > 64 || !aligned16(a.E) || !aligned16(a.Sp) || !aligned16(a.rho_leaf) || !a.E)
         return CD_EUNSUPPORTED;
     if (!list && (n_leaf < 128 || n_leaf % 128 != 0)) return CD_EUNSUPPORTED;
-    if (list && (a.Sp || !aligned16(a.oleaf) || (a.n_h && !aligned16(a.n_h)))) return CD_EUNSUPPORTED;
+    if (list && ((a.Sp && !a.oparent) || !aligned16(a.oleaf) || (a.n_h && !aligned16(a.n_h)))) return CD_EUNSUPPORTED;
     if (n_leaf == 0) return CD_OK;
     LeafTcArgs P;
     P.a = a;
@@ -511,6 +564,7 @@ cd_status launch_leaf_tc(const LeafLaunch &a, cudaStream_t s)
         const int64_t cap = g_pipe_polls.load();
         P.pipe_polls = cap < 0 ? kMaxPolls : (uint32_t)std::min<int64_t>(cap, kMaxPolls);
     }
+    P.span_max = g_span_max.load();
     int dev = 0, smax = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -603,6 +657,8 @@ double leaf_tc_job_flops(const void *job)
 }
 
 void set_leaf_tc_wait_polls(int64_t polls) { g_pipe_polls.store(polls < 0 ? -1 : polls); }
+
+void set_leaf_tc_span_max(int rows) { g_span_max.store(rows < 0 || rows > kSpanRows ? kSpanRows : rows); }
 
 cd_status leaf_tc_fault_check()
 {

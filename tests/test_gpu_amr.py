@@ -237,3 +237,21 @@ def test_amr_three_refined_levels_all_leaves(precision, mode):
              precision=precision)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+def test_amr_bf16_parent_rows_staged_per_oct_give_the_same_columns():
+    """The BF16 leaf kernel stages the parents' prefix rows of a list tile as
+    one span (the common case) or one row per oct (spans wider than 16 rows);
+    forcing the per-oct form everywhere changes no bit."""
+    lv = _mesh3()
+    tree = colden.build_tree_amr(lv["base"], lv["lmax"], 10 * PC, lv["level"], lv["ijk"], lv["rho"])
+    geom = colden.precompute_geometry("healpix", 2)
+    a = _run(tree, geom, precision=colden.BF16)
+    colden.debug_leaf_span(0)
+    try:
+        b = _run(tree, geom, precision=colden.BF16)
+    finally:
+        colden.debug_leaf_span(-1)
+    c = _run(tree, geom, precision=colden.BF16)
+    for x, y, z in zip(a, b, c):
+        assert np.array_equal(x, y) and np.array_equal(x, z)
