@@ -846,7 +846,7 @@ def run_learned(args):
         return float(((ntv.double() * torch.exp(dv.double()) - nrv.double()).abs() / 1.87e21).mean())
 
     losses = colden.train(net, x, y, steps=args.train_steps, batch=8192, lr=2e-3, lr_final=1e-4, seed=3,
-                          val=val_dav, eval_every=250, row_weights=wrow)
+                          val=val_dav, eval_every=args.eval_every, row_weights=wrow)
     torch.cuda.synchronize()
     train_s = time.time() - t0
     best_step, best_val = min(net.val_history, key=lambda h: h[1])
@@ -967,7 +967,7 @@ def run_learned(args):
                        "training": {"fields": n_fields, "rows_per_field": rows_per, "steps": args.train_steps,
                                     "matched_fields": n_match, "matched_level": args.eval_level,
                                     "validation": "mean |A_V| error on a held-out field at level %d (seed 400), "
-                                                  "%d leaves, every 250 steps" % (args.eval_level, n_val),
+                                                  "%d leaves, every %d steps" % (args.eval_level, n_val, args.eval_every),
                                     "stop_step": int(best_step), "val_a_v_abs_mean": float(best_val),
                                     "delta_range": [d_lo, d_hi], "delta_margin": args.delta_margin,
                                     "row_sampling": "with replacement, probability proportional to the squared "
@@ -1089,6 +1089,8 @@ def main():
     ap.add_argument("--eval-level", type=int, default=9, help="learned: leaf level of the evaluation field")
     ap.add_argument("--eager", action="store_true",
                     help="uniform / amr: time the update and evaluation as eager calls instead of a captured graph")
+    ap.add_argument("--eval-every", type=int, default=50,
+                    help="learned: Adam steps between validation scores (the training stop)")
     ap.add_argument("--delta-margin", type=float, default=0.5,
                     help="learned: trusted delta range = training targets' range widened by this (ln units)")
     ap.add_argument("--matched-fields", type=int, default=4,
