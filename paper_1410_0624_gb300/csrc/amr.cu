@@ -45,17 +45,33 @@ inline unsigned grid_for(int64_t n, int block, int cap = 152 * 32)
 // Leaf densities are finite (checked on the host path), so NaN is free as a
 // marker.
 
+// Dense levels whose leaves take their values in the gather below: bit l of
+// mask set for every level that no prolongation writes afterwards
+struct LeafScatter {
+    float *dense[CD_MAXL + 1];
+    uint32_t mask;
+};
+
 // One launch for two independent passes over disjoint arrays: entries [0, n)
-// gather the caller's leaf densities into output order, entries [n, n + nr)
-// mark the base level's refined cells NaN
+// gather the caller's leaf densities into output order (and into the dense
+// array of the leaf's level when D.mask has it), entries [n, n + nr) mark the
+// base level's refined cells NaN
 __global__ void gather_and_mark(const float *__restrict__ in, const int64_t *__restrict__ src, int64_t n,
                                 float *__restrict__ out, const uint64_t *__restrict__ keys, int64_t nr, int l,
-                                float *__restrict__ dense)
+                                float *__restrict__ dense, const uint64_t *__restrict__ lkey,
+                                const int8_t *__restrict__ llvl, const __grid_constant__ LeafScatter D)
 {
     const int64_t side = (int64_t)1 << l;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n + nr; i += (int64_t)gridDim.x * blockDim.x) {
         if (i < n) {
-            out[i] = in[src[i]];
+            const float v = in[src[i]];
+            out[i] = v;
+            const int lv = llvl[i];
+            if ((D.mask >> lv) & 1u) {
+                const uint64_t m = lkey[i];
+                const int64_t sd = (int64_t)1 << lv;
+                D.dense[lv][((int64_t)compact3(m >> 2) * sd + compact3(m >> 1)) * sd + compact3(m)] = v;
+            }
         } else {
             const uint64_t m = keys[i - n];
             dense[((int64_t)compact3(m >> 2) * side + compact3(m >> 1)) * side + compact3(m)] = __int_as_float(0x7fc00000);
@@ -697,20 +713,30 @@ void free_tc_lists(cd_tree t)
 cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s)
 {
     const int lmax = t->L, lf = lmax - 1;
+    // levels that no prolongation writes: their leaves go in with the gather
+    const auto prolonged = [&](int l) {
+        return l != t->base && !(t->sparse_finest && l == lf) && !(t->sparse_mid && l == lf - 1);
+    };
+    LeafScatter D = {};
+    for (int l = t->base; l <= lf; ++l) {
+        D.dense[l] = t->rho_lvl[l];
+        if (!prolonged(l)) D.mask |= 1u << l;
+    }
     {
-        // leaves into output order, and the base level's refined cells marked NaN
+        // leaves into output order (and into the unprolonged dense levels), and
+        // the base level's refined cells marked NaN
         const int64_t nr = t->n_ref[t->base];
         LaunchScope ls(CD_K_RESTRICT, s);
-        gather_and_mark<<<grid_for(t->n_leaf + nr, 256), 256, 0, s>>>(rho_dev, t->leaf_src, t->n_leaf, t->rho_leaf,
-                                                                        t->ref_key[t->base], nr, t->base,
-                                                                        t->rho_lvl[t->base]);
+        gather_and_mark<<<grid_for(t->n_leaf + nr, 256), 256, 0, s>>>(
+            rho_dev, t->leaf_src, t->n_leaf, t->rho_leaf, t->ref_key[t->base], nr, t->base, t->rho_lvl[t->base],
+            t->leaf_key, t->leaf_lvl, D);
     }
     CD_CHECK_LAUNCH();
     // dense levels base .. lf, top-down
     for (int l = t->base; l <= lf; ++l) {
         if (l == t->base) {
             // done above
-        } else if ((t->sparse_finest && l == lf) || (t->sparse_mid && l == lf - 1)) {
+        } else if (!prolonged(l)) {
             // no prolongation into the finest dense levels: fill_deep paints the part that is read
         } else if (l >= 2) {
             LaunchScope ls(CD_K_RESTRICT, s);
@@ -722,7 +748,7 @@ cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s)
         }
         CD_CHECK_LAUNCH();
         const int64_t no = t->oct_begin[l] - t->oct_begin[l - 1];   // octs of level l - 1: their leaf children
-        if (no > 0) {
+        if (no > 0 && prolonged(l)) {
             LaunchScope ls(CD_K_RESTRICT, s);
             scatter_octs<<<grid_for(8 * no, 256), 256, 0, s>>>(t->rho_leaf, t->oct_key + t->oct_begin[l - 1],
                                                                t->oct_leaf + 8 * t->oct_begin[l - 1], no, l,
