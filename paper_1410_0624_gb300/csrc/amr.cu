@@ -59,13 +59,16 @@ struct LeafScatter {
 __global__ void gather_and_mark(const float *__restrict__ in, const int64_t *__restrict__ src, int64_t n,
                                 float *__restrict__ out, const uint64_t *__restrict__ keys, int64_t nr, int l,
                                 float *__restrict__ dense, const uint64_t *__restrict__ lkey,
-                                const int8_t *__restrict__ llvl, const __grid_constant__ LeafScatter D)
+                                const int8_t *__restrict__ llvl, const __grid_constant__ LeafScatter D,
+                                const int32_t *__restrict__ slot, float *__restrict__ rho8)
 {
     const int64_t side = (int64_t)1 << l;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n + nr; i += (int64_t)gridDim.x * blockDim.x) {
         if (i < n) {
             const float v = in[src[i]];
             out[i] = v;
+            const int32_t sl = slot[i];   // the leaf as child of its oct (-1: no oct)
+            if (sl >= 0) rho8[sl] = v;
             const int lv = llvl[i];
             if ((D.mask >> lv) & 1u) {
                 const uint64_t m = lkey[i];
@@ -178,44 +181,34 @@ __global__ void fill_deep(const uint64_t *__restrict__ keys, const int8_t *__res
     }
 }
 
-// Sibling densities of every oct: a leaf child's own density (its row in the
-// output order: an oct whose children are all leaves reads 8 consecutive
-// values), a refined child's volume mean from the dense array of level k+1.
-// One launch over the octs of every level (they are stored level by level,
-// oct_begin[k] .. oct_begin[k+1]).
+// Sibling densities of every oct (oct_rho8, [n_oct][8]): a leaf child's own
+// density is written by gather_and_mark (through leaf_slot); this launch
+// takes the refined children, each the volume mean at level k+1 from the
+// dense array (ref8 lists their slots 8 oct + child; the octs are stored
+// level by level, oct_begin[k] .. oct_begin[k+1]).
 struct Rho8Args {
     const uint64_t *okey;
-    const int32_t *oleaf;
-    const float *rho_leaf;
+    const int32_t *ref8;
     float *rho8;
-    int64_t n8;                          // 8 x all octs
+    int64_t n;                           // refined children
     int nlev;                            // levels 0 .. nlev-1 hold octs
     int64_t begin[CD_MAXL + 2];          // oct_begin
-    const float *dense[CD_MAXL + 1];     // level k+1 as a dense array, or NULL: from the leaves
+    const float *dense[CD_MAXL + 1];     // level k+1 as a dense array
 };
 
 __global__ void gather_rho8(const __grid_constant__ Rho8Args A)
 {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < A.n8; e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < A.n; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = A.ref8[q];
         const int64_t i = e >> 3;
         const int o = (int)(e & 7);
         int k = 0;
         while (k + 1 < A.nlev && i >= A.begin[k + 1]) ++k;
-        const float *dense_k1 = A.dense[k];
-        const int32_t row = A.oleaf[e];
-        float v;
-        if (row >= 0) {
-            v = A.rho_leaf[row];
-        } else if (dense_k1) {
-            const int64_t side = (int64_t)1 << (k + 1);
-            const uint64_t m = A.okey[i];
-            const int64_t x = 2 * (int64_t)compact3(m) + (o & 1), y = 2 * (int64_t)compact3(m >> 1) + ((o >> 1) & 1),
-                          z = 2 * (int64_t)compact3(m >> 2) + ((o >> 2) & 1);
-            v = dense_k1[(z * side + y) * side + x];
-        } else {
-            v = 0.f;   // not reached: the finest octs' children are all leaves
-        }
-        A.rho8[e] = v;
+        const int64_t side = (int64_t)1 << (k + 1);
+        const uint64_t m = A.okey[i];
+        const int64_t x = 2 * (int64_t)compact3(m) + (o & 1), y = 2 * (int64_t)compact3(m >> 1) + ((o >> 1) & 1),
+                      z = 2 * (int64_t)compact3(m >> 2) + ((o >> 2) & 1);
+        A.rho8[e] = A.dense[k][(z * side + y) * side + x];
     }
 }
 
@@ -612,6 +605,17 @@ cd_status build_amr(cd_tree t, int base, int lmax, int64_t n, const int8_t *leve
     if (!up((void **)&t->oct_key, allkey.data(), allkey.size() * 8)) return st;
     if (!up((void **)&t->oct_parent, allpar.data(), allpar.size() * 4)) return st;
     if (!up((void **)&t->oct_leaf, allleaf.data(), allleaf.size() * 4)) return st;
+    {
+        // each leaf's slot among its oct's children, and the refined children's slots
+        std::vector<int32_t> slot(n, -1), ref8;
+        for (size_t j = 0; j < allleaf.size(); ++j) {
+            if (allleaf[j] >= 0) slot[allleaf[j]] = (int32_t)j;
+            else ref8.push_back((int32_t)j);
+        }
+        t->n_ref8 = (int64_t)ref8.size();
+        if (!up((void **)&t->leaf_slot, slot.data(), n * 4)) return st;
+        if (!up((void **)&t->ref8, ref8.data(), ref8.size() * 4)) return st;
+    }
     if (!up((void **)&t->oct_rho8, nullptr, allkey.size() * 8 * 4)) return st;
     if (!up((void **)&t->leaf_key, okey.data(), n * 8)) return st;
     if (!up((void **)&t->leaf_lvl, olvl.data(), n)) return st;
@@ -729,7 +733,7 @@ cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s)
         LaunchScope ls(CD_K_RESTRICT, s);
         gather_and_mark<<<grid_for(t->n_leaf + nr, 256), 256, 0, s>>>(
             rho_dev, t->leaf_src, t->n_leaf, t->rho_leaf, t->ref_key[t->base], nr, t->base, t->rho_lvl[t->base],
-            t->leaf_key, t->leaf_lvl, D);
+            t->leaf_key, t->leaf_lvl, D, t->leaf_slot, t->oct_rho8);
     }
     CD_CHECK_LAUNCH();
     // dense levels base .. lf, top-down
@@ -803,16 +807,15 @@ cd_status update_amr(cd_tree t, const float *rho_dev, cudaStream_t s)
     }
     Rho8Args R = {};
     R.okey = t->oct_key;
-    R.oleaf = t->oct_leaf;
-    R.rho_leaf = t->rho_leaf;
+    R.ref8 = t->ref8;
     R.rho8 = t->oct_rho8;
-    R.n8 = 8 * t->oct_begin[lmax];
+    R.n = t->n_ref8;
     R.nlev = lmax;
     for (int k = 0; k <= lmax; ++k) R.begin[k] = t->oct_begin[k];
     for (int k = 0; k < lmax; ++k) R.dense[k] = k + 1 <= lf ? t->rho_lvl[k + 1] : nullptr;
-    if (R.n8 > 0) {
+    if (R.n > 0) {
         LaunchScope ls(CD_K_RESTRICT, s);
-        gather_rho8<<<grid_for(R.n8, 256), 256, 0, s>>>(R);
+        gather_rho8<<<grid_for(R.n, 256), 256, 0, s>>>(R);
         CD_CHECK_LAUNCH();
     }
     return CD_OK;

@@ -825,7 +825,7 @@ void cd_tree_free(cd_tree t)
     }
     for (void *p : {(void *)t->deep_key, (void *)t->deep_paint, (void *)t->mid_key, (void *)t->mid_paint,
                     (void *)t->oct_key, (void *)t->oct_parent,
-                    (void *)t->oct_leaf, (void *)t->oct_rho8,
+                    (void *)t->oct_leaf, (void *)t->oct_rho8, (void *)t->leaf_slot, (void *)t->ref8,
                     (void *)t->leaf_key, (void *)t->leaf_lvl, (void *)t->leaf_src})
         if (p) cd::lib_free(p);
     delete[] t->leaf_level_h;

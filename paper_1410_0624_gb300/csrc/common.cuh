@@ -183,6 +183,9 @@ struct cd_tree_s {
     cd::TcList tc_ref[CD_MAXL + 1];       // tensor-core lists: refined cells of level k (far-shell prefixes)
     cd::TcList tc_oct[CD_MAXL + 1];       // tensor-core lists: leaf-bearing octs of level k
     float *oct_rho8 = nullptr;            // (device) [n_oct][8] volume-mean density of child o
+    int32_t *leaf_slot = nullptr;         // (device) output order: 8 oct + child of the leaf (-1: no oct)
+    int32_t *ref8 = nullptr;              // (device) the slots 8 oct + child of the refined children
+    int64_t n_ref8 = 0;
     // The finest dense level lf = L-1 is filled only where it is read (when lf >
     // base): leaves and refined cells of lf, and the children of the level-(lf-1)
     // cells around the parents of the octs of level lf (their shells' stencils)
