@@ -480,6 +480,15 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P0, LeafBatch Bt)
             const bool all = __all_sync(0xffffffffu, in_run);
             if ((i & 31) == 0) s_run[g][quarter] = all ? 1 : 0;
         }
+        // list tiles: the rows the copies below need, read from the stage before the
+        // barrier (after it, thread 0 may already prefetch the tile after next into
+        // this stage)
+        int lrow[8];
+        const int lrow0 = lst ? sL[0] : 0;
+        if (lst && i < nb) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) lrow[t] = sL[8 * i + t];
+        }
         fence_proxy_async_smem();
         tc_fence_before();
         named_barrier(bid, 128);
@@ -487,23 +496,24 @@ __global__ void __launch_bounds__(512, 1) leaf_tc(LeafTcArgs P0, LeafBatch Bt)
             bulk_s2g(P.a.n_h + tile * 128 * nd, sO, (uint32_t)(128 * nd * 4));
             bulk_commit();
         }
-        const bool tile_run = lst && P0.out_bulk && sL[0] >= 0 && s_run[g][0] && s_run[g][1] && s_run[g][2] &&
-                              s_run[g][3] && in_bounds(sL[0] + 8 * nb - 1, P.a.n_rows, kCheckLeafTcOut);
+        const bool tile_run = lst && P0.out_bulk && lrow0 >= 0 && s_run[g][0] && s_run[g][1] && s_run[g][2] &&
+                              s_run[g][3] && in_bounds(lrow0 + 8 * nb - 1, P.a.n_rows, kCheckLeafTcOut);
         if (tile_run && i == 0) {
-            bulk_s2g(P.a.n_h + (int64_t)sL[0] * nd, sO, (uint32_t)(8 * nb * nd * 4));
+            bulk_s2g(P.a.n_h + (int64_t)lrow0 * nd, sO, (uint32_t)(8 * nb * nd * 4));
             bulk_commit();
         }
         if (lst && P0.out_bulk && i < nb && !tile_run) {
             // oct i's children: one copy when their rows are consecutive, else one per leaf row
-            const int r0 = sL[8 * i];
+            const int r0 = lrow[0];
             bool run = r0 >= 0 && in_bounds(r0 + 7, P.a.n_rows, kCheckLeafTcOut);
 #pragma unroll
-            for (int t = 1; t < 8; ++t) run = run && sL[8 * i + t] == r0 + t;
+            for (int t = 1; t < 8; ++t) run = run && lrow[t] == r0 + t;
             if (run) {
                 bulk_s2g(P.a.n_h + (int64_t)r0 * nd, sO + (size_t)8 * i * nd, (uint32_t)(8 * nd * 4));
             } else {
+#pragma unroll
                 for (int t = 0; t < 8; ++t) {
-                    const int r = sL[8 * i + t];
+                    const int r = lrow[t];
                     if (r >= 0 && in_bounds(r, P.a.n_rows, kCheckLeafTcOut))
                         bulk_s2g(P.a.n_h + (int64_t)r * nd, sO + (size_t)(8 * i + t) * nd, (uint32_t)(nd * 4));
                 }
