@@ -78,3 +78,41 @@ def test_batch_outputs_rejected_per_box(stub):
         colden.Batch(trees, geoms, n_h=good[:1])
     with pytest.raises(ValueError, match="geometries"):
         colden.Batch(trees, geoms[:1], n_h=good)
+
+
+def test_eval_graph_buffers_checked_before_the_library(stub):
+    """colden.EvalGraph checks rho (n_leaf floats) and the outputs as the
+    evaluation does, before cd_eval_graph_create is reached."""
+    t, g = _tree(), _geom()
+    with pytest.raises(ValueError, match="rho holds 63"):
+        colden.EvalGraph(t, g, rho=torch.empty(63), n_h=torch.empty(64 * 12))
+    with pytest.raises(ValueError, match="n_h holds 767"):
+        colden.EvalGraph(t, g, rho=torch.empty(64), n_h=torch.empty(64 * 12 - 1))
+    with pytest.raises(ValueError, match="shield"):
+        colden.EvalGraph(t, g, shield=torch.empty(10))
+    with pytest.raises(ValueError):
+        colden.EvalGraph(t, g, rho=torch.empty(64, dtype=torch.float64))
+
+
+def test_fit_delta_range_passes_the_target_count(monkeypatch):
+    """Net.fit_delta_range hands the library every target (numel) and the
+    margin; the range it reports is the library's."""
+    calls = {}
+
+    class Lib:
+        def cd_net_fit_delta_range(self, h, n, y, margin, stream):
+            calls.update(n=n, margin=margin)
+            return 0
+
+        def cd_net_get_delta_range(self, h, lo, hi):
+            lo._obj.value, hi._obj.value = -1.5, 2.5
+            return 0
+
+    monkeypatch.setattr(colden, "_lib", Lib())
+    net = object.__new__(colden.Net)
+    net._h = colden.ctypes.c_void_p(1)
+    with mock.patch.object(torch.Tensor, "is_cuda", new_callable=mock.PropertyMock, return_value=True):
+        got = net.fit_delta_range(torch.empty(7, 48), 0.25, stream=0)
+    net._h = None
+    assert calls == {"n": 7 * 48, "margin": 0.25}
+    assert got == (-1.5, 2.5)
